@@ -1,0 +1,92 @@
+"""Pins of the oracle's quadratures against closed forms, brute force and numpy.
+
+Half-range Hermite quadrature: Sec. IV.B.1 (Eqs. "eq:hh_quad", "eq:wk_half"),
+App. B.  Full-range Gauss-Hermite: Sec. IV.A.1 (Eqs. "eq:H_quad", "eq:H_wk").
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle.quadrature import gauss_hermite, half_range_hermite, to_f64
+
+
+def mu(s):
+    """int_0^inf z^s exp(-z^2/2)/sqrt(2 pi) dz via the Gamma function."""
+    return 2.0 ** ((s - 1) / 2.0) * math.gamma((s + 1) / 2.0) / math.sqrt(2 * math.pi)
+
+
+def test_q1_closed_form():
+    # h_1 is proportional to z - mu_1/mu_0: root sqrt(2/pi), weight mu_0 = 1/2.
+    d = half_range_hermite(1)
+    assert float(d["z"][0]) == pytest.approx(math.sqrt(2 / math.pi), rel=1e-15)
+    assert float(d["w"][0]) == pytest.approx(0.5, rel=1e-15)
+
+
+def test_q2_closed_form():
+    # Monic pi_2 = z^2 + a z + b orthogonal to 1 and z; roots by the quadratic
+    # formula; weights from sum_k w_k z_k^s = mu_s for s = 0, 1.
+    m = [mu(s) for s in range(4)]
+    A = np.array([[m[1], m[0]], [m[2], m[1]]])
+    a, b = np.linalg.solve(A, [-m[2], -m[3]])
+    r = np.sort(np.roots([1.0, a, b]).real)
+    w = np.linalg.solve(np.vstack([np.ones(2), r]), [m[0], m[1]])
+    d = half_range_hermite(2)
+    np.testing.assert_allclose(to_f64(d["z"]), r, rtol=1e-13)
+    np.testing.assert_allclose(to_f64(d["w"]), w, rtol=1e-13)
+
+
+@pytest.mark.parametrize("Q", [1, 2, 3, 4, 5, 8, 12, 16])
+def test_half_range_exactness_brute_force(Q):
+    # Gauss rule of order Q is exact for degree < 2Q (Sec. IV.B.1), and not beyond.
+    d = half_range_hermite(Q)
+    z, w = to_f64(d["z"]), to_f64(d["w"])
+    assert np.all(z > 0) and np.all(np.diff(z) > 0) and np.all(w > 0)
+    for s in range(2 * Q):
+        assert np.sum(w * z ** s) == pytest.approx(mu(s), rel=2e-13)
+    if Q <= 8:   # the degree-2Q defect shrinks fast with Q; FP64 resolves it up to Q = 8
+        assert abs(np.sum(w * z ** (2 * Q)) - mu(2 * Q)) > 1e-9 * mu(2 * Q)
+
+
+@pytest.mark.parametrize("Q", [2, 4, 8])
+def test_half_range_orthonormality_by_integration(Q):
+    # <h_l, h_l'> = delta over [0, inf) with omega, integrated numerically.
+    C = half_range_hermite(Q)["C"]
+    om = lambda z: math.exp(-z * z / 2) / math.sqrt(2 * math.pi)
+    h = lambda l, z: sum(float(C[l][s]) * z ** s for s in range(l + 1))
+    for l in range(Q + 1):
+        for lp in range(l + 1):
+            val, _ = integrate.quad(lambda z: om(z) * h(l, z) * h(lp, z), 0, np.inf,
+                                    epsabs=1e-13, epsrel=1e-12, limit=200)
+            assert val == pytest.approx(1.0 if l == lp else 0.0, abs=1e-9)
+        assert float(C[l][l]) > 0
+
+
+@pytest.mark.parametrize("Q", [2, 4, 8, 16])
+def test_half_range_christoffel_weights(Q):
+    # For orthonormal polynomials the Gauss weights are 1 / sum_{l<Q} h_l(z_k)^2,
+    # a different formula from Eq. "eq:wk_half" used by the oracle.
+    d = half_range_hermite(Q)
+    C = d["C"]
+    from oracle.quadrature import poly_eval
+    for zk, wk in zip(d["z"], d["w"]):
+        s = sum(poly_eval(C[l][: l + 1], zk) ** 2 for l in range(Q))
+        assert float(1 / s) == pytest.approx(float(wk), rel=1e-14)
+
+
+@pytest.mark.parametrize("Q", range(1, 17))
+def test_half_range_envelope(Q):
+    # All half-range Hermite points lie within +-2.5 sqrt(Q) (Fig. "hh_hyp" caption).
+    z = to_f64(half_range_hermite(Q)["z"])
+    assert z.max() < 2.5 * math.sqrt(Q)
+
+
+@pytest.mark.parametrize("Q", [2, 4, 6, 8, 16])
+def test_gauss_hermite_matches_numpy(Q):
+    # Probabilists' Gauss-Hermite with omega normalised to unit mass.
+    x, w = np.polynomial.hermite_e.hermegauss(Q)
+    d = gauss_hermite(Q)
+    np.testing.assert_allclose(to_f64(d["z"]), x, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(to_f64(d["w"]), w / math.sqrt(2 * math.pi), rtol=1e-12)
+    assert np.abs(to_f64(d["z"])).max() < 2 * math.sqrt(Q)   # envelope +-2 sqrt(Q)
