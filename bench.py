@@ -1,0 +1,302 @@
+"""Benchmark of the RK-3 step on the large 2D channel (1024 x 512 nodes,
+16 x 8 x 8 = 1024 velocities, FP32, WENO-5, walls T = 1 and 2, Kn = 0.5,
+a = (-0.3, -0.3, 0)).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = one RK-3 step (three wall + three stage kernels) over the whole
+grid.  The metric is node-velocity updates per second (a node-velocity update
+advances one (node, velocity) value one full RK-3 step).  Prints one JSON
+line.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of
+the same workload instead.  Under torchrun each rank runs an independent
+replica (the method has no data-parallel split that needs a collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1708_03249_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = "large_2d_channel_1024x512_hhlb8x8x8_weno5_fp32"
+METRIC = "node-velocity updates/s"
+BYTES_PER_NV_STAGE = 32.0 / 3.0      # FP32: stage 1 reads f^n, writes f1 (8 B); stages 2, 3 read two, write one (12 B)
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("hlb_kernels.cu", "hlb_internal.h"):
+        with open(os.path.join(ROOT, "paper_1708_03249_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        mx = float(parts[2])
+                    except ValueError:
+                        continue
+                    for name, val in zip(names, parts[5:9]):
+                        if val.lower() == "active":
+                            reasons.add(name)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------
+def oracle_sample(steps: int = 1, nx: int = 32, ny: int = 32):
+    """Time the FP64 oracle on an nx x ny window of the same workload (same
+    velocity set, physics and dt), ``steps`` RK-3 steps; returns (nv/s, secs, desc)."""
+    import numpy as np
+    from oracle.solver import Solver, config_from
+    cfg = dict(W.LARGE_2D)
+    full_dx = cfg["Lx"] / cfg["nx"]
+    cfg.update(nx=nx, ny=ny, Lx=nx * full_dx, Ly=ny * full_dx)
+    s = Solver(config_from(cfg))
+    s.init_equilibrium(1.0, 0.05, -0.02, 1.2)
+    s.f *= W.perturbation(s.f.shape, seed=3, amplitude=0.02)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    nv = nx * ny * s.vs.V * steps
+    desc = f"{nx}x{ny} nodes of the workload's velocity set x {steps} RK-3 step(s), FP64 numpy oracle"
+    return nv / dt, dt, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    total_nv, total_t = 0.0, 0.0
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        rate, secs, desc = oracle_sample(steps=1)
+        if i >= args.warmup:
+            total_nv += rate * secs
+            total_t += secs
+    value = total_nv / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "node-velocity updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "node-velocity updates/s", "cores": 1,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "node-velocity updates/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1708_03249_gb300 import build as hbuild
+    from paper_1708_03249_gb300 import hlb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(hlb.LIB_PATH):
+        if rank == 0:
+            hbuild.build()
+        if dist is not None:
+            dist.barrier()
+    stream = torch.cuda.Stream()
+    cfg = W.LARGE_2D
+    h = hlb.Handle(cfg, stream=stream.cuda_stream)
+    nodes, values, state_bytes = h.nodes, h.values, h.state_bytes
+    V = values // nodes
+    h.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up (graph replay off: the timed region launches eagerly with per-launch events)
+    h.set_options(use_graphs=False, time_kernels=True)
+    h.step(args.warmup)
+    torch.cuda.synchronize()
+    h.kernel_times(reset=True)
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        h.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    kt = h.kernel_times(reset=True)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    n, u, T, q = h.moments()
+    finite = bool(np.isfinite(n).all() and np.isfinite(T).all())
+    value = world * nodes * V * args.steps / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: H2D of the state from
+    # pinned memory, one RK-3 step, D2H of the moments, every iteration
+    pinned = torch.empty(values, dtype=torch.float32, pin_memory=True)
+    h.get_state(pinned.numpy())
+    h.set_options(use_graphs=True, time_kernels=False)
+    e2e_iters = max(2, min(args.steps, 5))
+    moms = [np.empty(nodes), np.empty(3 * nodes), np.empty(nodes), np.empty(nodes)]
+    import ctypes
+    ptrs = [m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for m in moms]
+    lib = hlb.lib()
+    for it in range(1 + e2e_iters):
+        if it == 1:
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        hlb._check(lib.hlb_set_state(h._h, pinned.data_ptr(), state_bytes))
+        h.step(1)
+        hlb._check(lib.hlb_moments(h._h, *ptrs))
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * nodes * V * e2e_iters / e2e_s
+    h.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    stage_avg_ms = kt["stage_ms"] / max(kt["stage_launches"], 1)
+    achieved = nodes * V * BYTES_PER_NV_STAGE / (stage_avg_ms * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        with open(PROFILE_TRAFFIC) as fh:
+            prof = json.load(fh)
+        if prof.get("kernel_hash") == kernel_source_hash():
+            traffic = prof.get("dram_bytes_per_launch")
+    cpu_rate, cpu_secs, cpu_desc = oracle_sample(steps=3)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "node-velocity updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": cfg["nx"], "ny": cfg["ny"], "velocities": V,
+                   "nodes": nodes, "values_per_copy": values, "precision": "fp32",
+                   "advection": "weno5", "parallelism": f"replicas{world}",
+                   "l2": "state (2.15 GB per copy) larger than L2; no flush needed",
+                   "moments_finite": finite},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "stage_kernel<float, WENO5>",
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                     "stage_avg_ms": stage_avg_ms,
+                     "stage_share": kt["stage_ms"] / max(kt["stage_ms"] + kt["wall_ms"], 1e-9),
+                     "bytes_per_unit": BYTES_PER_NV_STAGE, "unit_desc": "node-velocity per stage launch"},
+        "cpu_baseline": {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": 1,
+                         "kind": "oracle", "sample": cpu_desc},
+        "e2e": {"value": e2e_value, "unit": "node-velocity updates/s",
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": 6 * 8 * nodes},
+        "gpu_launches": kt["stage_launches"] + kt["wall_launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

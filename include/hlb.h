@@ -1,0 +1,200 @@
+/*
+ * hlb.h -- C ABI of libhlb, the GB300 (sm_103a) time step of the half-range
+ * Gauss-Hermite lattice Boltzmann model with a force term
+ * (Ambrus, Sofonea, Fournier, Blanco, arXiv:1708.03249).
+ *
+ * The library advances the discrete Boltzmann-BGK equation with an external
+ * force (Eq. "eq:boltzk"; multi-D form Eq. "eq:boltz_multi_k", App. A)
+ *     d_t f_k + p_k . grad f_k + a . (grad_p f)_k = -(f_k - feq_k)/tau
+ * for a gas between two diffuse-reflecting walls at rest (Sec. V, Eq.
+ * "eq:fwall"), walls at x = 0 and x = Lx, periodic in y.  Units: m = 1 and
+ * p_0 = 1 (momenta equal velocities); a = F/m.
+ *
+ *  - momentum set (App. A): p_x on the half-range Gauss-Hermite quadrature
+ *    of order Qx per half (2 Qx values, Sec. IV.B.1, Eq. "eq:hh_pk"); p_y and
+ *    p_z on full-range Gauss-Hermite quadratures of even order Qy, Qz
+ *    (Sec. IV.A.1; 0 = axis absent);
+ *  - force: (grad_p f)_k = sum_k' K_kk' f_k' per axis, with K^h of Eq.
+ *    "eq:hh_Kk_hh" along p_x (the paper's main result: the distributional
+ *    derivative across the p_x = 0 jump) and K^H of Eq. "eq:H_Kk" along p_y,
+ *    p_z;
+ *  - collision: BGK towards feq = n g_x g_y g_z (Eqs. "eq:hh_gk", "eq:H_gk"),
+ *    tau = Kn/n (Eq. "eq:tau");
+ *  - advection: WENO-5 without epsilon (Sec. IV.C.2, Tab. "weno") or linear
+ *    2nd-order upwind, on a uniform or tanh-stretched grid (Eq. "eq:x_eta");
+ *  - walls: diffuse reflection with the emitted density fixed by zero net
+ *    mass flux (Sec. IV.C.3, Eq. "eq:nplus_def");
+ *  - time: the TVD RK-3 of Eq. "eq:rk3".
+ *
+ * Memory and ownership.  A handle owns all device memory (the state, two
+ * stage buffers, tables) and enqueues on the CUDA stream given at creation
+ * (or on a stream of its own).  Every pointer argument below is a HOST pointer owned by
+ * the caller unless its name ends in _dev; a _dev pointer is device memory
+ * owned by the caller, valid for the duration of the call.  The CUDA device
+ * is the one current on the calling thread at hlb_create; later calls must
+ * be made with that device current.
+ *
+ * State layout (the "logical state" of get/set_state): for each instance in
+ * creation order, f[y][x][kz][jy][ix], ix fastest (2 Qx entries, the first Qx
+ * for p_x = +z_k, the next Qx for p_x = -z_k), then jy (max(Qy,1)), kz
+ * (max(Qz,1)); element type double for HLB_FP64 handles, float for HLB_FP32.
+ *
+ * Errors.  Every call returns an hlb_status; nothing aborts.  On failure
+ * hlb_last_error() returns a message describing the most recent failing call
+ * of the calling thread.  HLB_ECUDA is returned for any CUDA runtime error
+ * (the message carries cudaGetErrorString); a handle whose call returned
+ * HLB_ECUDA should be destroyed.  HLB_EINVAL is returned, before any device
+ * work, for invalid arguments.
+ */
+#ifndef HLB_H
+#define HLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hlb_handle hlb_handle;
+
+typedef enum {
+    HLB_OK = 0,
+    HLB_EINVAL = 1,        /* invalid argument (checked on the host)           */
+    HLB_ENOMEM = 2,        /* device or host allocation failed                 */
+    HLB_ECUDA = 3,         /* a CUDA runtime call failed                       */
+    HLB_ETIMEOUT = 4,      /* a bounded device wait gave up                    */
+    HLB_ENONFINITE = 5,    /* NaN or Inf found in the moments                  */
+    HLB_EUNSUPPORTED = 6   /* valid request this build does not implement      */
+} hlb_status;
+
+enum { HLB_UPWIND2 = 0, HLB_WENO5 = 1 };
+enum { HLB_FP64 = 0, HLB_FP32 = 1 };
+
+/* One channel instance.  Field order and types are part of the ABI. */
+typedef struct {
+    int Qx;              /* half-range order per half, 1..32 (2 Qx values of p_x)          */
+    int Qy, Qz;          /* full-range orders: 0 (axis absent) or even 2..32 (Sec. IV.A.1) */
+    int Nx_eq, Ny_eq, Nz_eq; /* equilibrium orders N (0 <= N < Q); -1 => Q - 1            */
+    int nx, ny;          /* cells: nx >= 6 (WENO5) or >= 3 (upwind2) between the walls;
+                            ny >= 1 periodic cells in y (ny = 1: 1D channel)               */
+    double Lx, Ly;       /* channel width (walls at x = 0, Lx) and periodic length in y   */
+    double stretch_A;    /* 0: uniform; 0 < A < 1: tanh stretching, Eqs. "eq:x_eta","eq:etai" */
+    int advection;       /* HLB_UPWIND2 or HLB_WENO5                                      */
+    int precision;       /* HLB_FP64 or HLB_FP32 (state and bulk arithmetic)              */
+    double cfl;          /* dt = cfl / (max|p_x|/min dx + [ny>1] max|p_y|/dy) if dt <= 0   */
+    double dt;           /* explicit time step if > 0                                     */
+    double T_left, T_right;  /* wall temperatures (> 0) at x = 0 and x = Lx               */
+    double ax, ay, az;   /* acceleration a = F/m; gravity g along -x is ax = -g            */
+    double Kn;           /* Knudsen number > 0; +INFINITY = collisionless (no BGK term)   */
+} hlb_config;
+
+/* Create a handle for `ninst` independent instances (ninst >= 1).  Instances
+ * that share (Qx, Qy, Qz, N*, advection) are advanced together by the same
+ * kernels; mixed velocity sets form separate groups.  All instances of one
+ * handle must share `precision`.  `cuda_stream` is a cudaStream_t on which
+ * every later call enqueues its work; NULL makes the handle create (and
+ * later destroy) its own non-blocking stream.  The state is zero until
+ * hlb_init_equilibrium or hlb_set_state.
+ * Errors: HLB_EINVAL (bad config: message names the instance and field),
+ * HLB_ENOMEM, HLB_ECUDA. */
+hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_handle** out);
+
+/* Free everything the handle owns (after synchronising its stream).  NULL is a no-op. */
+void hlb_destroy(hlb_handle* h);
+
+/* Per-instance parameters (inst = -1: all instances).  Wall temperatures
+ * define the emitted Maxwellians g^w = g_x(0,T_w) g_y(0,T_w) g_z(0,T_w)
+ * (Eq. "eq:fwall"); ax, ay, az the acceleration (App. A, Eq. "eq:Fnp_exp");
+ * Kn the relaxation tau = Kn/n (Eq. "eq:tau").  Changing the walls or the
+ * force after a step is allowed; the CFL time step is fixed at creation.
+ * Errors: HLB_EINVAL. */
+hlb_status hlb_set_walls(hlb_handle* h, int inst, double T_left, double T_right);
+hlb_status hlb_set_force(hlb_handle* h, int inst, double ax, double ay, double az);
+hlb_status hlb_set_Kn(hlb_handle* h, int inst, double Kn);
+
+/* State = n g_x(ux,T) g_y(uy,T) g_z(0,T) at every node of every instance
+ * (App. A equilibrium), computed on the host in FP64 and broadcast on the
+ * device.  Enqueued on the handle's stream.  Errors: HLB_EINVAL (n, T <= 0). */
+hlb_status hlb_init_equilibrium(hlb_handle* h, double n, double ux, double uy, double T);
+
+/* Enqueue `nsteps` RK-3 steps (Eq. "eq:rk3") on the handle's stream and
+ * return without waiting.  Each step runs, per stage: the wall kernel (the
+ * emitted densities n_w from the incident fluxes, FP64 balance) and the
+ * fused stage kernel (moments, equilibrium, force, BGK, advection, RK
+ * combination).  With graphs enabled (default) the steps are replayed from a
+ * captured CUDA graph.  Errors: HLB_EINVAL (nsteps < 0), HLB_ECUDA. */
+hlb_status hlb_step(hlb_handle* h, long nsteps);
+
+/* Macroscopic moments of the current state (Eq. "eq:fmoms", App. A), in
+ * FP64, for all nodes of all instances in state order.  n, T, q: one value
+ * per node; u: 3 values per node (u_x, u_y, u_z).  T = sum |p-u|^2 f/(D n)
+ * with D the number of momentum axes; q = q_x = sum (p_x-u_x)|p-u|^2 f/2.
+ * Any output pointer may be NULL.  Synchronises the handle's stream.
+ * Errors: HLB_ECUDA, HLB_ENONFINITE (a non-finite n or T; outputs are
+ * still written). */
+hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q);
+
+/* Same as hlb_moments, but the outputs are device arrays (each may be NULL);
+ * enqueued on the handle's stream, no synchronisation, no non-finite check. */
+hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev);
+
+/* Number of nodes and of values in the state (all instances), and the bytes
+ * of one state copy.  Any output pointer may be NULL. */
+hlb_status hlb_sizes(const hlb_handle* h, long long* nodes, long long* values, long long* bytes);
+
+/* Time step and step counter of instance `inst`. */
+hlb_status hlb_get_dt(const hlb_handle* h, int inst, double* dt);
+hlb_status hlb_get_nsteps(const hlb_handle* h, long long* nsteps);
+
+/* Copy the state to / from a caller buffer of exactly hlb_sizes(...bytes)
+ * bytes (layout in the header comment).  Host variants synchronise the
+ * stream; _dev variants enqueue a device copy.  Errors: HLB_EINVAL (size). */
+hlb_status hlb_get_state(hlb_handle* h, void* host_f, size_t bytes);
+hlb_status hlb_set_state(hlb_handle* h, const void* host_f, size_t bytes);
+hlb_status hlb_get_state_dev(hlb_handle* h, void* f_dev, size_t bytes);
+hlb_status hlb_set_state_dev(hlb_handle* h, const void* f_dev, size_t bytes);
+
+/* Diagnostics of the current state: the particle number per instance
+ * N = int n dx dy (Eq. "eq:Ndef"; ninst values) and the last step's
+ * residual max|f^{n+1} - f^n| / (dt max|f^{n+1}|) per instance (0 before the
+ * first step).  Either pointer may be NULL.  Synchronises. */
+hlb_status hlb_diag(hlb_handle* h, double* total_N, double* residual);
+
+/* Host-side tables of instance `inst`'s velocity set, for inspection and
+ * testing (no device work).  Any pointer may be NULL; sizes: px 2Qx, py
+ * max(Qy,1), pz max(Qz,1), wx 2Qx, wy, wz likewise, Kx (2Qx)^2 row-major
+ * [k][k'], Ky Qy^2, Kz Qz^2, x-cell widths nx. */
+hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, double* pz,
+                      double* wx, double* wy, double* wz, double* Kx, double* Ky, double* Kz,
+                      double* dx);
+
+/* One momentum axis built on the host (no handle, no device work): half != 0
+ * gives the half-range Hermite axis of order Q (2Q points, Eq. "eq:hh_pk",
+ * K^h of Eq. "eq:hh_Kk_hh"), half == 0 the full-range Gauss-Hermite axis of
+ * even order Q (Q points, K^H of Eq. "eq:H_Kk").  p and w have the axis'
+ * point count, K its square (row-major [k][k']); any pointer may be NULL. */
+hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K);
+
+/* Equilibrium g_x(u, T) (2Qx values) of a velocity set, computed on the host
+ * by the same per-node routine the kernels use (FP64).  No handle needed. */
+hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g);
+
+/* Enable (1) / disable (0) CUDA-graph replay in hlb_step, and per-launch
+ * CUDA-event timing (timing forces eager launches).  hlb_kernel_times
+ * returns the accumulated device time (ms) and launch counts of the stage
+ * and wall kernels since the last reset (reset != 0 clears them after
+ * reading).  Synchronises. */
+hlb_status hlb_set_options(hlb_handle* h, int use_graphs, int time_kernels);
+hlb_status hlb_kernel_times(hlb_handle* h, double* stage_ms, long long* stage_launches,
+                            double* wall_ms, long long* wall_launches, int reset);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char* hlb_last_error(void);
+
+/* Library version string. */
+const char* hlb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLB_H */

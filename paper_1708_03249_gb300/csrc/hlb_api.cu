@@ -1,0 +1,781 @@
+// C ABI of libhlb: handle management, tables upload, RK-3 stepping (eager or
+// replayed from a captured CUDA graph), moments, state I/O and diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hlb.h"
+#include "hlb_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hlb_status fail(hlb_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define HLB_CUDA(expr)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(HLB_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+struct Group {
+    int precision = HLB_FP32, adv = HLB_WENO5;
+    int Qx = 0, Qy = 0, Qz = 0, Nx = 0, Ny = 0, Nz = 0;
+    hlb::AxisTables tx, ty, tz;
+    int V = 0, QX2 = 0, VY = 1, VZ = 1;
+    size_t esize = 4;
+    std::vector<int> members;               // handle-level instance ids
+    std::vector<hlb::InstDev> inst;
+    std::vector<int> node_start, row_start;
+    std::vector<double> dx_all;
+    long long nvalues = 0;
+    int nnodes = 0, nrows = 0;
+    DevBuf buf[3];
+    int cur = 0, prev = -1;
+    DevBuf d_inst, d_node_start, d_row_start, d_K, d_p, d_pd, d_T, d_rec, d_dx, d_gw, d_nw, d_resid;
+    DevBuf d_mom;                            // moments scratch: 6 doubles per node
+    hlb::GroupDev dev{};
+    int block = 256, grid = 1;
+    size_t smem = 0;
+};
+
+struct KernelTimer {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> stage, wall;
+};
+
+}  // namespace
+
+struct hlb_handle {
+    std::vector<hlb_config> cfg;
+    std::vector<int> inst_group, inst_local;
+    std::vector<long long> inst_node_off;    // global node offset of each instance
+    std::vector<long long> inst_value_off;   // global value offset of each instance
+    std::vector<std::unique_ptr<Group>> groups;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int precision = HLB_FP32;
+    long long nsteps = 0;
+    long long total_nodes = 0, total_values = 0;
+    bool use_graphs = true, time_kernels = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    KernelTimer timer;
+    double stage_ms = 0, wall_ms = 0;
+    long long stage_n = 0, wall_n = 0;
+    bool have_residual = false;
+    size_t esize = 4;
+};
+
+namespace {
+
+std::string check_config(const hlb_config& c, int i) {
+    auto bad = [&](const char* what) { return "instance " + std::to_string(i) + ": " + what; };
+    if (c.Qx < 1 || c.Qx > hlb::kMaxQ) return bad("Qx must be in [1, 32]");
+    for (int q : {c.Qy, c.Qz})
+        if (q < 0 || q > hlb::kMaxQ || (q % 2)) return bad("Qy, Qz must be 0 or even in [2, 32]");
+    if (c.Nx_eq >= c.Qx || c.Nx_eq < -1) return bad("Nx_eq must be -1 or in [0, Qx - 1]");
+    if (c.Qy && (c.Ny_eq >= c.Qy || c.Ny_eq < -1)) return bad("Ny_eq must be -1 or in [0, Qy - 1]");
+    if (c.Qz && (c.Nz_eq >= c.Qz || c.Nz_eq < -1)) return bad("Nz_eq must be -1 or in [0, Qz - 1]");
+    if (c.advection != HLB_WENO5 && c.advection != HLB_UPWIND2) return bad("advection must be HLB_UPWIND2 or HLB_WENO5");
+    if (c.precision != HLB_FP32 && c.precision != HLB_FP64) return bad("precision must be HLB_FP64 or HLB_FP32");
+    if (c.nx < (c.advection == HLB_WENO5 ? 6 : 3)) return bad("nx must be >= 6 (WENO5) or >= 3 (upwind2)");
+    if (c.ny < 1 || c.ny == 2) return bad("ny must be 1 or >= 3");
+    if ((long long)c.nx * c.ny > (1LL << 30)) return bad("nx * ny too large");
+    if (!(c.Lx > 0) || !std::isfinite(c.Lx)) return bad("Lx must be > 0");
+    if (c.ny > 1 && (!(c.Ly > 0) || !std::isfinite(c.Ly))) return bad("Ly must be > 0");
+    if (!(c.stretch_A >= 0 && c.stretch_A < 1)) return bad("stretch_A must be in [0, 1)");
+    if (!(c.dt > 0) && !(c.cfl > 0)) return bad("either dt > 0 or cfl > 0");
+    if (!std::isfinite(c.dt) || !std::isfinite(c.cfl)) return bad("dt and cfl must be finite");
+    if (!(c.T_left > 0) || !(c.T_right > 0) || !std::isfinite(c.T_left) || !std::isfinite(c.T_right))
+        return bad("wall temperatures must be finite and > 0");
+    if (!std::isfinite(c.ax) || !std::isfinite(c.ay) || !std::isfinite(c.az)) return bad("acceleration must be finite");
+    if (!(c.Kn > 0)) return bad("Kn must be > 0 (+INFINITY: collisionless)");
+    return "";
+}
+
+template <typename T>
+hlb_status upload(DevBuf& b, const std::vector<T>& v) {
+    if (b.p) { cudaFree(b.p); b.p = nullptr; }
+    size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) return fail(HLB_ENOMEM, "cudaMalloc of tables failed");
+    if (!v.empty()) HLB_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HLB_OK;
+}
+
+template <typename R>
+std::vector<R> cast_vec(const std::vector<double>& v) {
+    return std::vector<R>(v.begin(), v.end());
+}
+
+hlb_status upload_real(DevBuf& b, const std::vector<double>& v, int precision) {
+    return precision == HLB_FP64 ? upload(b, v) : upload(b, cast_vec<float>(v));
+}
+
+// Wall Maxwellian of a group at temperature Tw (V values, FP64) and its
+// emitted-flux denominator for the given wall side.
+void wall_maxwellian(const Group& G, double Tw, std::vector<double>& gvec) {
+    std::vector<double> gx(G.QX2), gy(G.VY), gz(G.VZ);
+    hlb::axis_equilibrium(G.tx, 0.0, Tw, gx.data());
+    hlb::axis_equilibrium(G.ty, 0.0, Tw, gy.data());
+    hlb::axis_equilibrium(G.tz, 0.0, Tw, gz.data());
+    gvec.assign(G.V, 0.0);
+    for (int k = 0; k < G.VZ; ++k)
+        for (int j = 0; j < G.VY; ++j)
+            for (int i = 0; i < G.QX2; ++i) gvec[(k * G.VY + j) * G.QX2 + i] = gx[i] * gy[j] * gz[k];
+}
+
+double emitted_denominator(const Group& G, const std::vector<double>& gvec, bool left) {
+    double s = 0.0;
+    for (int v = 0; v < G.V; ++v) {
+        const double px = G.tx.p[v % G.QX2];
+        if ((left && px > 0) || (!left && px < 0)) s += px * gvec[v];
+    }
+    return s;
+}
+
+hlb_status upload_inst(Group& G) { return upload(G.d_inst, G.inst); }
+
+hlb_status refresh_walls(hlb_handle* h, Group& G) {
+    std::vector<double> all((size_t)G.members.size() * 2 * G.V);
+    for (size_t m = 0; m < G.members.size(); ++m) {
+        const hlb_config& c = h->cfg[G.members[m]];
+        std::vector<double> gl, gr;
+        wall_maxwellian(G, c.T_left, gl);
+        wall_maxwellian(G, c.T_right, gr);
+        G.inst[m].den_left = emitted_denominator(G, gl, true);
+        G.inst[m].den_right = emitted_denominator(G, gr, false);
+        G.inst[m].gw_off = (int)(m * 2 * G.V);
+        std::copy(gl.begin(), gl.end(), all.begin() + m * 2 * G.V);
+        std::copy(gr.begin(), gr.end(), all.begin() + m * 2 * G.V + G.V);
+    }
+    hlb_status s = upload_real(G.d_gw, all, G.precision);
+    if (s != HLB_OK) return s;
+    return upload_inst(G);
+}
+
+void fill_dev(Group& G) {
+    hlb::GroupDev& d = G.dev;
+    d.V = G.V; d.QX2 = G.QX2; d.VY = G.VY; d.VZ = G.VZ; d.Qx = G.Qx;
+    d.Nx = G.Nx; d.Ny = G.Qy ? G.Ny : 0; d.Nz = G.Qz ? G.Nz : 0;
+    d.Qy = G.Qy; d.Qz = G.Qz;
+    d.D = 1 + (G.Qy > 0) + (G.Qz > 0);
+    d.ninst = (int)G.members.size();
+    d.nnodes = G.nnodes;
+    d.nrows = G.nrows;
+    d.inst = (const hlb::InstDev*)G.d_inst.p;
+    d.node_start = (const int*)G.d_node_start.p;
+    d.row_start = (const int*)G.d_row_start.p;
+    d.K = G.d_K.p; d.p = G.d_p.p; d.pd = (const double*)G.d_pd.p; d.Tt = G.d_T.p;
+    d.rec = (const double*)G.d_rec.p; d.dx = (const double*)G.d_dx.p;
+    d.gw = G.d_gw.p; d.nw = (double*)G.d_nw.p;
+}
+
+hlb_status build_group(hlb_handle* h, Group& G) {
+    const hlb_config& c0 = h->cfg[G.members[0]];
+    G.precision = c0.precision;
+    G.adv = c0.advection;
+    G.Qx = c0.Qx; G.Qy = c0.Qy; G.Qz = c0.Qz;
+    G.Nx = c0.Nx_eq < 0 ? c0.Qx - 1 : c0.Nx_eq;
+    G.Ny = c0.Qy ? (c0.Ny_eq < 0 ? c0.Qy - 1 : c0.Ny_eq) : 0;
+    G.Nz = c0.Qz ? (c0.Nz_eq < 0 ? c0.Qz - 1 : c0.Nz_eq) : 0;
+    std::string e = hlb::build_half_axis(G.Qx, G.Nx, G.tx);
+    if (!e.empty()) return fail(HLB_EINVAL, e);
+    if (G.Qy) { e = hlb::build_full_axis(G.Qy, G.Ny, G.ty); if (!e.empty()) return fail(HLB_EINVAL, e); }
+    else hlb::absent_axis(G.ty);
+    if (G.Qz) { e = hlb::build_full_axis(G.Qz, G.Nz, G.tz); if (!e.empty()) return fail(HLB_EINVAL, e); }
+    else hlb::absent_axis(G.tz);
+    G.QX2 = 2 * G.Qx; G.VY = G.ty.count; G.VZ = G.tz.count;
+    G.V = G.QX2 * G.VY * G.VZ;
+    G.esize = G.precision == HLB_FP64 ? 8 : 4;
+
+    // instances
+    G.inst.resize(G.members.size());
+    G.node_start.assign(G.members.size() + 1, 0);
+    G.row_start.assign(G.members.size() + 1, 0);
+    G.dx_all.clear();
+    long long nv = 0;
+    int nodes = 0, rows = 0;
+    for (size_t m = 0; m < G.members.size(); ++m) {
+        const hlb_config& c = h->cfg[G.members[m]];
+        hlb::InstDev& I = G.inst[m];
+        std::vector<double> dx;
+        hlb::grid_widths(c.nx, c.Lx, c.stretch_A, dx);
+        I.f_off = nv;
+        I.node_off = nodes;
+        I.row_off = rows;
+        I.nx = c.nx;
+        I.ny = c.ny;
+        I.dx_off = (int)G.dx_all.size();
+        G.dx_all.insert(G.dx_all.end(), dx.begin(), dx.end());
+        const double dy = c.ny > 1 ? c.Ly / c.ny : 0.0;
+        I.inv_dy = c.ny > 1 ? 1.0 / dy : 0.0;
+        if (c.dt > 0) {
+            I.dt = c.dt;
+        } else {
+            double maxpx = 0, maxpy = 0;
+            for (double p : G.tx.p) maxpx = std::max(maxpx, std::fabs(p));
+            for (double p : G.ty.p) maxpy = std::max(maxpy, std::fabs(p));
+            double rate = maxpx / *std::min_element(dx.begin(), dx.end());
+            if (c.ny > 1) rate += maxpy / dy;
+            I.dt = c.cfl / rate;
+        }
+        I.inv_Kn = std::isinf(c.Kn) ? 0.0 : 1.0 / c.Kn;
+        I.ax = c.ax; I.ay = c.ay; I.az = c.az;
+        nv += (long long)c.nx * c.ny * G.V;
+        nodes += c.nx * c.ny;
+        rows += c.ny;
+        G.node_start[m + 1] = nodes;
+        G.row_start[m + 1] = rows;
+    }
+    G.nvalues = nv;
+    G.nnodes = nodes;
+    G.nrows = rows;
+
+    // tables
+    std::vector<double> K, p, T, rec;
+    K.insert(K.end(), G.tx.K.begin(), G.tx.K.end());
+    K.insert(K.end(), G.ty.K.begin(), G.ty.K.end());
+    K.insert(K.end(), G.tz.K.begin(), G.tz.K.end());
+    p.insert(p.end(), G.tx.p.begin(), G.tx.p.end());
+    p.insert(p.end(), G.ty.p.begin(), G.ty.p.end());
+    p.insert(p.end(), G.tz.p.begin(), G.tz.p.end());
+    T.insert(T.end(), G.tx.T.begin(), G.tx.T.end());
+    T.insert(T.end(), G.ty.T.begin(), G.ty.T.end());
+    T.insert(T.end(), G.tz.T.begin(), G.tz.T.end());
+    rec.insert(rec.end(), G.tx.ra.begin(), G.tx.ra.end());
+    rec.insert(rec.end(), G.tx.rb.begin(), G.tx.rb.end());
+    rec.insert(rec.end(), G.tx.rc.begin(), G.tx.rc.end());
+    rec.insert(rec.end(), G.tx.h0.begin(), G.tx.h0.end());
+    hlb_status s;
+    if ((s = upload_real(G.d_K, K, G.precision)) != HLB_OK) return s;
+    if ((s = upload_real(G.d_p, p, G.precision)) != HLB_OK) return s;
+    if ((s = upload(G.d_pd, p)) != HLB_OK) return s;
+    if ((s = upload_real(G.d_T, T, G.precision)) != HLB_OK) return s;
+    if ((s = upload(G.d_rec, rec)) != HLB_OK) return s;
+    if ((s = upload(G.d_dx, G.dx_all)) != HLB_OK) return s;
+    if ((s = upload(G.d_node_start, G.node_start)) != HLB_OK) return s;
+    if ((s = upload(G.d_row_start, G.row_start)) != HLB_OK) return s;
+    if ((s = upload(G.d_nw, std::vector<double>((size_t)G.nrows * 2, 0.0))) != HLB_OK) return s;
+    if ((s = upload(G.d_resid, std::vector<double>(G.members.size() * 2, 0.0))) != HLB_OK) return s;
+    if ((s = refresh_walls(h, G)) != HLB_OK) return s;
+
+    // state buffers
+    const size_t bytes = (size_t)G.nvalues * G.esize;
+    for (auto& b : G.buf) {
+        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HLB_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes for the state failed");
+        }
+        HLB_CUDA(cudaMemset(b.p, 0, bytes));
+    }
+    if (cudaMalloc(&G.d_mom.p, std::max<size_t>((size_t)G.nnodes * 6 * sizeof(double), 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HLB_ENOMEM, "cudaMalloc of moment scratch failed");
+    }
+    fill_dev(G);
+
+    // launch shape of the stage kernel
+    G.block = std::min(256, std::max(32, ((G.V + 31) / 32) * 32));
+    G.smem = hlb::stage_smem_bytes(G.dev, G.precision, G.block);
+    if (G.smem > 200 * 1024) return fail(HLB_EUNSUPPORTED, "velocity set too large for the stage kernel's shared memory");
+    HLB_CUDA(hlb::prepare_stage(G.precision, G.adv, G.smem));
+    int per_sm = 1, dev = 0, nsm = 1;
+    HLB_CUDA(cudaGetDevice(&dev));
+    HLB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    HLB_CUDA(hlb::stage_occupancy(G.precision, G.adv, G.block, G.smem, &per_sm));
+    G.grid = std::max(1, std::min(G.nnodes, nsm * std::max(1, per_sm)));
+    return HLB_OK;
+}
+
+// One RK-3 step of one group: three (wall, stage) pairs; buffer roles rotate.
+void enqueue_group_step(hlb_handle* h, Group& G) {
+    void* S = G.buf[G.cur].p;
+    void* X = G.buf[(G.cur + 1) % 3].p;
+    void* Y = G.buf[(G.cur + 2) % 3].p;
+    const void* ins[3] = {S, X, Y};
+    void* outs[3] = {X, Y, X};
+    for (int st = 0; st < 3; ++st) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+        if (h->time_kernels) {
+            cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
+            cudaEventRecord(e0, h->stream);
+        }
+        hlb::launch_wall(G.precision, G.adv, G.dev, ins[st], h->stream);
+        if (h->time_kernels) cudaEventRecord(e1, h->stream);
+        hlb::launch_stage(G.precision, G.adv, G.dev, ins[st], S, outs[st], st, G.grid, G.block, G.smem, h->stream);
+        if (h->time_kernels) {
+            cudaEventRecord(e2, h->stream);
+            h->timer.wall.push_back({e0, e1});
+            h->timer.stage.push_back({e1, e2});
+        }
+    }
+    G.prev = G.cur;
+    G.cur = (G.cur + 1) % 3;
+}
+
+void enqueue_step(hlb_handle* h) {
+    for (auto& G : h->groups) enqueue_group_step(h, *G);
+}
+
+hlb_status collect_timer(hlb_handle* h) {
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    // events shared between the wall and stage lists are destroyed once
+    std::vector<cudaEvent_t> owned;
+    for (auto& pr : h->timer.wall) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, pr.first, pr.second);
+        h->wall_ms += ms;
+        h->wall_n += 1;
+        owned.push_back(pr.first);
+    }
+    for (auto& pr : h->timer.stage) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, pr.first, pr.second);
+        h->stage_ms += ms;
+        h->stage_n += 1;
+        owned.push_back(pr.first);
+        owned.push_back(pr.second);
+    }
+    for (auto e : owned) cudaEventDestroy(e);
+    h->timer.wall.clear();
+    h->timer.stage.clear();
+    return HLB_OK;
+}
+
+hlb_status build_graph(hlb_handle* h) {
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    const int per = std::max(1, 10 / (int)h->groups.size());
+    h->graph_steps = 3 * per;
+    cudaGraph_t graph = nullptr;
+    HLB_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < h->graph_steps; ++s) enqueue_step(h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return fail(HLB_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    // capture does not execute: restore the buffer phase
+    for (auto& G : h->groups) { G->cur = (G->cur + 3 * 100 - h->graph_steps) % 3; }
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(HLB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return HLB_OK;
+}
+
+Group* group_of(hlb_handle* h, int inst, int* local) {
+    Group* G = h->groups[h->inst_group[inst]].get();
+    if (local) *local = h->inst_local[inst];
+    return G;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hlb_last_error(void) { return g_last_error.c_str(); }
+const char* hlb_version(void) { return "libhlb 0.1 (sm_103a)"; }
+
+hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_handle** out) {
+    g_last_error.clear();
+    if (!out) return fail(HLB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg || ninst < 1) return fail(HLB_EINVAL, "cfg is NULL or ninst < 1");
+    for (int i = 0; i < ninst; ++i) {
+        std::string e = check_config(cfg[i], i);
+        if (!e.empty()) return fail(HLB_EINVAL, e);
+        if (cfg[i].precision != cfg[0].precision) return fail(HLB_EINVAL, "all instances must share precision");
+    }
+    std::unique_ptr<hlb_handle> h(new hlb_handle());
+    h->cfg.assign(cfg, cfg + ninst);
+    h->precision = cfg[0].precision;
+    h->esize = h->precision == HLB_FP64 ? 8 : 4;
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        HLB_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    // group by velocity model
+    std::map<std::tuple<int, int, int, int, int, int, int>, int> key2g;
+    h->inst_group.resize(ninst);
+    h->inst_local.resize(ninst);
+    for (int i = 0; i < ninst; ++i) {
+        const hlb_config& c = cfg[i];
+        auto key = std::make_tuple(c.Qx, c.Qy, c.Qz, c.Nx_eq < 0 ? c.Qx - 1 : c.Nx_eq,
+                                   c.Qy ? (c.Ny_eq < 0 ? c.Qy - 1 : c.Ny_eq) : 0,
+                                   c.Qz ? (c.Nz_eq < 0 ? c.Qz - 1 : c.Nz_eq) : 0, c.advection);
+        auto it = key2g.find(key);
+        int gi;
+        if (it == key2g.end()) {
+            gi = (int)h->groups.size();
+            key2g[key] = gi;
+            h->groups.emplace_back(new Group());
+        } else {
+            gi = it->second;
+        }
+        h->inst_group[i] = gi;
+        h->inst_local[i] = (int)h->groups[gi]->members.size();
+        h->groups[gi]->members.push_back(i);
+    }
+    for (auto& G : h->groups) {
+        hlb_status s = build_group(h.get(), *G);
+        if (s != HLB_OK) return s;
+    }
+    h->inst_node_off.resize(ninst);
+    h->inst_value_off.resize(ninst);
+    long long nodes = 0, values = 0;
+    for (int i = 0; i < ninst; ++i) {
+        h->inst_node_off[i] = nodes;
+        h->inst_value_off[i] = values;
+        const Group* G = h->groups[h->inst_group[i]].get();
+        nodes += (long long)cfg[i].nx * cfg[i].ny;
+        values += (long long)cfg[i].nx * cfg[i].ny * G->V;
+    }
+    h->total_nodes = nodes;
+    h->total_values = values;
+    *out = h.release();
+    return HLB_OK;
+}
+
+void hlb_destroy(hlb_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    collect_timer(h);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+hlb_status hlb_set_walls(hlb_handle* h, int inst, double T_left, double T_right) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (inst < -1 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    if (!(T_left > 0) || !(T_right > 0) || !std::isfinite(T_left) || !std::isfinite(T_right))
+        return fail(HLB_EINVAL, "wall temperatures must be finite and > 0");
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < (int)h->cfg.size(); ++i)
+        if (inst < 0 || i == inst) { h->cfg[i].T_left = T_left; h->cfg[i].T_right = T_right; }
+    for (auto& G : h->groups) {
+        hlb_status s = refresh_walls(h, *G);
+        if (s != HLB_OK) return s;
+        fill_dev(*G);
+    }
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    return HLB_OK;
+}
+
+hlb_status hlb_set_force(hlb_handle* h, int inst, double ax, double ay, double az) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (inst < -1 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    if (!std::isfinite(ax) || !std::isfinite(ay) || !std::isfinite(az)) return fail(HLB_EINVAL, "acceleration must be finite");
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < (int)h->cfg.size(); ++i) {
+        if (inst >= 0 && i != inst) continue;
+        h->cfg[i].ax = ax; h->cfg[i].ay = ay; h->cfg[i].az = az;
+        int l;
+        Group* G = group_of(h, i, &l);
+        G->inst[l].ax = ax; G->inst[l].ay = ay; G->inst[l].az = az;
+    }
+    for (auto& G : h->groups) {
+        hlb_status s = upload_inst(*G);
+        if (s != HLB_OK) return s;
+        fill_dev(*G);
+    }
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    return HLB_OK;
+}
+
+hlb_status hlb_set_Kn(hlb_handle* h, int inst, double Kn) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (inst < -1 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    if (!(Kn > 0)) return fail(HLB_EINVAL, "Kn must be > 0 (+INFINITY: collisionless)");
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < (int)h->cfg.size(); ++i) {
+        if (inst >= 0 && i != inst) continue;
+        h->cfg[i].Kn = Kn;
+        int l;
+        Group* G = group_of(h, i, &l);
+        G->inst[l].inv_Kn = std::isinf(Kn) ? 0.0 : 1.0 / Kn;
+    }
+    for (auto& G : h->groups) {
+        hlb_status s = upload_inst(*G);
+        if (s != HLB_OK) return s;
+        fill_dev(*G);
+    }
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    return HLB_OK;
+}
+
+hlb_status hlb_init_equilibrium(hlb_handle* h, double n, double ux, double uy, double T) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (!(n > 0) || !(T > 0) || !std::isfinite(n) || !std::isfinite(T) || !std::isfinite(ux) || !std::isfinite(uy))
+        return fail(HLB_EINVAL, "need finite n > 0, T > 0, ux, uy");
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        std::vector<double> gx(G.QX2), gy(G.VY), gz(G.VZ), gv(G.V);
+        hlb::axis_equilibrium(G.tx, ux, T, gx.data());
+        hlb::axis_equilibrium(G.ty, uy, T, gy.data());
+        hlb::axis_equilibrium(G.tz, 0.0, T, gz.data());
+        for (int k = 0; k < G.VZ; ++k)
+            for (int j = 0; j < G.VY; ++j)
+                for (int i = 0; i < G.QX2; ++i) gv[(k * G.VY + j) * G.QX2 + i] = n * gx[i] * gy[j] * gz[k];
+        DevBuf tmp;
+        hlb_status s = upload_real(tmp, gv, G.precision);
+        if (s != HLB_OK) return s;
+        hlb::launch_broadcast(G.precision, G.buf[G.cur].p, tmp.p, G.nvalues, G.V, h->stream);
+        HLB_CUDA(cudaGetLastError());
+        HLB_CUDA(cudaStreamSynchronize(h->stream));   // tmp is freed on return
+    }
+    h->have_residual = false;
+    return HLB_OK;
+}
+
+hlb_status hlb_step(hlb_handle* h, long nsteps) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(HLB_EINVAL, "nsteps < 0");
+    long left = nsteps;
+    while (left > 0) {
+        const bool phase0 = std::all_of(h->groups.begin(), h->groups.end(), [](const std::unique_ptr<Group>& G) { return G->cur == 0; });
+        if (h->use_graphs && !h->time_kernels && phase0) {
+            if (!h->graph) {
+                hlb_status s = build_graph(h);
+                if (s != HLB_OK) return s;
+            }
+            if (left >= h->graph_steps) {
+                HLB_CUDA(cudaGraphLaunch(h->graph, h->stream));
+                for (auto& G : h->groups) { G->prev = (G->cur + 2) % 3; }   // cur returns to 0
+                left -= h->graph_steps;
+                h->nsteps += h->graph_steps;
+                continue;
+            }
+        }
+        enqueue_step(h);
+        HLB_CUDA(cudaGetLastError());
+        left -= 1;
+        h->nsteps += 1;
+    }
+    if (nsteps > 0) h->have_residual = true;
+    HLB_CUDA(cudaGetLastError());
+    return HLB_OK;
+}
+
+hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        double* m = (double*)G.d_mom.p;
+        hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + G.nnodes, m + 4LL * G.nnodes,
+                            m + 5LL * G.nnodes, 0, h->stream);
+        HLB_CUDA(cudaGetLastError());
+        for (size_t k = 0; k < G.members.size(); ++k) {
+            const int i = G.members[k];
+            const long long go = h->inst_node_off[i];
+            const long long lo = G.node_start[k];
+            const long long cnt = G.node_start[k + 1] - G.node_start[k];
+            if (n_dev) HLB_CUDA(cudaMemcpyAsync(n_dev + go, m + lo, cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+            if (u_dev) HLB_CUDA(cudaMemcpyAsync(u_dev + 3 * go, m + G.nnodes + 3 * lo, 3 * cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+            if (T_dev) HLB_CUDA(cudaMemcpyAsync(T_dev + go, m + 4LL * G.nnodes + lo, cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+            if (q_dev) HLB_CUDA(cudaMemcpyAsync(q_dev + go, m + 5LL * G.nnodes + lo, cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    return HLB_OK;
+}
+
+hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    bool finite = true;
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        double* m = (double*)G.d_mom.p;
+        hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + G.nnodes, m + 4LL * G.nnodes,
+                            m + 5LL * G.nnodes, 0, h->stream);
+        HLB_CUDA(cudaGetLastError());
+        std::vector<double> host((size_t)G.nnodes * 6);
+        HLB_CUDA(cudaMemcpyAsync(host.data(), m, host.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+        HLB_CUDA(cudaStreamSynchronize(h->stream));
+        const double* hn = host.data();
+        const double* hu = hn + G.nnodes;
+        const double* hT = hn + 4LL * G.nnodes;
+        const double* hq = hn + 5LL * G.nnodes;
+        for (size_t k = 0; k < G.members.size(); ++k) {
+            const long long go = h->inst_node_off[G.members[k]];
+            for (int j = G.node_start[k]; j < G.node_start[k + 1]; ++j) {
+                const long long o = go + (j - G.node_start[k]);
+                if (n) n[o] = hn[j];
+                if (u) { u[3 * o] = hu[3 * j]; u[3 * o + 1] = hu[3 * j + 1]; u[3 * o + 2] = hu[3 * j + 2]; }
+                if (T) T[o] = hT[j];
+                if (q) q[o] = hq[j];
+                if (!std::isfinite(hn[j]) || !std::isfinite(hT[j])) finite = false;
+            }
+        }
+    }
+    if (!finite) return fail(HLB_ENONFINITE, "non-finite moments in the state");
+    return HLB_OK;
+}
+
+hlb_status hlb_sizes(const hlb_handle* h, long long* nodes, long long* values, long long* bytes) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (nodes) *nodes = h->total_nodes;
+    if (values) *values = h->total_values;
+    if (bytes) *bytes = h->total_values * (long long)h->esize;
+    return HLB_OK;
+}
+
+hlb_status hlb_get_dt(const hlb_handle* h, int inst, double* dt) {
+    if (!h || !dt) return fail(HLB_EINVAL, "handle or dt is NULL");
+    if (inst < 0 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    const Group* G = h->groups[h->inst_group[inst]].get();
+    *dt = G->inst[h->inst_local[inst]].dt;
+    return HLB_OK;
+}
+
+hlb_status hlb_get_nsteps(const hlb_handle* h, long long* nsteps) {
+    if (!h || !nsteps) return fail(HLB_EINVAL, "handle or nsteps is NULL");
+    *nsteps = h->nsteps;
+    return HLB_OK;
+}
+
+static hlb_status state_copy(hlb_handle* h, void* ext, size_t bytes, bool to_ext, cudaMemcpyKind kind, bool sync) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (!ext) return fail(HLB_EINVAL, "buffer is NULL");
+    if (bytes != (size_t)(h->total_values * (long long)h->esize))
+        return fail(HLB_EINVAL, "state buffer must be exactly " + std::to_string(h->total_values * (long long)h->esize) + " bytes");
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        char* dev = (char*)G.buf[G.cur].p;
+        for (size_t k = 0; k < G.members.size(); ++k) {
+            const int i = G.members[k];
+            const size_t off_ext = (size_t)h->inst_value_off[i] * G.esize;
+            const size_t off_dev = (size_t)G.inst[k].f_off * G.esize;
+            const size_t len = (size_t)(G.node_start[k + 1] - G.node_start[k]) * G.V * G.esize;
+            if (to_ext) HLB_CUDA(cudaMemcpyAsync((char*)ext + off_ext, dev + off_dev, len, kind, h->stream));
+            else HLB_CUDA(cudaMemcpyAsync(dev + off_dev, (const char*)ext + off_ext, len, kind, h->stream));
+        }
+    }
+    if (sync) HLB_CUDA(cudaStreamSynchronize(h->stream));
+    if (!to_ext) h->have_residual = false;
+    return HLB_OK;
+}
+
+hlb_status hlb_get_state(hlb_handle* h, void* host_f, size_t bytes) {
+    return state_copy(h, host_f, bytes, true, cudaMemcpyDeviceToHost, true);
+}
+hlb_status hlb_set_state(hlb_handle* h, const void* host_f, size_t bytes) {
+    return state_copy(h, const_cast<void*>(host_f), bytes, false, cudaMemcpyHostToDevice, true);
+}
+hlb_status hlb_get_state_dev(hlb_handle* h, void* f_dev, size_t bytes) {
+    return state_copy(h, f_dev, bytes, true, cudaMemcpyDeviceToDevice, false);
+}
+hlb_status hlb_set_state_dev(hlb_handle* h, const void* f_dev, size_t bytes) {
+    return state_copy(h, const_cast<void*>(f_dev), bytes, false, cudaMemcpyDeviceToDevice, false);
+}
+
+hlb_status hlb_diag(hlb_handle* h, double* total_N, double* residual) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    const int ninst = (int)h->cfg.size();
+    if (total_N) {
+        std::vector<double> n((size_t)h->total_nodes);
+        hlb_status s = hlb_moments(h, n.data(), nullptr, nullptr, nullptr);
+        if (s != HLB_OK && s != HLB_ENONFINITE) return s;
+        for (int i = 0; i < ninst; ++i) {
+            const hlb_config& c = h->cfg[i];
+            const Group* G = h->groups[h->inst_group[i]].get();
+            const int l = h->inst_local[i];
+            const double dy = c.ny > 1 ? c.Ly / c.ny : 1.0;
+            double acc = 0.0;
+            for (int y = 0; y < c.ny; ++y)
+                for (int x = 0; x < c.nx; ++x)
+                    acc += n[h->inst_node_off[i] + (long long)y * c.nx + x] * G->dx_all[G->inst[l].dx_off + x];
+            total_N[i] = acc * dy;
+        }
+    }
+    if (residual) {
+        for (int i = 0; i < ninst; ++i) residual[i] = 0.0;
+        if (h->have_residual) {
+            for (auto& Gp : h->groups) {
+                Group& G = *Gp;
+                if (G.prev < 0) continue;
+                HLB_CUDA(cudaMemsetAsync(G.d_resid.p, 0, G.members.size() * 2 * sizeof(double), h->stream));
+                hlb::launch_residual(G.precision, G.dev, G.buf[G.prev].p, G.buf[G.cur].p, (double*)G.d_resid.p, h->stream);
+                HLB_CUDA(cudaGetLastError());
+                std::vector<double> r(G.members.size() * 2);
+                HLB_CUDA(cudaMemcpyAsync(r.data(), G.d_resid.p, r.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+                HLB_CUDA(cudaStreamSynchronize(h->stream));
+                for (size_t k = 0; k < G.members.size(); ++k)
+                    residual[G.members[k]] = r[2 * k + 1] > 0 ? r[2 * k] / (G.inst[k].dt * r[2 * k + 1]) : 0.0;
+            }
+        }
+    }
+    return HLB_OK;
+}
+
+hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, double* pz, double* wx,
+                      double* wy, double* wz, double* Kx, double* Ky, double* Kz, double* dx) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (inst < 0 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    const Group* G = h->groups[h->inst_group[inst]].get();
+    auto cp = [](const std::vector<double>& v, double* o) { if (o) std::copy(v.begin(), v.end(), o); };
+    cp(G->tx.p, px); cp(G->ty.p, py); cp(G->tz.p, pz);
+    cp(G->tx.w, wx); cp(G->ty.w, wy); cp(G->tz.w, wz);
+    cp(G->tx.K, Kx); cp(G->ty.K, Ky); cp(G->tz.K, Kz);
+    if (dx) {
+        const hlb::InstDev& I = G->inst[h->inst_local[inst]];
+        std::copy(G->dx_all.begin() + I.dx_off, G->dx_all.begin() + I.dx_off + I.nx, dx);
+    }
+    return HLB_OK;
+}
+
+hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K) {
+    hlb::AxisTables ax;
+    std::string e = half ? hlb::build_half_axis(Q, Q - 1, ax) : hlb::build_full_axis(Q, Q - 1, ax);
+    if (!e.empty()) return fail(HLB_EINVAL, e);
+    if (p) std::copy(ax.p.begin(), ax.p.end(), p);
+    if (w) std::copy(ax.w.begin(), ax.w.end(), w);
+    if (K) std::copy(ax.K.begin(), ax.K.end(), K);
+    return HLB_OK;
+}
+
+hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g) {
+    if (!g) return fail(HLB_EINVAL, "g is NULL");
+    if (!(T > 0) || !std::isfinite(u) || !std::isfinite(T)) return fail(HLB_EINVAL, "need finite u and T > 0");
+    hlb::AxisTables ax;
+    std::string e = hlb::build_half_axis(Qx, Nx_eq < 0 ? Qx - 1 : Nx_eq, ax);
+    if (!e.empty()) return fail(HLB_EINVAL, e);
+    hlb::axis_equilibrium(ax, u, T, g);
+    return HLB_OK;
+}
+
+hlb_status hlb_set_options(hlb_handle* h, int use_graphs, int time_kernels) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    h->use_graphs = use_graphs != 0;
+    h->time_kernels = time_kernels != 0;
+    return HLB_OK;
+}
+
+hlb_status hlb_kernel_times(hlb_handle* h, double* stage_ms, long long* stage_launches, double* wall_ms,
+                            long long* wall_launches, int reset) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    hlb_status s = collect_timer(h);
+    if (s != HLB_OK) return s;
+    if (stage_ms) *stage_ms = h->stage_ms;
+    if (stage_launches) *stage_launches = h->stage_n;
+    if (wall_ms) *wall_ms = h->wall_ms;
+    if (wall_launches) *wall_launches = h->wall_n;
+    if (reset) { h->stage_ms = h->wall_ms = 0; h->stage_n = h->wall_n = 0; }
+    return HLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations shared by the host tables, the API and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace hlb {
+
+// Mirrors of the public enums of hlb.h, usable in device code.
+constexpr int HLB_UPWIND2_ = 0, HLB_WENO5_ = 1;
+constexpr int HLB_FP64_ = 0, HLB_FP32_ = 1;
+
+constexpr int kMaxQ = 32;          // largest quadrature order per axis
+constexpr int kMaxN = kMaxQ;       // largest equilibrium order + 1
+
+// One momentum axis of the direct-product velocity set (App. A).
+struct AxisTables {
+    int Q = 0;                       // quadrature order (per half for the half-range axis)
+    bool half = false;               // half-range Hermite (p_x) or full-range Gauss-Hermite
+    int count = 1;                   // velocities on the axis: 2Q, Q, or 1 if absent
+    int N = 0;                       // equilibrium order
+    std::vector<double> p, w;        // [count]
+    std::vector<double> K;           // [count * count], row-major K[k][k']
+    // Equilibrium tables.  Half-range: T[k][l] = w_k h_l(z_k) (k < Q, l <= N),
+    // recurrence h_{l+1} = (a_l z + b_l) h_l + c_l h_{l-1}, h0[l] = h_l(0).
+    // Full-range: T[j][l] = w_j He_l(z_j) / l!.
+    std::vector<double> T;
+    std::vector<double> ra, rb, rc, h0;
+};
+
+// Build the tables of a half-range (p_x) or full-range (p_y, p_z) axis.
+// Returns "" on success or an error message.
+std::string build_half_axis(int Q, int N, AxisTables& out);
+std::string build_full_axis(int Q, int N, AxisTables& out);
+void absent_axis(AxisTables& out);
+
+// g(u, T) on the axis (count values), FP64, by the same recurrences the
+// kernels use per node.
+void axis_equilibrium(const AxisTables& ax, double u, double T, double* g);
+
+// x-cell widths of the uniform (A = 0) or tanh-stretched grid.
+void grid_widths(int nx, double L, double A, std::vector<double>& dx);
+
+// ---------------------------------------------------------------------------
+// Device-side descriptors (passed by value to kernels).
+// ---------------------------------------------------------------------------
+struct InstDev {
+    long long f_off;     // first value of the instance in the state arrays
+    int node_off;        // first node of the instance (flattened over the group)
+    int row_off;         // first (instance, y) row
+    int nx, ny;
+    int dx_off;          // offset into the concatenated x-cell widths
+    double inv_dy;       // 1/dy (0 for a 1D instance)
+    double dt;
+    double inv_Kn;       // 1/Kn (0: collisionless)
+    double ax, ay, az;
+    double den_left, den_right;   // sum over emitted populations of p_x g^w
+    int gw_off;          // offset of [2][V] wall Maxwellians (values of R)
+};
+
+struct GroupDev {
+    int V, QX2, VY, VZ, Qx, Nx, Ny, Nz, Qy, Qz, D;
+    int ninst, nnodes, nrows;
+    const InstDev* inst;
+    const int* node_start;   // [ninst + 1]
+    const int* row_start;    // [ninst + 1]
+    const void* K;           // R: Kx [QX2^2], Ky [VY^2], Kz [VZ^2] concatenated
+    const void* p;           // R: px [QX2], py [VY], pz [VZ]
+    const double* pd;        // FP64 copies of px, py, pz
+    const void* Tt;          // R: Tx [Qx (Nx+1)], Ty [VY (Ny+1)], Tz [VZ (Nz+1)]
+    const double* rec;       // FP64: ra[Nx], rb[Nx], rc[Nx], h0[Nx+1]
+    const double* dx;        // FP64 x-cell widths, concatenated per instance
+    const void* gw;          // R: wall Maxwellians
+    double* nw;              // FP64 [nrows][2] emitted densities
+};
+
+}  // namespace hlb
+
+// Launchers (hlb_kernels.cu).
+#include <cuda_runtime.h>
+namespace hlb {
+size_t stage_smem_bytes(const GroupDev& g, int precision, int block);
+cudaError_t prepare_stage(int precision, int adv, size_t smem);
+cudaError_t stage_occupancy(int precision, int adv, int block, size_t smem, int* blocks_per_sm);
+void launch_stage(int precision, int adv, const GroupDev& g, const void* fs, const void* fn, void* fo,
+                  int stage, int grid, int block, size_t smem, cudaStream_t st);
+void launch_wall(int precision, int adv, const GroupDev& g, const void* fs, cudaStream_t st);
+void launch_broadcast(int precision, void* f, const void* gvec, long long nvalues, int V, cudaStream_t st);
+void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
+                    double* q, int node_base, cudaStream_t st);
+void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out,
+                     cudaStream_t st);
+}  // namespace hlb

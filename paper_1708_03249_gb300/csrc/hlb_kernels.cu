@@ -1,0 +1,597 @@
+// Device kernels of libhlb (sm_103a).
+//
+// Per RK-3 stage (Eq. "eq:rk3") two kernels run:
+//   wall_kernel   one CTA per (instance, y-row): incident fluxes at both wall
+//                 faces from the quadratically extrapolated ghosts (Sec.
+//                 IV.C.3), summed in FP64, give the emitted densities
+//                 n_w = -sum_inc F / sum_emit p_x g^w (Eq. "eq:nplus_def").
+//   stage_kernel  fused per node: moments (Eq. "eq:fmoms") by a block
+//                 reduction, the equilibrium factors g_x, g_y, g_z (FP64
+//                 recurrences, App. A), the force term sum_a a_a K_a f
+//                 (Eqs. "eq:hh_Kk_hh", "eq:H_Kk"), BGK with tau = Kn/n,
+//                 WENO-5 / upwind2 fluxes along x (walls: Eq.
+//                 "eq:weno_populate" ghosts) and y (periodic), and the RK-3
+//                 combination; writes the stage output.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "hlb_internal.h"
+
+namespace hlb {
+
+namespace {
+
+constexpr double kInvSqrt2Pi = 0.39894228040143267793994605993438;
+constexpr double kSqrt2Pi = 2.5066282746310005024157652848110;
+
+template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
+template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+
+// WENO-5 face value per unit velocity for a positive velocity: (a..e) are the
+// values at cells i-2..i+2 of face i+1/2 (Sec. IV.C.2).  No epsilon: the
+// weights are delta_q/sigma_q^2 normalised, or, if any sigma_q vanishes,
+// delta_q over the vanishing set (Tab. "weno").  The sigmas are formed from
+// the stencil values divided by their largest magnitude; the weights are
+// invariant under that scaling and it keeps sigma^2 inside FP32's range.
+template <typename R>
+__device__ __forceinline__ R weno5_face(R a, R b, R c, R d, R e) {
+    const R F1 = (R(2) * a - R(7) * b + R(11) * c) * R(1.0 / 6.0);
+    const R F2 = (-b + R(5) * c + R(2) * d) * R(1.0 / 6.0);
+    const R F3 = (R(2) * c + R(5) * d - e) * R(1.0 / 6.0);
+    const R m = rmax(rmax(rmax(rabs(a), rabs(b)), rmax(rabs(c), rabs(d))), rabs(e));
+    if (m == R(0)) return R(0);
+    const R r = R(1) / m;
+    const R A = a * r, B = b * r, C = c * r, Dd = d * r, E = e * r;
+    const R t1 = A - R(2) * B + C, t2 = A - R(4) * B + R(3) * C;
+    const R t3 = B - R(2) * C + Dd, t4 = B - Dd;
+    const R t5 = C - R(2) * Dd + E, t6 = R(3) * C - R(4) * Dd + E;
+    const R s1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+    const R s2 = R(13.0 / 12.0) * t3 * t3 + R(0.25) * t4 * t4;
+    const R s3 = R(13.0 / 12.0) * t5 * t5 + R(0.25) * t6 * t6;
+    R w1, w2, w3;
+    if (s1 == R(0) || s2 == R(0) || s3 == R(0)) {
+        w1 = s1 == R(0) ? R(0.1) : R(0);
+        w2 = s2 == R(0) ? R(0.6) : R(0);
+        w3 = s3 == R(0) ? R(0.3) : R(0);
+    } else {
+        w1 = R(0.1) / (s1 * s1);
+        w2 = R(0.6) / (s2 * s2);
+        w3 = R(0.3) / (s3 * s3);
+    }
+    return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);
+}
+
+template <typename R>
+__device__ __forceinline__ R upwind2_face(R b, R c) { return R(1.5) * c - R(0.5) * b; }
+
+__device__ __forceinline__ int find_slot(const int* start, int n, int key) {
+    int lo = 0, hi = n;            // start[lo] <= key < start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(start + mid) <= key) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Shared-memory layout of the stage kernel (sizes in elements).
+struct SmemLayout {
+    int nK, nP, nT, nG;
+    size_t offK, offP, offT, offF, offG;      // in R elements
+    size_t offD;                              // in bytes (8-aligned)
+    int nRec, nCoef;
+    size_t bytes;
+};
+
+template <typename R>
+__host__ __device__ inline SmemLayout smem_layout(const GroupDev& g, int nwarps) {
+    SmemLayout L;
+    L.nK = g.QX2 * g.QX2 + g.VY * g.VY + g.VZ * g.VZ;
+    L.nP = g.QX2 + g.VY + g.VZ;
+    L.nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
+    L.nG = g.QX2 + g.VY + g.VZ;
+    L.offK = 0;
+    L.offP = L.offK + L.nK;
+    L.offT = L.offP + L.nP;
+    L.offF = L.offT + L.nT;
+    L.offG = L.offF + g.V;
+    size_t rbytes = (L.offG + L.nG) * sizeof(R);
+    L.offD = (rbytes + 15) & ~size_t(15);
+    L.nRec = 3 * g.Nx + (g.Nx + 1);
+    L.nCoef = 2 * (g.Nx + 1) + (g.Ny + 1) + (g.Nz + 1);
+    // doubles: rec, coef, 8 scalars, 5 * nwarps reduction slots
+    L.bytes = L.offD + sizeof(double) * (L.nRec + L.nCoef + 8 + 5 * nwarps);
+    return L;
+}
+
+// Per-node equilibrium coefficients in FP64.  Thread role r:
+//   r = 0, 1: half-range G_l^{+-} (l <= Nx) by the recurrence in the
+//             orthonormal basis (see hlb_tables.cpp);
+//   r = 2:    full-range G_l along p_y;  r = 3: along p_z.
+__device__ void node_coefficients(const GroupDev& g, int r, double ux, double uy, double uz,
+                                  double T, const double* rec, double* coef) {
+    const int Nx = g.Nx;
+    if (r < 2) {
+        const double* ra = rec;
+        const double* rb = rec + Nx;
+        const double* rc = rec + 2 * Nx;
+        const double* h0 = rec + 3 * Nx;
+        double* G = coef + r * (Nx + 1);
+        const double us = r ? -ux : ux;
+        const double g0 = exp(-ux * ux / (2.0 * T)) / (kSqrt2Pi * sqrt(T));
+        G[0] = h0[0] * 0.5 * (1.0 + erf(us / sqrt(2.0 * T)));
+        double S = 0.0;
+        double gm1 = 0.0;
+        for (int l = 0; l < Nx; ++l) {
+            const double ig = (l ? gm1 / ra[l - 1] : 0.0) - kInvSqrt2Pi * h0[l] * S;
+            const double pg = us * G[l] + T * (g0 * h0[l] + ig);
+            G[l + 1] = ra[l] * pg + rb[l] * G[l] + rc[l] * gm1;
+            S += h0[l] * G[l];
+            gm1 = G[l];
+        }
+    } else {
+        const int N = r == 2 ? g.Ny : g.Nz;
+        const double u = r == 2 ? uy : uz;
+        double* G = coef + 2 * (Nx + 1) + (r == 2 ? 0 : g.Ny + 1);
+        G[0] = 1.0;
+        if (N >= 1) G[1] = u;
+        for (int l = 1; l < N; ++l) G[l + 1] = u * G[l] + l * (T - 1.0) * G[l - 1];
+    }
+}
+
+// Value of velocity v at x-position pos of a row (ghost rules at the walls).
+template <typename R>
+__device__ __forceinline__ R x_value(const R* __restrict__ frow, int pos, int nx, int V, int v,
+                                     bool px_pos, R nwl_g, R nwr_g) {
+    if (pos >= 0 && pos < nx) return frow[(size_t)pos * V + v];
+    if (pos < 0) {
+        if (px_pos) return nwl_g;                        // emitted: n_w g^w (3 ghosts)
+        const R f0 = frow[v], f1 = frow[(size_t)V + v], f2 = frow[2 * (size_t)V + v];
+        if (pos == -1) return R(3) * f0 - R(3) * f1 + f2;            // paper's cell 0
+        return R(6) * f0 - R(8) * f1 + R(3) * f2;                     // paper's cell -1
+    }
+    if (!px_pos) return nwr_g;
+    const R f0 = frow[(size_t)(nx - 1) * V + v], f1 = frow[(size_t)(nx - 2) * V + v],
+            f2 = frow[(size_t)(nx - 3) * V + v];
+    if (pos == nx) return R(3) * f0 - R(3) * f1 + f2;
+    return R(6) * f0 - R(8) * f1 + R(3) * f2;
+}
+
+// Fluxes at the faces x+1/2 and x-1/2 (per unit velocity) from a 6-cell
+// window; w[] holds cells x-3..x+2 for v > 0 and x-2..x+3 for v < 0.
+template <typename R, int ADV>
+__device__ __forceinline__ void face_pair(const R* w, bool pos, R& Fp, R& Fm) {
+    if (ADV == HLB_WENO5_) {
+        if (pos) {
+            Fp = weno5_face(w[1], w[2], w[3], w[4], w[5]);
+            Fm = weno5_face(w[0], w[1], w[2], w[3], w[4]);
+        } else {
+            Fp = weno5_face(w[5], w[4], w[3], w[2], w[1]);
+            Fm = weno5_face(w[4], w[3], w[2], w[1], w[0]);
+        }
+    } else {
+        if (pos) {
+            Fp = upwind2_face(w[2], w[3]);
+            Fm = upwind2_face(w[1], w[2]);
+        } else {
+            Fp = upwind2_face(w[4], w[3]);
+            Fm = upwind2_face(w[3], w[2]);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// stage kernel
+// ---------------------------------------------------------------------------
+template <typename R, int ADV>
+__global__ void __launch_bounds__(256)
+stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ fn,
+             R* __restrict__ fo, int stage) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nwarps = blockDim.x >> 5;
+    const SmemLayout L = smem_layout<R>(g, nwarps);
+    R* sR = reinterpret_cast<R*>(smem_raw);
+    R* sK = sR + L.offK;
+    R* sP = sR + L.offP;
+    R* sT = sR + L.offT;
+    R* sF = sR + L.offF;
+    R* sG = sR + L.offG;
+    double* sD = reinterpret_cast<double*>(smem_raw + L.offD);
+    double* sRec = sD;
+    double* sCoef = sRec + L.nRec;
+    double* sScal = sCoef + L.nCoef;
+    double* sRed = sScal + 8;
+
+    const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const R* gK = static_cast<const R*>(g.K);
+    const R* gP = static_cast<const R*>(g.p);
+    const R* gT = static_cast<const R*>(g.Tt);
+    for (int i = tid; i < L.nK; i += bs) sK[i] = gK[i];
+    for (int i = tid; i < L.nP; i += bs) sP[i] = gP[i];
+    for (int i = tid; i < L.nT; i += bs) sT[i] = gT[i];
+    for (int i = tid; i < L.nRec; i += bs) sRec[i] = g.rec[i];
+    __syncthreads();
+
+    const int V = g.V, QX2 = g.QX2, VY = g.VY, VZ = g.VZ, Qx = g.Qx;
+    const R* sKx = sK;
+    const R* sKy = sK + QX2 * QX2;
+    const R* sKz = sKy + VY * VY;
+    const R* sPx = sP;
+    const R* sPy = sP + QX2;
+    const R* sPz = sPy + VY;
+    const R* sTx = sT;
+    const R* sTy = sT + Qx * (g.Nx + 1);
+    const R* sTz = sTy + VY * (g.Ny + 1);
+    const R* gw = static_cast<const R*>(g.gw);
+
+    for (int node = blockIdx.x; node < g.nnodes; node += gridDim.x) {
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const InstDev I = g.inst[ii];
+        const int local = node - I.node_off;
+        const int nx = I.nx;
+        const int y = local / nx, x = local - y * nx;
+        const size_t row_off = (size_t)I.f_off + (size_t)y * nx * V;
+        const R* frow = fs + row_off;
+
+        // 1. node values and moment partial sums
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+        for (int v = tid; v < V; v += bs) {
+            const R val = frow[(size_t)x * V + v];
+            sF[v] = val;
+            const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
+            const R px = sPx[ix], py = sPy[jy], pz = sPz[kz];
+            a0 += val;
+            a1 += px * val;
+            a2 += py * val;
+            a3 += pz * val;
+            a4 += (px * px + py * py + pz * pz) * val;
+        }
+        a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
+        if (lane == 0) {
+            sRed[warp * 5 + 0] = a0; sRed[warp * 5 + 1] = a1; sRed[warp * 5 + 2] = a2;
+            sRed[warp * 5 + 3] = a3; sRed[warp * 5 + 4] = a4;
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double m[5] = {0, 0, 0, 0, 0};
+            for (int w = 0; w < nwarps; ++w)
+                for (int k = 0; k < 5; ++k) m[k] += sRed[w * 5 + k];
+            const double n = m[0];
+            const double ux = m[1] / n, uy = m[2] / n, uz = m[3] / n;
+            const double T = (m[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
+            if (tid == 0) {
+                sScal[0] = n;
+                sScal[1] = n * I.inv_Kn;     // 1/tau
+            }
+            node_coefficients(g, tid, ux, uy, uz, T, sRec, sCoef);
+        }
+        __syncthreads();
+        // 2. equilibrium factors g_x (times n), g_y, g_z
+        {
+            const int nf = QX2 + VY + VZ;
+            for (int t = tid; t < nf; t += bs) {
+                double acc = 0.0;
+                if (t < QX2) {
+                    const int k = t % Qx, sg = t / Qx;
+                    const double* G = sCoef + sg * (g.Nx + 1);
+                    for (int l = 0; l <= g.Nx; ++l) acc += (double)sTx[k * (g.Nx + 1) + l] * G[l];
+                    acc *= sScal[0];
+                } else if (t < QX2 + VY) {
+                    const int j = t - QX2;
+                    if (g.Qy) {
+                        const double* G = sCoef + 2 * (g.Nx + 1);
+                        for (int l = 0; l <= g.Ny; ++l) acc += (double)sTy[j * (g.Ny + 1) + l] * G[l];
+                    } else {
+                        acc = 1.0;
+                    }
+                } else {
+                    const int k = t - QX2 - VY;
+                    if (g.Qz) {
+                        const double* G = sCoef + 2 * (g.Nx + 1) + (g.Ny + 1);
+                        for (int l = 0; l <= g.Nz; ++l) acc += (double)sTz[k * (g.Nz + 1) + l] * G[l];
+                    } else {
+                        acc = 1.0;
+                    }
+                }
+                sG[t] = (R)acc;
+            }
+        }
+        __syncthreads();
+
+        const R inv_tau = (R)sScal[1];
+        const R dt = (R)I.dt;
+        const R inv_dx = (R)(1.0 / g.dx[I.dx_off + x]);
+        const R inv_dy = (R)I.inv_dy;
+        const R ax = (R)I.ax, ay = (R)I.ay, az = (R)I.az;
+        const double nwl = g.nw[(size_t)(I.row_off + y) * 2 + 0];
+        const double nwr = g.nw[(size_t)(I.row_off + y) * 2 + 1];
+        const R* gwl = gw + I.gw_off;
+        const R* gwr = gwl + V;
+        const int ny = I.ny;
+
+        // 3. per velocity
+        for (int v = tid; v < V; v += bs) {
+            const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
+            const R f = sF[v];
+            const R feq = sG[ix] * sG[QX2 + jy] * sG[QX2 + VY + kz];
+            // force: sum_a a_a (K_a f)
+            R force = 0;
+            if (ax != R(0)) {
+                const R* Kr = sKx + ix * QX2;
+                const R* fr = sF + (v - ix);
+                R acc = 0;
+                for (int i = 0; i < QX2; ++i) acc += Kr[i] * fr[i];
+                force += ax * acc;
+            }
+            if (ay != R(0) && g.Qy) {
+                const R* Kr = sKy + jy * VY;
+                const R* fr = sF + (v - jy * QX2);
+                R acc = 0;
+                for (int j = 0; j < VY; ++j) acc += Kr[j] * fr[j * QX2];
+                force += ay * acc;
+            }
+            if (az != R(0) && g.Qz) {
+                const R* Kr = sKz + kz * VZ;
+                const R* fr = sF + (v - kz * QX2 * VY);
+                R acc = 0;
+                for (int k = 0; k < VZ; ++k) acc += Kr[k] * fr[(size_t)k * QX2 * VY];
+                force += az * acc;
+            }
+            // advection along x
+            const R vx = sPx[ix];
+            const bool xpos = ix < Qx;
+            R w[6];
+            const int base = xpos ? x - 3 : x - 2;
+            const R nwl_g = (R)nwl * gwl[v], nwr_g = (R)nwr * gwr[v];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) w[k] = x_value(frow, base + k, nx, V, v, xpos, nwl_g, nwr_g);
+            R Fp, Fm;
+            face_pair<R, ADV>(w, xpos, Fp, Fm);
+            R Lval = -vx * (Fp - Fm) * inv_dx;
+            // advection along y (periodic)
+            if (ny > 1) {
+                const R vy = sPy[jy];
+                const bool ypos = vy > R(0);
+                const int yb = ypos ? y - 3 : y - 2;
+                const R* fcol = fs + (size_t)I.f_off + (size_t)x * V + v;
+                const size_t rstride = (size_t)nx * V;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    int yy = yb + k;
+                    yy += (yy < 0) ? ny : 0;
+                    yy -= (yy >= ny) ? ny : 0;
+                    w[k] = fcol[(size_t)yy * rstride];
+                }
+                R Gp, Gm;
+                face_pair<R, ADV>(w, ypos, Gp, Gm);
+                Lval -= vy * (Gp - Gm) * inv_dy;
+            }
+            Lval -= force;
+            Lval -= (f - feq) * inv_tau;
+            R out;
+            if (stage == 0) {
+                out = f + dt * Lval;
+            } else {
+                const R fnv = fn[row_off + (size_t)x * V + v];
+                if (stage == 1) out = R(0.75) * fnv + R(0.25) * f + R(0.25) * dt * Lval;
+                else out = fnv * R(1.0 / 3.0) + R(2.0 / 3.0) * f + R(2.0 / 3.0) * dt * Lval;
+            }
+            fo[row_off + (size_t)x * V + v] = out;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// wall kernel: emitted densities of both walls of one (instance, y) row
+// ---------------------------------------------------------------------------
+template <typename R, int ADV>
+__global__ void __launch_bounds__(256)
+wall_kernel(const GroupDev g, const R* __restrict__ fs) {
+    __shared__ double red[2][8];
+    const int row = blockIdx.x;
+    if (row >= g.nrows) return;
+    const int ii = g.ninst > 1 ? find_slot(g.row_start, g.ninst, row) : 0;
+    const InstDev I = g.inst[ii];
+    const int y = row - I.row_off;
+    const int nx = I.nx, V = g.V, QX2 = g.QX2;
+    const R* frow = fs + (size_t)I.f_off + (size_t)y * nx * V;
+    double accL = 0.0, accR = 0.0;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        const int ix = v % QX2;
+        const double px = g.pd[ix];
+        double f0, f1, f2;
+        if (px < 0) {       // incident on the left wall: face -1/2
+            f0 = frow[v]; f1 = frow[(size_t)V + v]; f2 = frow[2 * (size_t)V + v];
+        } else {            // incident on the right wall: face nx-1/2
+            f0 = frow[(size_t)(nx - 1) * V + v]; f1 = frow[(size_t)(nx - 2) * V + v];
+            f2 = frow[(size_t)(nx - 3) * V + v];
+        }
+        double F;
+        if (ADV == HLB_WENO5_) {
+            const double d = 3.0 * f0 - 3.0 * f1 + f2, e = 6.0 * f0 - 8.0 * f1 + 3.0 * f2;
+            F = px * weno5_face<double>(f2, f1, f0, d, e);
+        } else {
+            F = px * upwind2_face<double>(f1, f0);
+        }
+        if (px < 0) accL += F; else accR += F;
+    }
+    accL = warp_sum(accL);
+    accR = warp_sum(accR);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][warp] = accL; red[1][warp] = accR; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sl = 0.0, sr = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sl += red[0][w]; sr += red[1][w]; }
+        g.nw[(size_t)row * 2 + 0] = -sl / I.den_left;
+        g.nw[(size_t)row * 2 + 1] = -sr / I.den_right;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// state initialisation, moments (FP64 output), residual
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void broadcast_kernel(R* __restrict__ f, const R* __restrict__ g, long long nvalues, int V) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvalues;
+         i += (long long)gridDim.x * blockDim.x)
+        f[i] = g[i % V];
+}
+
+// One warp per node; two passes (mean velocity, then central moments).
+template <typename R>
+__global__ void moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double* u_out,
+                               double* T_out, double* q_out, int node_base) {
+    const int warps = (blockDim.x >> 5) * gridDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); node < g.nnodes; node += warps) {
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const InstDev I = g.inst[ii];
+        const int local = node - I.node_off;
+        const R* f = fs + (size_t)I.f_off + (size_t)local * g.V;
+        const double* px = g.pd;
+        const double* py = g.pd + g.QX2;
+        const double* pz = py + g.VY;
+        double n = 0, jx = 0, jy = 0, jz = 0;
+        for (int v = lane; v < g.V; v += 32) {
+            const int ix = v % g.QX2, j = (v / g.QX2) % g.VY, k = v / (g.QX2 * g.VY);
+            const double val = f[v];
+            n += val; jx += px[ix] * val; jy += py[j] * val; jz += pz[k] * val;
+        }
+        n = warp_sum(n); jx = warp_sum(jx); jy = warp_sum(jy); jz = warp_sum(jz);
+        const double ux = jx / n, uy = jy / n, uz = jz / n;
+        double e = 0, q = 0;
+        for (int v = lane; v < g.V; v += 32) {
+            const int ix = v % g.QX2, j = (v / g.QX2) % g.VY, k = v / (g.QX2 * g.VY);
+            const double val = f[v];
+            const double cx = px[ix] - ux, cy = py[j] - uy, cz = pz[k] - uz;
+            const double c2 = cx * cx + cy * cy + cz * cz;
+            e += c2 * val;
+            q += cx * c2 * val;
+        }
+        e = warp_sum(e);
+        q = warp_sum(q);
+        if (lane == 0) {
+            const long long o = node_base + node;
+            if (n_out) n_out[o] = n;
+            if (u_out) { u_out[3 * o] = ux; u_out[3 * o + 1] = uy; u_out[3 * o + 2] = uz; }
+            if (T_out) T_out[o] = e / (g.D * n);
+            if (q_out) q_out[o] = 0.5 * q;
+        }
+    }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// Per instance: max |a - b| and max |b| (non-negative doubles order like their bits).
+template <typename R>
+__global__ void residual_kernel(const GroupDev g, const R* __restrict__ a, const R* __restrict__ b,
+                                double* out /* [ninst][2] */) {
+    const int warps = (blockDim.x >> 5) * gridDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); node < g.nnodes; node += warps) {
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const InstDev I = g.inst[ii];
+        const size_t off = (size_t)I.f_off + (size_t)(node - I.node_off) * g.V;
+        double md = 0.0, mb = 0.0;
+        for (int v = lane; v < g.V; v += 32) {
+            const double bv = b[off + v];
+            md = fmax(md, fabs(bv - (double)a[off + v]));
+            mb = fmax(mb, fabs(bv));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+            mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        }
+        if (lane == 0) {
+            atomic_max_nonneg(out + 2 * ii, md);
+            atomic_max_nonneg(out + 2 * ii + 1, mb);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers (non-template entry points used by hlb_api.cu)
+// ---------------------------------------------------------------------------
+size_t stage_smem_bytes(const GroupDev& g, int precision, int block) {
+    return precision == HLB_FP64_ ? smem_layout<double>(g, block / 32).bytes
+                                  : smem_layout<float>(g, block / 32).bytes;
+}
+
+template <typename R, int ADV>
+static cudaError_t set_attr(size_t smem) {
+    return cudaFuncSetAttribute(stage_kernel<R, ADV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_stage(int precision, int adv, size_t smem) {
+    if (precision == HLB_FP64_) return adv == HLB_WENO5_ ? set_attr<double, HLB_WENO5_>(smem) : set_attr<double, HLB_UPWIND2_>(smem);
+    return adv == HLB_WENO5_ ? set_attr<float, HLB_WENO5_>(smem) : set_attr<float, HLB_UPWIND2_>(smem);
+}
+
+cudaError_t stage_occupancy(int precision, int adv, int block, size_t smem, int* blocks_per_sm) {
+    const void* fn;
+    if (precision == HLB_FP64_) fn = adv == HLB_WENO5_ ? (const void*)stage_kernel<double, HLB_WENO5_> : (const void*)stage_kernel<double, HLB_UPWIND2_>;
+    else fn = adv == HLB_WENO5_ ? (const void*)stage_kernel<float, HLB_WENO5_> : (const void*)stage_kernel<float, HLB_UPWIND2_>;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
+}
+
+void launch_stage(int precision, int adv, const GroupDev& g, const void* fs, const void* fn, void* fo,
+                  int stage, int grid, int block, size_t smem, cudaStream_t st) {
+    if (precision == HLB_FP64_) {
+        if (adv == HLB_WENO5_) stage_kernel<double, HLB_WENO5_><<<grid, block, smem, st>>>(g, (const double*)fs, (const double*)fn, (double*)fo, stage);
+        else stage_kernel<double, HLB_UPWIND2_><<<grid, block, smem, st>>>(g, (const double*)fs, (const double*)fn, (double*)fo, stage);
+    } else {
+        if (adv == HLB_WENO5_) stage_kernel<float, HLB_WENO5_><<<grid, block, smem, st>>>(g, (const float*)fs, (const float*)fn, (float*)fo, stage);
+        else stage_kernel<float, HLB_UPWIND2_><<<grid, block, smem, st>>>(g, (const float*)fs, (const float*)fn, (float*)fo, stage);
+    }
+}
+
+void launch_wall(int precision, int adv, const GroupDev& g, const void* fs, cudaStream_t st) {
+    const int block = 128;
+    if (precision == HLB_FP64_) {
+        if (adv == HLB_WENO5_) wall_kernel<double, HLB_WENO5_><<<g.nrows, block, 0, st>>>(g, (const double*)fs);
+        else wall_kernel<double, HLB_UPWIND2_><<<g.nrows, block, 0, st>>>(g, (const double*)fs);
+    } else {
+        if (adv == HLB_WENO5_) wall_kernel<float, HLB_WENO5_><<<g.nrows, block, 0, st>>>(g, (const float*)fs);
+        else wall_kernel<float, HLB_UPWIND2_><<<g.nrows, block, 0, st>>>(g, (const float*)fs);
+    }
+}
+
+void launch_broadcast(int precision, void* f, const void* gvec, long long nvalues, int V, cudaStream_t st) {
+    const int block = 256;
+    long long blocks = (nvalues + block - 1) / block;
+    const int grid = (int)(blocks < 65535LL * 16 ? blocks : 65535LL * 16);
+    if (precision == HLB_FP64_) broadcast_kernel<double><<<grid, block, 0, st>>>((double*)f, (const double*)gvec, nvalues, V);
+    else broadcast_kernel<float><<<grid, block, 0, st>>>((float*)f, (const float*)gvec, nvalues, V);
+}
+
+void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
+                    double* q, int node_base, cudaStream_t st) {
+    const int block = 256;
+    const int grid = (g.nnodes + 7) / 8 < 4096 ? (g.nnodes + 7) / 8 : 4096;
+    if (precision == HLB_FP64_) moments_kernel<double><<<grid, block, 0, st>>>(g, (const double*)fs, n, u, T, q, node_base);
+    else moments_kernel<float><<<grid, block, 0, st>>>(g, (const float*)fs, n, u, T, q, node_base);
+}
+
+void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out, cudaStream_t st) {
+    const int block = 256;
+    const int grid = (g.nnodes + 7) / 8 < 4096 ? (g.nnodes + 7) / 8 : 4096;
+    if (precision == HLB_FP64_) residual_kernel<double><<<grid, block, 0, st>>>(g, (const double*)a, (const double*)b, out);
+    else residual_kernel<float><<<grid, block, 0, st>>>(g, (const float*)a, (const float*)b, out);
+}
+
+}  // namespace hlb

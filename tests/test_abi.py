@@ -1,0 +1,93 @@
+"""The C ABI on the host: the library loads, exports every declared symbol,
+rejects bad configurations with HLB_EINVAL, and its host-built tables (an
+independent construction: discretised Stieltjes, Sturm bisection, Christoffel
+weights, the equilibrium recurrence in the orthonormal basis) agree with the
+oracle's 80-digit tables.  No GPU compute is called here."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1708_03249_gb300 import hlb, workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "hlb.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hlb_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(hlb_lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(hlb_lib, name), name
+        assert name in hlb.SIGNATURES, f"binding lacks {name}"
+
+
+def test_version(hlb_lib):
+    assert "sm_103a" in hlb.version()
+
+
+@pytest.mark.parametrize("field,value", [("Qx", 0), ("Qx", 33), ("Qy", 3), ("Qz", -2), ("nx", 5),
+                                          ("ny", 2), ("Kn", 0.0), ("T_left", -1.0), ("stretch_A", 1.0),
+                                          ("advection", 7), ("precision", 3), ("Nx_eq", 4), ("Lx", 0.0),
+                                          ("ax", math.nan)])
+def test_invalid_config_is_rejected(hlb_lib, field, value):
+    cfg = W.make(Qx=4, Qy=4, nx=16, Kn=1.0)
+    cfg[field] = value
+    with pytest.raises(hlb.HlbError) as e:
+        hlb.Handle(cfg)
+    assert e.value.status == hlb.HLB_EINVAL
+    assert "instance 0" in str(e.value)
+
+
+def test_mixed_precision_batch_is_rejected(hlb_lib):
+    a = W.make(Qx=4, nx=16, precision=W.FP32)
+    b = W.make(Qx=4, nx=16, precision=W.FP64)
+    with pytest.raises(hlb.HlbError) as e:
+        hlb.Handle([a, b])
+    assert e.value.status == hlb.HLB_EINVAL
+
+
+@pytest.mark.parametrize("Q", [1, 2, 3, 4, 8, 16])
+def test_half_range_axis_matches_oracle(hlb_lib, Q):
+    from oracle.model import VelocitySet
+    p, w, K = hlb.axis(Q, True)
+    vs = VelocitySet(Q)
+    np.testing.assert_allclose(p, vs.px, rtol=2e-15 * Q, atol=1e-15)
+    np.testing.assert_allclose(w, vs.wx, rtol=5e-14)
+    np.testing.assert_allclose(K, vs.Kx, atol=5e-14 * np.abs(vs.Kx).max())
+
+
+@pytest.mark.parametrize("Q", [2, 4, 8, 16])
+def test_full_range_axis_matches_oracle(hlb_lib, Q):
+    from oracle.model import h_force_matrix
+    from oracle.quadrature import gauss_hermite, to_f64
+    p, w, K = hlb.axis(Q, False)
+    d = gauss_hermite(Q)
+    np.testing.assert_allclose(p, to_f64(d["z"]), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(w, to_f64(d["w"]), rtol=5e-14)
+    np.testing.assert_allclose(K, h_force_matrix(Q), atol=5e-15 * np.abs(h_force_matrix(Q)).max())
+
+
+@pytest.mark.parametrize("Q,u,T,tol", [(4, 0.3, 1.4, 1e-13), (8, -0.4, 0.6, 1e-11), (8, 0.1, 2.0, 1e-11),
+                                       (16, 0.25, 1.3, 1e-7)])
+def test_equilibrium_recurrence_matches_oracle(hlb_lib, Q, u, T, tol):
+    # The library's orthonormal-basis recurrence (the per-node route of the
+    # kernels) against the oracle's term-by-term Eq. "eq:hh_gk".
+    from oracle.model import hh_equilibrium
+    g = hlb.equilibrium_x(Q, u, T)
+    ref = hh_equilibrium(Q, Q - 1, u, T, tol=0.0)
+    np.testing.assert_allclose(g, ref, atol=tol * np.abs(ref).max())
+
+
+def test_invalid_axis_and_equilibrium_arguments(hlb_lib):
+    with pytest.raises(hlb.HlbError):
+        hlb.axis(3, False)            # odd full-range order (Sec. IV.A.1)
+    with pytest.raises(hlb.HlbError):
+        hlb.equilibrium_x(4, 0.0, -1.0)
