@@ -32,9 +32,14 @@ template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b
 // WENO-5 face value per unit velocity for a positive velocity: (a..e) are the
 // values at cells i-2..i+2 of face i+1/2 (Sec. IV.C.2).  No epsilon: the
 // weights are delta_q/sigma_q^2 normalised, or, if any sigma_q vanishes,
-// delta_q over the vanishing set (Tab. "weno").  The sigmas are formed from
-// the stencil values divided by their largest magnitude; the weights are
-// invariant under that scaling and it keeps sigma^2 inside FP32's range.
+// delta_q over the vanishing set (Tab. "weno").
+//  - The sigmas are formed from the stencil values divided by their largest
+//    magnitude (the weights do not change under a common scaling), so that
+//    small populations do not underflow sigma in FP32.
+//  - delta_q/sigma_q^2 is evaluated as delta_q (sigma_min/sigma_q)^2, the
+//    same ratios multiplied by sigma_min^2: every factor lies in [0, 1], so
+//    nothing overflows, and a sigma far above sigma_min underflows to a zero
+//    weight, its exact limit.
 template <typename R>
 __device__ __forceinline__ R weno5_face(R a, R b, R c, R d, R e) {
     const R F1 = (R(2) * a - R(7) * b + R(11) * c) * R(1.0 / 6.0);
@@ -50,15 +55,17 @@ __device__ __forceinline__ R weno5_face(R a, R b, R c, R d, R e) {
     const R s1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
     const R s2 = R(13.0 / 12.0) * t3 * t3 + R(0.25) * t4 * t4;
     const R s3 = R(13.0 / 12.0) * t5 * t5 + R(0.25) * t6 * t6;
+    const R smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
     R w1, w2, w3;
-    if (s1 == R(0) || s2 == R(0) || s3 == R(0)) {
+    if (smin == R(0)) {
         w1 = s1 == R(0) ? R(0.1) : R(0);
         w2 = s2 == R(0) ? R(0.6) : R(0);
         w3 = s3 == R(0) ? R(0.3) : R(0);
     } else {
-        w1 = R(0.1) / (s1 * s1);
-        w2 = R(0.6) / (s2 * s2);
-        w3 = R(0.3) / (s3 * s3);
+        const R u1 = smin / s1, u2 = smin / s2, u3 = smin / s3;
+        w1 = R(0.1) * u1 * u1;
+        w2 = R(0.6) * u2 * u2;
+        w3 = R(0.3) * u3 * u3;
     }
     return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);
 }
@@ -243,11 +250,15 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
         const size_t row_off = (size_t)I.f_off + (size_t)y * nx * V;
         const R* frow = fs + row_off;
 
+        // Collisionless instances (Kn = +inf) have no BGK term at all: no
+        // moments and no equilibrium are formed for them.
+        const bool collide = I.inv_Kn != 0.0;
         // 1. node values and moment partial sums
         R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
         for (int v = tid; v < V; v += bs) {
             const R val = frow[(size_t)x * V + v];
             sF[v] = val;
+            if (!collide) continue;
             const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
             const R px = sPx[ix], py = sPy[jy], pz = sPz[kz];
             a0 += val;
@@ -256,6 +267,7 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
             a3 += pz * val;
             a4 += (px * px + py * py + pz * pz) * val;
         }
+        if (collide) {
         a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
         if (lane == 0) {
             sRed[warp * 5 + 0] = a0; sRed[warp * 5 + 1] = a1; sRed[warp * 5 + 2] = a2;
@@ -306,9 +318,10 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
                 sG[t] = (R)acc;
             }
         }
+        }  // collide
         __syncthreads();
 
-        const R inv_tau = (R)sScal[1];
+        const R inv_tau = collide ? (R)sScal[1] : R(0);
         const R dt = (R)I.dt;
         const R inv_dx = (R)(1.0 / g.dx[I.dx_off + x]);
         const R inv_dy = (R)I.inv_dy;
@@ -323,7 +336,7 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
         for (int v = tid; v < V; v += bs) {
             const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
             const R f = sF[v];
-            const R feq = sG[ix] * sG[QX2 + jy] * sG[QX2 + VY + kz];
+            const R feq = collide ? sG[ix] * sG[QX2 + jy] * sG[QX2 + VY + kz] : R(0);
             // force: sum_a a_a (K_a f)
             R force = 0;
             if (ax != R(0)) {
@@ -377,7 +390,7 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
                 Lval -= vy * (Gp - Gm) * inv_dy;
             }
             Lval -= force;
-            Lval -= (f - feq) * inv_tau;
+            if (collide) Lval -= (f - feq) * inv_tau;
             R out;
             if (stage == 0) {
                 out = f + dt * Lval;
