@@ -51,9 +51,13 @@ struct Group {
     int cur = 0, prev = -1;
     DevBuf d_inst, d_node_start, d_row_start, d_K, d_p, d_pd, d_T, d_rec, d_dx, d_gw, d_nw, d_resid;
     DevBuf d_mom;                            // moments scratch: 6 doubles per node
+    DevBuf d_Td, d_invdx, d_wscale, d_coef, d_works, d_err;
     hlb::GroupDev dev{};
     int block = 256, grid = 1;
     size_t smem = 0;
+    // marching stage kernel (node + march) or the generic per-node kernel
+    int TY = 1, SX = 0, nworks = 0;
+    bool march_ok = false;
 };
 
 struct KernelTimer {
@@ -185,6 +189,12 @@ void fill_dev(Group& G) {
     d.K = G.d_K.p; d.p = G.d_p.p; d.pd = (const double*)G.d_pd.p; d.Tt = G.d_T.p;
     d.rec = (const double*)G.d_rec.p; d.dx = (const double*)G.d_dx.p;
     d.gw = G.d_gw.p; d.nw = (double*)G.d_nw.p;
+    d.Td = (const double*)G.d_Td.p;
+    d.inv_dx = G.d_invdx.p;
+    d.wscale = G.d_wscale.p;
+    d.coef = G.d_coef.p;
+    d.ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
+    d.err = (int*)G.d_err.p;
 }
 
 hlb_status build_group(hlb_handle* h, Group& G) {
@@ -263,7 +273,17 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     rec.insert(rec.end(), G.tx.rb.begin(), G.tx.rb.end());
     rec.insert(rec.end(), G.tx.rc.begin(), G.tx.rc.end());
     rec.insert(rec.end(), G.tx.h0.begin(), G.tx.h0.end());
+    for (double a : G.tx.ra) rec.push_back(1.0 / a);
+    std::vector<double> invdx(G.dx_all.size()), wscale(G.V);
+    for (size_t i = 0; i < invdx.size(); ++i) invdx[i] = 1.0 / G.dx_all[i];
+    for (int k = 0; k < G.VZ; ++k)
+        for (int j = 0; j < G.VY; ++j)
+            for (int i = 0; i < G.QX2; ++i)
+                wscale[(k * G.VY + j) * G.QX2 + i] = 1.0 / (G.tx.w[i] * G.ty.w[j] * G.tz.w[k]);
     hlb_status s;
+    if ((s = upload(G.d_Td, T)) != HLB_OK) return s;
+    if ((s = upload_real(G.d_invdx, invdx, G.precision)) != HLB_OK) return s;
+    if ((s = upload_real(G.d_wscale, wscale, G.precision)) != HLB_OK) return s;
     if ((s = upload_real(G.d_K, K, G.precision)) != HLB_OK) return s;
     if ((s = upload_real(G.d_p, p, G.precision)) != HLB_OK) return s;
     if ((s = upload(G.d_pd, p)) != HLB_OK) return s;
@@ -274,6 +294,7 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     if ((s = upload(G.d_row_start, G.row_start)) != HLB_OK) return s;
     if ((s = upload(G.d_nw, std::vector<double>((size_t)G.nrows * 2, 0.0))) != HLB_OK) return s;
     if ((s = upload(G.d_resid, std::vector<double>(G.members.size() * 2, 0.0))) != HLB_OK) return s;
+    if ((s = upload(G.d_err, std::vector<int>(4, 0))) != HLB_OK) return s;
     if ((s = refresh_walls(h, G)) != HLB_OK) return s;
 
     // state buffers
@@ -288,6 +309,55 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     if (cudaMalloc(&G.d_mom.p, std::max<size_t>((size_t)G.nnodes * 6 * sizeof(double), 16)) != cudaSuccess) {
         cudaGetLastError();
         return fail(HLB_ENOMEM, "cudaMalloc of moment scratch failed");
+    }
+    {
+        const int ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
+        if (cudaMalloc(&G.d_coef.p, std::max<size_t>((size_t)G.nnodes * ncp * G.esize, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(HLB_ENOMEM, "cudaMalloc of the equilibrium factor lines failed");
+        }
+    }
+    // marching kernel: slab = the 2Qx x Qy velocities of one p_z; strips of TY
+    // rows (2D) and x-segments sized for enough CTAs to fill the GPU
+    {
+        bool two_d = false, small_ny = false;
+        long long xwork = 0;
+        for (size_t m = 0; m < G.members.size(); ++m) {
+            const hlb_config& c = h->cfg[G.members[m]];
+            if (c.ny > 1) two_d = true;
+            xwork += (long long)c.nx * c.ny * G.VZ;
+        }
+        G.TY = two_d ? 2 : 1;
+        for (size_t m = 0; m < G.members.size(); ++m) {
+            const hlb_config& c = h->cfg[G.members[m]];
+            if ((c.ny > 1) != two_d || (two_d && c.ny < G.TY + 3)) small_ny = true;
+        }
+        bool big = false;      // the marching kernel indexes an instance with 32-bit offsets
+        for (size_t m = 0; m < G.members.size(); ++m) {
+            const hlb_config& c = h->cfg[G.members[m]];
+            if ((long long)c.nx * c.ny * G.V >= (1LL << 31) - (long long)G.V * 8) big = true;
+        }
+        G.march_ok = !small_ny && !big && hlb::march_available(G.precision, G.adv, G.QX2, G.VY, G.TY);
+        if (G.march_ok) {
+            const long long rows = xwork / std::max(1LL, (long long)G.TY);
+            long long sx = rows / 4096;
+            sx = std::max(24LL, std::min(512LL, (sx + 5) / 6 * 6));
+            G.SX = (int)sx;
+            std::vector<hlb::Work> works;
+            for (int kz = 0; kz < G.VZ; ++kz)
+                for (size_t m = 0; m < G.members.size(); ++m) {
+                    const hlb_config& c = h->cfg[G.members[m]];
+                    for (int xa = 0; xa < c.nx; xa += G.SX)
+                        for (int y0 = 0; y0 < c.ny; y0 += G.TY) {
+                            hlb::Work w{};
+                            w.inst = (int)m; w.y0 = y0; w.xa = xa; w.xb = std::min(c.nx, xa + G.SX); w.kz = kz;
+                            works.push_back(w);
+                        }
+                }
+            G.nworks = (int)works.size();
+            if ((s = upload(G.d_works, works)) != HLB_OK) return s;
+            HLB_CUDA(hlb::prepare_march(G.precision, G.adv, G.QX2, G.VY, G.TY));
+        }
     }
     fill_dev(G);
 
@@ -304,6 +374,14 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     return HLB_OK;
 }
 
+// The marching kernel keeps one p_z per CTA; a force along p_z mixes them.
+bool group_has_z_force(const hlb_handle* h, const Group& G) {
+    if (!G.Qz) return false;
+    for (int i : G.members)
+        if (h->cfg[i].az != 0.0) return true;
+    return false;
+}
+
 // One RK-3 step of one group: three (wall, stage) pairs; buffer roles rotate.
 void enqueue_group_step(hlb_handle* h, Group& G) {
     void* S = G.buf[G.cur].p;
@@ -317,9 +395,15 @@ void enqueue_group_step(hlb_handle* h, Group& G) {
             cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
             cudaEventRecord(e0, h->stream);
         }
+        const bool march = G.march_ok && !group_has_z_force(h, G);
+        if (march) hlb::launch_node(G.precision, G.dev, ins[st], h->stream);
         hlb::launch_wall(G.precision, G.adv, G.dev, ins[st], h->stream);
         if (h->time_kernels) cudaEventRecord(e1, h->stream);
-        hlb::launch_stage(G.precision, G.adv, G.dev, ins[st], S, outs[st], st, G.grid, G.block, G.smem, h->stream);
+        if (march)
+            hlb::launch_march(G.precision, G.adv, G.QX2, G.VY, G.TY, G.dev, (const hlb::Work*)G.d_works.p,
+                              G.nworks, ins[st], S, outs[st], st, h->stream);
+        else
+            hlb::launch_stage(G.precision, G.adv, G.dev, ins[st], S, outs[st], st, G.grid, G.block, G.smem, h->stream);
         if (h->time_kernels) {
             cudaEventRecord(e2, h->stream);
             h->timer.wall.push_back({e0, e1});
@@ -373,6 +457,22 @@ hlb_status build_graph(hlb_handle* h) {
     e = cudaGraphInstantiate(&h->graph, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(HLB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return HLB_OK;
+}
+
+// Reads and clears the groups' device error words (after a stream sync).
+hlb_status check_device_error(hlb_handle* h) {
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    for (auto& G : h->groups) {
+        int err = 0;
+        HLB_CUDA(cudaMemcpy(&err, G->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) {
+            HLB_CUDA(cudaMemset(G->d_err.p, 0, sizeof(int)));
+            if (err == HLB_ETIMEOUT)
+                return fail(HLB_ETIMEOUT, "a bounded device wait (bulk-copy pipeline) gave up; state is invalid");
+            return fail((hlb_status)err, "device error word set");
+        }
+    }
     return HLB_OK;
 }
 
@@ -596,6 +696,10 @@ hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* 
 
 hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    {
+        hlb_status e = check_device_error(h);
+        if (e != HLB_OK) return e;
+    }
     bool finite = true;
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
@@ -671,6 +775,10 @@ static hlb_status state_copy(hlb_handle* h, void* ext, size_t bytes, bool to_ext
 }
 
 hlb_status hlb_get_state(hlb_handle* h, void* host_f, size_t bytes) {
+    if (h) {
+        hlb_status e = check_device_error(h);
+        if (e != HLB_OK) return e;
+    }
     return state_copy(h, host_f, bytes, true, cudaMemcpyDeviceToHost, true);
 }
 hlb_status hlb_set_state(hlb_handle* h, const void* host_f, size_t bytes) {

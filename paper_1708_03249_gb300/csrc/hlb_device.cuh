@@ -1,0 +1,285 @@
+// Device helpers shared by the stage kernels (included by the .cu files).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hlb_internal.h"
+
+namespace hlb {
+
+constexpr double kInvSqrt2Pi = 0.39894228040143267793994605993438;
+constexpr double kSqrt2Pi = 2.5066282746310005024157652848110;
+
+template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
+template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+
+// WENO-5 face value per unit velocity for a positive velocity: (a..e) are the
+// values at cells i-2..i+2 of face i+1/2 (Sec. IV.C.2).  No epsilon: the
+// weights are delta_q/sigma_q^2 normalised, or, if any sigma_q vanishes,
+// delta_q over the vanishing set (Tab. "weno").
+//  - The sigmas are formed from the stencil values divided by their largest
+//    magnitude (the weights do not change under a common scaling), so that
+//    small populations do not underflow sigma in FP32.
+//  - delta_q/sigma_q^2 is evaluated as delta_q (sigma_min/sigma_q)^2, the
+//    same ratios multiplied by sigma_min^2: every factor lies in [0, 1], so
+//    nothing overflows, and a sigma far above sigma_min underflows to a zero
+//    weight, its exact limit.
+template <typename R>
+__device__ __forceinline__ R weno5_face(R a, R b, R c, R d, R e) {
+    const R F1 = (R(2) * a - R(7) * b + R(11) * c) * R(1.0 / 6.0);
+    const R F2 = (-b + R(5) * c + R(2) * d) * R(1.0 / 6.0);
+    const R F3 = (R(2) * c + R(5) * d - e) * R(1.0 / 6.0);
+    const R m = rmax(rmax(rmax(rabs(a), rabs(b)), rmax(rabs(c), rabs(d))), rabs(e));
+    if (m == R(0)) return R(0);
+    const R r = R(1) / m;
+    const R A = a * r, B = b * r, C = c * r, Dd = d * r, E = e * r;
+    const R t1 = A - R(2) * B + C, t2 = A - R(4) * B + R(3) * C;
+    const R t3 = B - R(2) * C + Dd, t4 = B - Dd;
+    const R t5 = C - R(2) * Dd + E, t6 = R(3) * C - R(4) * Dd + E;
+    const R s1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
+    const R s2 = R(13.0 / 12.0) * t3 * t3 + R(0.25) * t4 * t4;
+    const R s3 = R(13.0 / 12.0) * t5 * t5 + R(0.25) * t6 * t6;
+    const R smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
+    R w1, w2, w3;
+    if (smin == R(0)) {
+        w1 = s1 == R(0) ? R(0.1) : R(0);
+        w2 = s2 == R(0) ? R(0.6) : R(0);
+        w3 = s3 == R(0) ? R(0.3) : R(0);
+    } else {
+        const R u1 = smin / s1, u2 = smin / s2, u3 = smin / s3;
+        w1 = R(0.1) * u1 * u1;
+        w2 = R(0.6) * u2 * u2;
+        w3 = R(0.3) * u3 * u3;
+    }
+    return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);
+}
+
+// Same weights as weno5_face, for the marching kernel: the smoothness
+// indicators are formed from the stencil values times a fixed per-velocity
+// scale ``sv`` (the inverse quadrature weight of the population, so that the
+// scaled values are O(n)), and the reciprocals use the fast FP32 unit.  A
+// non-zero sigma below 1e-30 (far under FP32's resolution of an O(1) scaled
+// stencil) is treated as 1e-30, which ties it with any other such sigma.
+template <typename R>
+__device__ __forceinline__ R weno5_face_sv(R a, R b, R c, R d, R e, R sv);
+
+template <>
+__device__ __forceinline__ double weno5_face_sv<double>(double a, double b, double c, double d, double e,
+                                                        double sv) {
+    (void)sv;
+    return weno5_face<double>(a, b, c, d, e);
+}
+
+template <>
+__device__ __forceinline__ float weno5_face_sv<float>(float a, float b, float c, float d, float e, float sv) {
+    const float F1 = (2.0f * a - 7.0f * b + 11.0f * c) * (1.0f / 6.0f);
+    const float F2 = (-b + 5.0f * c + 2.0f * d) * (1.0f / 6.0f);
+    const float F3 = (2.0f * c + 5.0f * d - e) * (1.0f / 6.0f);
+    const float A = a * sv, B = b * sv, C = c * sv, Dd = d * sv, E = e * sv;
+    const float t1 = A - 2.0f * B + C, t2 = A - 4.0f * B + 3.0f * C;
+    const float t3 = B - 2.0f * C + Dd, t4 = B - Dd;
+    const float t5 = C - 2.0f * Dd + E, t6 = 3.0f * C - 4.0f * Dd + E;
+    const float s1 = (13.0f / 12.0f) * t1 * t1 + 0.25f * t2 * t2;
+    const float s2 = (13.0f / 12.0f) * t3 * t3 + 0.25f * t4 * t4;
+    const float s3 = (13.0f / 12.0f) * t5 * t5 + 0.25f * t6 * t6;
+    float w1, w2, w3;
+    if (fminf(s1, fminf(s2, s3)) == 0.0f) {
+        w1 = s1 == 0.0f ? 0.1f : 0.0f;
+        w2 = s2 == 0.0f ? 0.6f : 0.0f;
+        w3 = s3 == 0.0f ? 0.3f : 0.0f;
+    } else {
+        const float c1 = fmaxf(s1, 1e-30f), c2 = fmaxf(s2, 1e-30f), c3 = fmaxf(s3, 1e-30f);
+        const float m = fminf(c1, fminf(c2, c3));
+        const float u1 = m * __fdividef(1.0f, c1), u2 = m * __fdividef(1.0f, c2), u3 = m * __fdividef(1.0f, c3);
+        w1 = 0.1f * u1 * u1;
+        w2 = 0.6f * u2 * u2;
+        w3 = 0.3f * u3 * u3;
+    }
+    return (w1 * F1 + w2 * F2 + w3 * F3) * __fdividef(1.0f, w1 + w2 + w3);
+}
+
+template <typename R>
+__device__ __forceinline__ R upwind2_face(R b, R c) { return R(1.5) * c - R(0.5) * b; }
+
+// ---------------------------------------------------------------------------
+// WENO-5 on pre-scaled stencils (values already multiplied by the
+// population's inverse weight), branch-free.  Clamping every sigma at 1e-30
+// before forming delta_q (sigma_min/sigma_q)^2 reproduces all zero-set rows of
+// Tab. "weno": vanishing sigmas tie at the clamp and share weight in the
+// ratio of their delta_q, and the others get (1e-30/sigma)^2 ~ 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float weno5_scaled(float a, float b, float c, float d, float e) {
+    const float F1 = fmaf(11.0f / 6.0f, c, fmaf(-7.0f / 6.0f, b, (1.0f / 3.0f) * a));
+    const float F2 = fmaf(1.0f / 3.0f, d, fmaf(5.0f / 6.0f, c, (-1.0f / 6.0f) * b));
+    const float F3 = fmaf(-1.0f / 6.0f, e, fmaf(5.0f / 6.0f, d, (1.0f / 3.0f) * c));
+    const float t1 = fmaf(-2.0f, b, a) + c, t2 = fmaf(3.0f, c, fmaf(-4.0f, b, a));
+    const float t3 = fmaf(-2.0f, c, b) + d, t4 = b - d;
+    const float t5 = fmaf(-2.0f, d, c) + e, t6 = fmaf(-4.0f, d, fmaf(3.0f, c, e));
+    const float s1 = fmaxf(fmaf(13.0f / 12.0f * t1, t1, 0.25f * t2 * t2), 1e-30f);
+    const float s2 = fmaxf(fmaf(13.0f / 12.0f * t3, t3, 0.25f * t4 * t4), 1e-30f);
+    const float s3 = fmaxf(fmaf(13.0f / 12.0f * t5, t5, 0.25f * t6 * t6), 1e-30f);
+    const float m = fminf(s1, fminf(s2, s3));
+    const float u1 = m * __fdividef(1.0f, s1), u2 = m * __fdividef(1.0f, s2), u3 = m * __fdividef(1.0f, s3);
+    const float w1 = 0.1f * u1 * u1, w2 = 0.6f * u2 * u2, w3 = 0.3f * u3 * u3;
+    return fmaf(w1, F1, fmaf(w2, F2, w3 * F3)) * __fdividef(1.0f, w1 + w2 + w3);
+}
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Two independent faces at once in the packed FP32 pipe (f32x2 on sm_100+).
+__device__ __forceinline__ float2 weno5_scaled2(float2 a, float2 b, float2 c, float2 d, float2 e) {
+    const float2 F1 = __ffma2_rn(f2(11.0f / 6.0f), c, __ffma2_rn(f2(-7.0f / 6.0f), b, __fmul2_rn(f2(1.0f / 3.0f), a)));
+    const float2 F2 = __ffma2_rn(f2(1.0f / 3.0f), d, __ffma2_rn(f2(5.0f / 6.0f), c, __fmul2_rn(f2(-1.0f / 6.0f), b)));
+    const float2 F3 = __ffma2_rn(f2(-1.0f / 6.0f), e, __ffma2_rn(f2(5.0f / 6.0f), d, __fmul2_rn(f2(1.0f / 3.0f), c)));
+    const float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.0f), b, a), c);
+    const float2 t2 = __ffma2_rn(f2(3.0f), c, __ffma2_rn(f2(-4.0f), b, a));
+    const float2 t3 = __fadd2_rn(__ffma2_rn(f2(-2.0f), c, b), d);
+    const float2 t4 = __fadd2_rn(b, __fmul2_rn(f2(-1.0f), d));
+    const float2 t5 = __fadd2_rn(__ffma2_rn(f2(-2.0f), d, c), e);
+    const float2 t6 = __ffma2_rn(f2(-4.0f), d, __ffma2_rn(f2(3.0f), c, e));
+    const float2 q1 = __ffma2_rn(__fmul2_rn(f2(13.0f / 12.0f), t1), t1, __fmul2_rn(__fmul2_rn(f2(0.25f), t2), t2));
+    const float2 q2 = __ffma2_rn(__fmul2_rn(f2(13.0f / 12.0f), t3), t3, __fmul2_rn(__fmul2_rn(f2(0.25f), t4), t4));
+    const float2 q3 = __ffma2_rn(__fmul2_rn(f2(13.0f / 12.0f), t5), t5, __fmul2_rn(__fmul2_rn(f2(0.25f), t6), t6));
+    const float2 s1 = make_float2(fmaxf(q1.x, 1e-30f), fmaxf(q1.y, 1e-30f));
+    const float2 s2 = make_float2(fmaxf(q2.x, 1e-30f), fmaxf(q2.y, 1e-30f));
+    const float2 s3 = make_float2(fmaxf(q3.x, 1e-30f), fmaxf(q3.y, 1e-30f));
+    const float2 m = make_float2(fminf(s1.x, fminf(s2.x, s3.x)), fminf(s1.y, fminf(s2.y, s3.y)));
+    const float2 u1 = __fmul2_rn(m, make_float2(__fdividef(1.0f, s1.x), __fdividef(1.0f, s1.y)));
+    const float2 u2 = __fmul2_rn(m, make_float2(__fdividef(1.0f, s2.x), __fdividef(1.0f, s2.y)));
+    const float2 u3 = __fmul2_rn(m, make_float2(__fdividef(1.0f, s3.x), __fdividef(1.0f, s3.y)));
+    const float2 w1 = __fmul2_rn(__fmul2_rn(f2(0.1f), u1), u1);
+    const float2 w2 = __fmul2_rn(__fmul2_rn(f2(0.6f), u2), u2);
+    const float2 w3 = __fmul2_rn(__fmul2_rn(f2(0.3f), u3), u3);
+    const float2 ws = __fadd2_rn(__fadd2_rn(w1, w2), w3);
+    const float2 num = __ffma2_rn(w1, F1, __ffma2_rn(w2, F2, __fmul2_rn(w3, F3)));
+    return __fmul2_rn(num, make_float2(__fdividef(1.0f, ws.x), __fdividef(1.0f, ws.y)));
+}
+
+__device__ __forceinline__ float2 upwind2_face2(float2 b, float2 c) {
+    return __ffma2_rn(f2(1.5f), c, __fmul2_rn(f2(-0.5f), b));
+}
+
+__device__ __forceinline__ int find_slot(const int* start, int n, int key) {
+    int lo = 0, hi = n;            // start[lo] <= key < start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(start + mid) <= key) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per-node equilibrium coefficients in FP64.  Thread role r:
+//   r = 0, 1: half-range G_l^{+-} (l <= Nx) by the recurrence in the
+//             orthonormal basis (see hlb_tables.cpp);
+//   r = 2:    full-range G_l along p_y;  r = 3: along p_z.
+__device__ inline void node_coefficients(const GroupDev& g, int r, double ux, double uy, double uz,
+                                  double T, const double* rec, double* coef) {
+    const int Nx = g.Nx;
+    if (r < 2) {
+        const double* ra = rec;
+        (void)ra;
+        const double* rb = rec + Nx;
+        const double* rc = rec + 2 * Nx;
+        const double* h0 = rec + 3 * Nx;
+        const double* inv_ra = rec + 4 * Nx + 1;
+        double* G = coef + r * (Nx + 1);
+        const double us = r ? -ux : ux;
+        const double g0 = exp(-ux * ux / (2.0 * T)) / (kSqrt2Pi * sqrt(T));
+        G[0] = h0[0] * 0.5 * (1.0 + erf(us / sqrt(2.0 * T)));
+        double S = 0.0;
+        double gm1 = 0.0;
+        for (int l = 0; l < Nx; ++l) {
+            const double ig = (l ? gm1 * inv_ra[l - 1] : 0.0) - kInvSqrt2Pi * h0[l] * S;
+            const double pg = us * G[l] + T * (g0 * h0[l] + ig);
+            G[l + 1] = ra[l] * pg + rb[l] * G[l] + rc[l] * gm1;
+            S += h0[l] * G[l];
+            gm1 = G[l];
+        }
+    } else {
+        const int N = r == 2 ? g.Ny : g.Nz;
+        const double u = r == 2 ? uy : uz;
+        double* G = coef + 2 * (Nx + 1) + (r == 2 ? 0 : g.Ny + 1);
+        G[0] = 1.0;
+        if (N >= 1) G[1] = u;
+        for (int l = 1; l < N; ++l) G[l + 1] = u * G[l] + l * (T - 1.0) * G[l - 1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (global -> shared) completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// its later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: gives up after about one second, records HLB_ETIMEOUT in
+// *err and returns false.  The caller carries on with whatever the buffer
+// holds, so that no barrier of the CTA is left waiting.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitNs) {
+            atomicExch(err, 4);   // HLB_ETIMEOUT
+            return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace hlb

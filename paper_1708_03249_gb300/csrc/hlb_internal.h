@@ -59,8 +59,17 @@ struct InstDev {
     int gw_off;          // offset of [2][V] wall Maxwellians (values of R)
 };
 
+// One CTA of the marching stage kernel: instance, y-strip, x-segment, kz slab.
+struct Work {
+    int inst, y0, xa, xb, kz, pad0, pad1, pad2;
+};
+
 struct GroupDev {
     int V, QX2, VY, VZ, Qx, Nx, Ny, Nz, Qy, Qz, D;
+    int ncp;                 // stride of a node's equilibrium-factor line
+    void* coef;              // R: [node][ncp] = g_x * n (QX2), g_y (VY), g_z (VZ), 1/tau
+    const void* inv_dx;      // R: 1/dx, concatenated per instance (same offsets as dx)
+    const void* wscale;      // R: [V] 1/(w_x w_y w_z) per velocity (WENO smoothness scale)
     int ninst, nnodes, nrows;
     const InstDev* inst;
     const int* node_start;   // [ninst + 1]
@@ -69,10 +78,12 @@ struct GroupDev {
     const void* p;           // R: px [QX2], py [VY], pz [VZ]
     const double* pd;        // FP64 copies of px, py, pz
     const void* Tt;          // R: Tx [Qx (Nx+1)], Ty [VY (Ny+1)], Tz [VZ (Nz+1)]
-    const double* rec;       // FP64: ra[Nx], rb[Nx], rc[Nx], h0[Nx+1]
+    const double* rec;       // FP64: ra[Nx], rb[Nx], rc[Nx], h0[Nx+1], 1/ra[Nx]
+    const double* Td;        // FP64 copies of Tx, Ty, Tz
     const double* dx;        // FP64 x-cell widths, concatenated per instance
     const void* gw;          // R: wall Maxwellians
     double* nw;              // FP64 [nrows][2] emitted densities
+    int* err;                // device error word (0 = ok; else an hlb_status)
 };
 
 }  // namespace hlb
@@ -86,6 +97,12 @@ cudaError_t stage_occupancy(int precision, int adv, int block, size_t smem, int*
 void launch_stage(int precision, int adv, const GroupDev& g, const void* fs, const void* fn, void* fo,
                   int stage, int grid, int block, size_t smem, cudaStream_t st);
 void launch_wall(int precision, int adv, const GroupDev& g, const void* fs, cudaStream_t st);
+void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t st);
+// Marching stage kernel for (QX2, VY, TY); returns false if no instantiation exists.
+bool march_available(int precision, int adv, int QX2, int VY, int TY);
+cudaError_t prepare_march(int precision, int adv, int QX2, int VY, int TY);
+void launch_march(int precision, int adv, int QX2, int VY, int TY, const GroupDev& g, const Work* works,
+                  int nworks, const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
 void launch_broadcast(int precision, void* f, const void* gvec, long long nvalues, int V, cudaStream_t st);
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
                     double* q, int node_base, cudaStream_t st);

@@ -18,76 +18,11 @@
 #include <cstdint>
 
 #include "hlb_internal.h"
+#include "hlb_device.cuh"
 
 namespace hlb {
 
 namespace {
-
-constexpr double kInvSqrt2Pi = 0.39894228040143267793994605993438;
-constexpr double kSqrt2Pi = 2.5066282746310005024157652848110;
-
-template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
-template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
-
-// WENO-5 face value per unit velocity for a positive velocity: (a..e) are the
-// values at cells i-2..i+2 of face i+1/2 (Sec. IV.C.2).  No epsilon: the
-// weights are delta_q/sigma_q^2 normalised, or, if any sigma_q vanishes,
-// delta_q over the vanishing set (Tab. "weno").
-//  - The sigmas are formed from the stencil values divided by their largest
-//    magnitude (the weights do not change under a common scaling), so that
-//    small populations do not underflow sigma in FP32.
-//  - delta_q/sigma_q^2 is evaluated as delta_q (sigma_min/sigma_q)^2, the
-//    same ratios multiplied by sigma_min^2: every factor lies in [0, 1], so
-//    nothing overflows, and a sigma far above sigma_min underflows to a zero
-//    weight, its exact limit.
-template <typename R>
-__device__ __forceinline__ R weno5_face(R a, R b, R c, R d, R e) {
-    const R F1 = (R(2) * a - R(7) * b + R(11) * c) * R(1.0 / 6.0);
-    const R F2 = (-b + R(5) * c + R(2) * d) * R(1.0 / 6.0);
-    const R F3 = (R(2) * c + R(5) * d - e) * R(1.0 / 6.0);
-    const R m = rmax(rmax(rmax(rabs(a), rabs(b)), rmax(rabs(c), rabs(d))), rabs(e));
-    if (m == R(0)) return R(0);
-    const R r = R(1) / m;
-    const R A = a * r, B = b * r, C = c * r, Dd = d * r, E = e * r;
-    const R t1 = A - R(2) * B + C, t2 = A - R(4) * B + R(3) * C;
-    const R t3 = B - R(2) * C + Dd, t4 = B - Dd;
-    const R t5 = C - R(2) * Dd + E, t6 = R(3) * C - R(4) * Dd + E;
-    const R s1 = R(13.0 / 12.0) * t1 * t1 + R(0.25) * t2 * t2;
-    const R s2 = R(13.0 / 12.0) * t3 * t3 + R(0.25) * t4 * t4;
-    const R s3 = R(13.0 / 12.0) * t5 * t5 + R(0.25) * t6 * t6;
-    const R smin = s1 < s2 ? (s1 < s3 ? s1 : s3) : (s2 < s3 ? s2 : s3);
-    R w1, w2, w3;
-    if (smin == R(0)) {
-        w1 = s1 == R(0) ? R(0.1) : R(0);
-        w2 = s2 == R(0) ? R(0.6) : R(0);
-        w3 = s3 == R(0) ? R(0.3) : R(0);
-    } else {
-        const R u1 = smin / s1, u2 = smin / s2, u3 = smin / s3;
-        w1 = R(0.1) * u1 * u1;
-        w2 = R(0.6) * u2 * u2;
-        w3 = R(0.3) * u3 * u3;
-    }
-    return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);
-}
-
-template <typename R>
-__device__ __forceinline__ R upwind2_face(R b, R c) { return R(1.5) * c - R(0.5) * b; }
-
-__device__ __forceinline__ int find_slot(const int* start, int n, int key) {
-    int lo = 0, hi = n;            // start[lo] <= key < start[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(start + mid) <= key) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Shared-memory layout of the stage kernel (sizes in elements).
 struct SmemLayout {
@@ -112,46 +47,11 @@ __host__ __device__ inline SmemLayout smem_layout(const GroupDev& g, int nwarps)
     L.offG = L.offF + g.V;
     size_t rbytes = (L.offG + L.nG) * sizeof(R);
     L.offD = (rbytes + 15) & ~size_t(15);
-    L.nRec = 3 * g.Nx + (g.Nx + 1);
+    L.nRec = 5 * g.Nx + 1;
     L.nCoef = 2 * (g.Nx + 1) + (g.Ny + 1) + (g.Nz + 1);
     // doubles: rec, coef, 8 scalars, 5 * nwarps reduction slots
     L.bytes = L.offD + sizeof(double) * (L.nRec + L.nCoef + 8 + 5 * nwarps);
     return L;
-}
-
-// Per-node equilibrium coefficients in FP64.  Thread role r:
-//   r = 0, 1: half-range G_l^{+-} (l <= Nx) by the recurrence in the
-//             orthonormal basis (see hlb_tables.cpp);
-//   r = 2:    full-range G_l along p_y;  r = 3: along p_z.
-__device__ void node_coefficients(const GroupDev& g, int r, double ux, double uy, double uz,
-                                  double T, const double* rec, double* coef) {
-    const int Nx = g.Nx;
-    if (r < 2) {
-        const double* ra = rec;
-        const double* rb = rec + Nx;
-        const double* rc = rec + 2 * Nx;
-        const double* h0 = rec + 3 * Nx;
-        double* G = coef + r * (Nx + 1);
-        const double us = r ? -ux : ux;
-        const double g0 = exp(-ux * ux / (2.0 * T)) / (kSqrt2Pi * sqrt(T));
-        G[0] = h0[0] * 0.5 * (1.0 + erf(us / sqrt(2.0 * T)));
-        double S = 0.0;
-        double gm1 = 0.0;
-        for (int l = 0; l < Nx; ++l) {
-            const double ig = (l ? gm1 / ra[l - 1] : 0.0) - kInvSqrt2Pi * h0[l] * S;
-            const double pg = us * G[l] + T * (g0 * h0[l] + ig);
-            G[l + 1] = ra[l] * pg + rb[l] * G[l] + rc[l] * gm1;
-            S += h0[l] * G[l];
-            gm1 = G[l];
-        }
-    } else {
-        const int N = r == 2 ? g.Ny : g.Nz;
-        const double u = r == 2 ? uy : uz;
-        double* G = coef + 2 * (Nx + 1) + (r == 2 ? 0 : g.Ny + 1);
-        G[0] = 1.0;
-        if (N >= 1) G[1] = u;
-        for (int l = 1; l < N; ++l) G[l + 1] = u * G[l] + l * (T - 1.0) * G[l - 1];
-    }
 }
 
 // Value of velocity v at x-position pos of a row (ghost rules at the walls).
