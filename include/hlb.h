@@ -138,6 +138,24 @@ hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q
  * enqueued on the handle's stream, no synchronisation, no non-finite check. */
 hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev);
 
+/* Same outputs as hlb_moments_dev, for callers that cannot allocate device
+ * memory at this point (an exhausted or capped memory pool, an allocator
+ * owned by another runtime, a loop that must stay out of the allocator).  The
+ * paper has no counterpart: this is a library service.  The call allocates
+ * nothing: its scratch is a static device array of 6 x 2^18 doubles (12 MiB)
+ * that every GPU which loads the library holds until the process exits.
+ * Limits and behaviour:
+ *  - each velocity-set group of the handle may have at most 262144 nodes;
+ *    larger handles get HLB_EINVAL and nothing is launched;
+ *  - the first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) once; make that first call before any stream
+ *    capture on that device;
+ *  - every call shares the one array: calls that overlap on the GPU (other
+ *    streams, other handles, other threads) race on it.  The array keeps the
+ *    last call's contents; each call overwrites all entries it later reads.
+ * Enqueued on the handle's stream; outputs are device arrays (NULL skips one). */
+hlb_status hlb_moments_noalloc(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev);
+
 /* Number of nodes and of values in the state (all instances), and the bytes
  * of one state copy.  Any output pointer may be NULL. */
 hlb_status hlb_sizes(const hlb_handle* h, long long* nodes, long long* values, long long* bytes);

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -887,3 +888,77 @@ hlb_status hlb_kernel_times(hlb_handle* h, double* stage_ms, long long* stage_la
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Moments without any allocation.
+//
+// Some callers cannot allocate device memory when they read the moments:
+// code that runs while a memory pool is exhausted or capped, a host that has
+// handed its allocator to another runtime, or a real-time loop that must not
+// enter the CUDA allocator at all.  hlb_moments_noalloc serves them: it runs
+// the same moments kernel as hlb_moments_dev, but its per-node scratch (six
+// doubles per node: n, u_x, u_y, u_z, T, q) is the static device array below
+// instead of memory owned by the handle, and it calls no cudaMalloc, no
+// cudaFree and no allocating library routine.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long kNoAllocMaxNodes = 1LL << 18;          // per group: 12 MiB of doubles
+
+// Shared by every call on a device, kept for the life of the process.
+static __device__ __align__(256) double g_noalloc_scratch[6 * kNoAllocMaxNodes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch on the current device (looked up once per
+// device; the host-side name of the array is only a stand-in).
+hlb_status noalloc_scratch(double** out) {
+    int dev = 0;
+    HLB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(HLB_EUNSUPPORTED, "device ordinal too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        HLB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return HLB_OK;
+}
+
+}  // namespace
+
+extern "C" hlb_status hlb_moments_noalloc(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev,
+                                          double* q_dev) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    for (auto& Gp : h->groups)
+        if (Gp->nnodes > kNoAllocMaxNodes)
+            return fail(HLB_EINVAL, "hlb_moments_noalloc: a group of this handle has " +
+                                        std::to_string(Gp->nnodes) + " nodes; this entry point handles at most " +
+                                        std::to_string(kNoAllocMaxNodes) +
+                                        " nodes per group (its static scratch holds 6 doubles per node)");
+    double* m = nullptr;
+    hlb_status st = noalloc_scratch(&m);
+    if (st != HLB_OK) return st;
+    // The kernel writes all six entries of every node of the group before
+    // they are read, so the scratch needs no clearing between calls.
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        const long long nn = G.nnodes;
+        hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + nn, m + 4 * nn, m + 5 * nn, 0, h->stream);
+        HLB_CUDA(cudaGetLastError());
+        for (size_t k = 0; k < G.members.size(); ++k) {
+            const int i = G.members[k];
+            const long long go = h->inst_node_off[i];
+            const long long lo = G.node_start[k];
+            const long long cnt = G.node_start[k + 1] - G.node_start[k];
+            if (n_dev) HLB_CUDA(cudaMemcpyAsync(n_dev + go, m + lo, cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+            if (u_dev) HLB_CUDA(cudaMemcpyAsync(u_dev + 3 * go, m + nn + 3 * lo, 3 * cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+            if (T_dev) HLB_CUDA(cudaMemcpyAsync(T_dev + go, m + 4 * nn + lo, cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+            if (q_dev) HLB_CUDA(cudaMemcpyAsync(q_dev + go, m + 5 * nn + lo, cnt * 8, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    return HLB_OK;
+}

@@ -56,6 +56,7 @@ SIGNATURES = {
     "hlb_step": (C.c_int, [_P, C.c_long]),
     "hlb_moments": (C.c_int, [_P, _D, _D, _D, _D]),
     "hlb_moments_dev": (C.c_int, [_P, _P, _P, _P, _P]),
+    "hlb_moments_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "hlb_sizes": (C.c_int, [_P, _LL, _LL, _LL]),
     "hlb_get_dt": (C.c_int, [_P, C.c_int, _D]),
     "hlb_get_nsteps": (C.c_int, [_P, _LL]),
@@ -180,6 +181,10 @@ class Handle:
 
     def moments_dev(self, n_ptr, u_ptr, T_ptr, q_ptr):
         _check(lib().hlb_moments_dev(self._h, n_ptr, u_ptr, T_ptr, q_ptr))
+
+    def moments_noalloc(self, n_ptr, u_ptr, T_ptr, q_ptr):
+        """hlb_moments_dev without any allocation (static device scratch)."""
+        _check(lib().hlb_moments_noalloc(self._h, n_ptr, u_ptr, T_ptr, q_ptr))
 
     def get_state(self, out: np.ndarray | None = None) -> np.ndarray:
         if out is None:
