@@ -52,7 +52,7 @@ struct Group {
     int cur = 0, prev = -1;
     DevBuf d_inst, d_node_start, d_row_start, d_K, d_p, d_pd, d_T, d_rec, d_dx, d_gw, d_nw, d_resid;
     DevBuf d_mom;                            // moments scratch: 6 doubles per node
-    DevBuf d_Td, d_invdx, d_wscale, d_coef, d_works, d_err;
+    DevBuf d_Td, d_invdx, d_wscale, d_coef, d_works, d_err, d_recf, d_Tf, d_sums;
     hlb::GroupDev dev{};
     int block = 256, grid = 1;
     size_t smem = 0;
@@ -194,8 +194,12 @@ void fill_dev(Group& G) {
     d.inv_dx = G.d_invdx.p;
     d.wscale = G.d_wscale.p;
     d.coef = G.d_coef.p;
+    d.sums = G.d_sums.p;
     d.ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
     d.err = (int*)G.d_err.p;
+    d.recf = (const float2*)G.d_recf.p;
+    d.Tf = (const float2*)G.d_Tf.p;
+    d.use_df = (G.precision == HLB_FP32 && G.Nx <= 11) ? 1 : 0;
 }
 
 hlb_status build_group(hlb_handle* h, Group& G) {
@@ -282,6 +286,18 @@ hlb_status build_group(hlb_handle* h, Group& G) {
             for (int i = 0; i < G.QX2; ++i)
                 wscale[(k * G.VY + j) * G.QX2 + i] = 1.0 / (G.tx.w[i] * G.ty.w[j] * G.tz.w[k]);
     hlb_status s;
+    {
+        auto split = [](const std::vector<double>& v) {
+            std::vector<float2> out(v.size());
+            for (size_t i = 0; i < v.size(); ++i) {
+                const float hi = (float)v[i];
+                out[i] = make_float2(hi, (float)(v[i] - (double)hi));
+            }
+            return out;
+        };
+        if ((s = upload(G.d_recf, split(rec))) != HLB_OK) return s;
+        if ((s = upload(G.d_Tf, split(T))) != HLB_OK) return s;
+    }
     if ((s = upload(G.d_Td, T)) != HLB_OK) return s;
     if ((s = upload_real(G.d_invdx, invdx, G.precision)) != HLB_OK) return s;
     if ((s = upload_real(G.d_wscale, wscale, G.precision)) != HLB_OK) return s;
@@ -313,7 +329,8 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     }
     {
         const int ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
-        if (cudaMalloc(&G.d_coef.p, std::max<size_t>((size_t)G.nnodes * ncp * G.esize, 16)) != cudaSuccess) {
+        if (cudaMalloc(&G.d_coef.p, std::max<size_t>((size_t)G.nnodes * ncp * G.esize, 16)) != cudaSuccess ||
+            cudaMalloc(&G.d_sums.p, std::max<size_t>((size_t)G.nnodes * 8 * G.esize, 16)) != cudaSuccess) {
             cudaGetLastError();
             return fail(HLB_ENOMEM, "cudaMalloc of the equilibrium factor lines failed");
         }
@@ -358,6 +375,7 @@ hlb_status build_group(hlb_handle* h, Group& G) {
             G.nworks = (int)works.size();
             if ((s = upload(G.d_works, works)) != HLB_OK) return s;
             HLB_CUDA(hlb::prepare_march(G.precision, G.adv, G.QX2, G.VY, G.TY));
+            HLB_CUDA(hlb::prepare_node());
         }
     }
     fill_dev(G);

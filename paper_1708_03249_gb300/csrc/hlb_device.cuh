@@ -108,6 +108,13 @@ __device__ __forceinline__ R upwind2_face(R b, R c) { return R(1.5) * c - R(0.5)
 // Tab. "weno": vanishing sigmas tie at the clamp and share weight in the
 // ratio of their delta_q, and the others get (1e-30/sigma)^2 ~ 0.
 // ---------------------------------------------------------------------------
+// 1/x on the special-function unit (|x| in [1e-30, 1e30] here).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float weno5_scaled(float a, float b, float c, float d, float e) {
     const float F1 = fmaf(11.0f / 6.0f, c, fmaf(-7.0f / 6.0f, b, (1.0f / 3.0f) * a));
     const float F2 = fmaf(1.0f / 3.0f, d, fmaf(5.0f / 6.0f, c, (-1.0f / 6.0f) * b));
@@ -119,9 +126,9 @@ __device__ __forceinline__ float weno5_scaled(float a, float b, float c, float d
     const float s2 = fmaxf(fmaf(13.0f / 12.0f * t3, t3, 0.25f * t4 * t4), 1e-30f);
     const float s3 = fmaxf(fmaf(13.0f / 12.0f * t5, t5, 0.25f * t6 * t6), 1e-30f);
     const float m = fminf(s1, fminf(s2, s3));
-    const float u1 = m * __fdividef(1.0f, s1), u2 = m * __fdividef(1.0f, s2), u3 = m * __fdividef(1.0f, s3);
+    const float u1 = m * rcp_approx(s1), u2 = m * rcp_approx(s2), u3 = m * rcp_approx(s3);
     const float w1 = 0.1f * u1 * u1, w2 = 0.6f * u2 * u2, w3 = 0.3f * u3 * u3;
-    return fmaf(w1, F1, fmaf(w2, F2, w3 * F3)) * __fdividef(1.0f, w1 + w2 + w3);
+    return fmaf(w1, F1, fmaf(w2, F2, w3 * F3)) * rcp_approx(w1 + w2 + w3);
 }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -144,15 +151,15 @@ __device__ __forceinline__ float2 weno5_scaled2(float2 a, float2 b, float2 c, fl
     const float2 s2 = make_float2(fmaxf(q2.x, 1e-30f), fmaxf(q2.y, 1e-30f));
     const float2 s3 = make_float2(fmaxf(q3.x, 1e-30f), fmaxf(q3.y, 1e-30f));
     const float2 m = make_float2(fminf(s1.x, fminf(s2.x, s3.x)), fminf(s1.y, fminf(s2.y, s3.y)));
-    const float2 u1 = __fmul2_rn(m, make_float2(__fdividef(1.0f, s1.x), __fdividef(1.0f, s1.y)));
-    const float2 u2 = __fmul2_rn(m, make_float2(__fdividef(1.0f, s2.x), __fdividef(1.0f, s2.y)));
-    const float2 u3 = __fmul2_rn(m, make_float2(__fdividef(1.0f, s3.x), __fdividef(1.0f, s3.y)));
+    const float2 u1 = __fmul2_rn(m, make_float2(rcp_approx(s1.x), rcp_approx(s1.y)));
+    const float2 u2 = __fmul2_rn(m, make_float2(rcp_approx(s2.x), rcp_approx(s2.y)));
+    const float2 u3 = __fmul2_rn(m, make_float2(rcp_approx(s3.x), rcp_approx(s3.y)));
     const float2 w1 = __fmul2_rn(__fmul2_rn(f2(0.1f), u1), u1);
     const float2 w2 = __fmul2_rn(__fmul2_rn(f2(0.6f), u2), u2);
     const float2 w3 = __fmul2_rn(__fmul2_rn(f2(0.3f), u3), u3);
     const float2 ws = __fadd2_rn(__fadd2_rn(w1, w2), w3);
     const float2 num = __ffma2_rn(w1, F1, __ffma2_rn(w2, F2, __fmul2_rn(w3, F3)));
-    return __fmul2_rn(num, make_float2(__fdividef(1.0f, ws.x), __fdividef(1.0f, ws.y)));
+    return __fmul2_rn(num, make_float2(rcp_approx(ws.x), rcp_approx(ws.y)));
 }
 
 __device__ __forceinline__ float2 upwind2_face2(float2 b, float2 c) {
@@ -210,6 +217,37 @@ __device__ inline void node_coefficients(const GroupDev& g, int r, double ux, do
         if (N >= 1) G[1] = u;
         for (int l = 1; l < N; ++l) G[l + 1] = u * G[l] + l * (T - 1.0) * G[l - 1];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (an unevaluated sum hi + lo of two FP32 numbers,
+// about 48 significant bits), built from the error-free transformations
+// TwoSum (Knuth) and TwoProduct by FMA.  Used for the per-node equilibrium
+// recurrence, whose rounding errors grow by ~1e4 over eight terms: FP32 is
+// too short and this GPU's FP64 rate is 1/64 of FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+    const float s = x.x + y.x;
+    const float bb = s - x.x;
+    const float e = (x.x - (s - bb)) + (y.x - bb);
+    return df_fast_two_sum(s, e + (x.y + y.y));
+}
+
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+    const float p = x.x * y.x;
+    float e = fmaf(x.x, y.x, -p);
+    e = fmaf(x.x, y.y, fmaf(x.y, y.x, e));
+    return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ float2 df_from_double(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
 }
 
 // ---------------------------------------------------------------------------
@@ -280,6 +318,68 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
         }
     }
     return true;
+}
+
+// The half-range coefficients G^{+-}_l (roles 0, 1) and the full-range ones
+// (roles 2: p_y, 3: p_z) of node_coefficients, in double-float.  recf holds
+// (hi, lo) pairs of ra, rb, rc, h0, 1/ra in the layout of rec; the values that
+// start the recurrence (erf, exp, sqrt) are formed in FP64 once.
+// Per-node inputs of node_coefficients_df, formed once per node in FP64:
+// ux, uy, uz, T, and for the half-range recurrence
+// E = erf(u_x / sqrt(2T)) and g(0) = exp(-u_x^2 / 2T) / sqrt(2 pi T).
+struct NodeDF {
+    float2 ux, uy, uz, T, Tm1, erf_z, g0, n;
+};
+
+__device__ inline void node_inputs_df(double n, double ux, double uy, double uz, double T, NodeDF& o) {
+    o.n = df_from_double(n);
+    o.ux = df_from_double(ux);
+    o.uy = df_from_double(uy);
+    o.uz = df_from_double(uz);
+    o.T = df_from_double(T);
+    o.Tm1 = df_from_double(T - 1.0);
+    const double rt = sqrt(T);
+    o.erf_z = df_from_double(erf(ux / (1.4142135623730951 * rt)));
+    o.g0 = df_from_double(exp(-ux * ux / (2.0 * T)) / (kSqrt2Pi * rt));
+}
+
+// The half-range coefficients G^{+-}_l (roles 0, 1) and the full-range ones
+// (roles 2: p_y, 3: p_z) of node_coefficients, in double-float; recf holds
+// (hi, lo) pairs of ra, rb, rc, h0, 1/ra in the layout of rec.
+__device__ inline void node_coefficients_df(const GroupDev& g, int r, const NodeDF& in, const float2* recf,
+                                            float2* coef) {
+    const int Nx = g.Nx;
+    // same slots as node_coefficients: G^+ | G^- | G_y | G_z
+    float2* G = coef + (r < 2 ? r * (Nx + 1) : 2 * (Nx + 1) + (r == 2 ? 0 : g.Ny + 1));
+    if (r < 2) {
+        const float2* ra = recf;
+        const float2* rb = recf + Nx;
+        const float2* rc = recf + 2 * Nx;
+        const float2* h0 = recf + 3 * Nx;
+        const float2* inv_ra = recf + 4 * Nx + 1;
+        const float sg = r ? -1.0f : 1.0f;
+        const float2 us = make_float2(sg * in.ux.x, sg * in.ux.y);
+        // int_0^inf g(+-p) dp = (1 +- erf(u_x/sqrt(2T)))/2, with h_0 = h0[0]
+        const float2 half = df_add(make_float2(0.5f, 0.0f), make_float2(0.5f * sg * in.erf_z.x, 0.5f * sg * in.erf_z.y));
+        G[0] = df_mul(h0[0], half);
+        const float2 m_om0 = make_float2(-3.989422917e-01f, 1.133517014e-08f);   // -1/sqrt(2 pi)
+        float2 S = make_float2(0.0f, 0.0f), gm1 = make_float2(0.0f, 0.0f);
+        for (int l = 0; l < Nx; ++l) {
+            float2 ig = df_mul(df_mul(m_om0, h0[l]), S);
+            if (l) ig = df_add(ig, df_mul(gm1, inv_ra[l - 1]));
+            const float2 pg = df_add(df_mul(us, G[l]), df_mul(in.T, df_add(df_mul(in.g0, h0[l]), ig)));
+            G[l + 1] = df_add(df_add(df_mul(ra[l], pg), df_mul(rb[l], G[l])), df_mul(rc[l], gm1));
+            S = df_add(S, df_mul(h0[l], G[l]));
+            gm1 = G[l];
+        }
+    } else {
+        const int N = r == 2 ? g.Ny : g.Nz;
+        const float2 u = r == 2 ? in.uy : in.uz;
+        G[0] = make_float2(1.0f, 0.0f);
+        if (N >= 1) G[1] = u;
+        for (int l = 1; l < N; ++l)
+            G[l + 1] = df_add(df_mul(u, G[l]), df_mul(df_mul(make_float2((float)l, 0.0f), in.Tm1), G[l - 1]));
+    }
 }
 
 }  // namespace hlb

@@ -1,6 +1,8 @@
 // Internal declarations shared by the host tables, the API and the kernels.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -68,6 +70,7 @@ struct GroupDev {
     int V, QX2, VY, VZ, Qx, Nx, Ny, Nz, Qy, Qz, D;
     int ncp;                 // stride of a node's equilibrium-factor line
     void* coef;              // R: [node][ncp] = g_x * n (QX2), g_y (VY), g_z (VZ), 1/tau
+    void* sums;              // R: [node][8] = n, j_x, j_y, j_z, E of the stage input
     const void* inv_dx;      // R: 1/dx, concatenated per instance (same offsets as dx)
     const void* wscale;      // R: [V] 1/(w_x w_y w_z) per velocity (WENO smoothness scale)
     int ninst, nnodes, nrows;
@@ -80,6 +83,9 @@ struct GroupDev {
     const void* Tt;          // R: Tx [Qx (Nx+1)], Ty [VY (Ny+1)], Tz [VZ (Nz+1)]
     const double* rec;       // FP64: ra[Nx], rb[Nx], rc[Nx], h0[Nx+1], 1/ra[Nx]
     const double* Td;        // FP64 copies of Tx, Ty, Tz
+    const float2* recf;      // double-float (hi, lo) copies of rec
+    const float2* Tf;        // double-float (hi, lo) copies of Tx, Ty, Tz
+    int use_df;              // FP32 groups with Nx <= 11: equilibrium in double-float
     const double* dx;        // FP64 x-cell widths, concatenated per instance
     const void* gw;          // R: wall Maxwellians
     double* nw;              // FP64 [nrows][2] emitted densities
@@ -98,6 +104,7 @@ void launch_stage(int precision, int adv, const GroupDev& g, const void* fs, con
                   int stage, int grid, int block, size_t smem, cudaStream_t st);
 void launch_wall(int precision, int adv, const GroupDev& g, const void* fs, cudaStream_t st);
 void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t st);
+cudaError_t prepare_node();
 // Marching stage kernel for (QX2, VY, TY); returns false if no instantiation exists.
 bool march_available(int precision, int adv, int QX2, int VY, int TY);
 cudaError_t prepare_march(int precision, int adv, int QX2, int VY, int TY);

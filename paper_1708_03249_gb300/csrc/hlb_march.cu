@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "hlb_device.cuh"
 #include "hlb_internal.h"
@@ -31,130 +32,220 @@ namespace {
 // ---------------------------------------------------------------------------
 // node kernel
 // ---------------------------------------------------------------------------
-// Node batch of one CTA.  FP64 runs at 1/64 of FP32 on this GPU and a warp
-// instruction costs the same whatever its active mask, so the FP64 work
-// (recurrences, dot products) is batched so that every lane is busy.
-constexpr int kNodeBatch = 32;
-
+// Per-node equilibrium factors, in two passes with no block-wide barrier:
+//   sums_kernel   streams the stage input once (one warp per node) and writes
+//                 the five quadrature sums n, j_x, j_y, j_z, E per node;
+//   coef_kernel   one warp per 32 nodes, one lane per node: n, u, T, then the
+//                 coefficient recurrences of all four roles, then the factor
+//                 line (dot products shared across the warp).
+// FP64 runs at 1/64 of FP32 here and a warp instruction costs the same
+// whatever its mask, so every FP64 instruction runs on full warps; FP32
+// groups with Nx <= 11 run the recurrences and dot products in double-float
+// (FP64 only for erf, exp, sqrt, once per node).
 template <typename R>
-__global__ void __launch_bounds__(256) node_kernel(const GroupDev g, const R* __restrict__ fs) {
-    extern __shared__ __align__(16) double nsm[];
-    const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz;
-    const int nrec = 5 * Nx + 1;
-    const int nT = g.Qx * (Nx + 1) + g.VY * (Ny + 1) + g.VZ * (Nz + 1);
-    const int ncoef = 2 * (Nx + 1) + (Ny + 1) + (Nz + 1);
+__global__ void __launch_bounds__(256) sums_kernel(const GroupDev g, const R* __restrict__ fs, R* __restrict__ sums) {
+    extern __shared__ __align__(16) double ssm[];
+    using R4 = typename std::conditional<sizeof(R) == 4, float4, double4>::type;
     const int QX2 = g.QX2, VY = g.VY, VZ = g.VZ, V = g.V;
     const int tid = threadIdx.x, bs = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = bs >> 5;
-    // shared: moment weights, FP64 tables, per-node sums / state / coefficients
-    R* sM = reinterpret_cast<R*>(nsm);
-    double* sRec = nsm + (4 * V * sizeof(R) + 7) / 8;
-    double* sT = sRec + nrec;
-    double* sSum = sT + nT;                              // [kNodeBatch][5]
-    double* sState = sSum + 5 * kNodeBatch;              // [kNodeBatch][6]: n, ux, uy, uz, T, 1/tau
-    double* sG = sState + 6 * kNodeBatch;                // [kNodeBatch][ncoef]
+    R4* sM = reinterpret_cast<R4*>(ssm);                 // [V]: p_x, p_y, p_z, |p|^2
+    R4* sYZ = sM + V;                                    // [VY * VZ]: p_y, p_z, p_y^2 + p_z^2
     const R* px = static_cast<const R*>(g.p);
     const R* py = px + QX2;
     const R* pz = py + VY;
     for (int v = tid; v < V; v += bs) {
         const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
         const R a = px[ix], b = py[jy], c = pz[kz];
-        sM[4 * v + 0] = a;
-        sM[4 * v + 1] = b;
-        sM[4 * v + 2] = c;
-        sM[4 * v + 3] = a * a + b * b + c * c;
+        R4 m4;
+        m4.x = a; m4.y = b; m4.z = c; m4.w = a * a + b * b + c * c;
+        sM[v] = m4;
     }
-    for (int i = tid; i < nrec; i += bs) sRec[i] = g.rec[i];
-    for (int i = tid; i < nT; i += bs) sT[i] = g.Td[i];
+    for (int bq = tid; bq < VY * VZ; bq += bs) {
+        const R b = py[bq % VY], c = pz[bq / VY];
+        R4 y4;
+        y4.x = b; y4.y = c; y4.z = b * b + c * c; y4.w = R(0);
+        sYZ[bq] = y4;
+    }
+    __syncthreads();
+    // 4-vector loads need 4 | 2Qx and 2Qx | 128 (2Qx a power of two up to 128):
+    // then 4 consecutive velocities share (jy, kz) and a lane's p_x never change
+    const bool vec4 = (QX2 & 3) == 0 && (QX2 & (QX2 - 1)) == 0 && QX2 <= 128;
+    for (int node = blockIdx.x * nw + warp; node < g.nnodes; node += gridDim.x * nw) {
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const InstDev& I = g.inst[ii];
+        const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+        if (vec4) {
+            const R4* f4 = reinterpret_cast<const R4*>(f);
+            const int x0 = (4 * lane) % QX2;
+            const R pxa = sM[x0].x, pxb = sM[x0 + 1].x, pxc = sM[x0 + 2].x, pxd = sM[x0 + 3].x;
+#pragma unroll 4
+            for (int q = lane; q < (V >> 2); q += 32) {
+                const R4 x = f4[q];
+                const R4 yz = sYZ[(q << 2) / QX2];
+                const R s = (x.x + x.y) + (x.z + x.w);
+                a0 += s;
+                a1 += pxa * x.x + pxb * x.y + pxc * x.z + pxd * x.w;
+                a2 += yz.x * s;
+                a3 += yz.y * s;
+                a4 += pxa * pxa * x.x + pxb * pxb * x.y + pxc * pxc * x.z + pxd * pxd * x.w + yz.z * s;
+            }
+        } else {
+            for (int v = lane; v < V; v += 32) {
+                const R val = f[v];
+                const R4 mw = sM[v];
+                a0 += val;
+                a1 += mw.x * val;
+                a2 += mw.y * val;
+                a3 += mw.z * val;
+                a4 += mw.w * val;
+            }
+        }
+        a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
+        if (lane == 0) {
+            R* o = sums + (size_t)node * 8;
+            o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = a4;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __restrict__ sums) {
+    extern __shared__ __align__(16) double csm[];
+    const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz;
+    const int nrec = 5 * Nx + 1;
+    const int nT = g.Qx * (Nx + 1) + g.VY * (Ny + 1) + g.VZ * (Nz + 1);
+    const int ncoef = 2 * (Nx + 1) + (Ny + 1) + (Nz + 1);
+    const int QX2 = g.QX2, VY = g.VY, VZ = g.VZ;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = bs >> 5;
+    const bool df = g.use_df != 0;
+    double* sRec = csm;
+    double* sT = sRec + nrec;
+    double* sW = sT + nT;                                // per warp: [32][ncoef] coefficients + [32] state
+    const int per_warp = 32 * ncoef + 32 * 2 + 32 * (int)(sizeof(NodeDF) / 8);
+    double* sG = sW + warp * per_warp;
+    double* sNT = sG + 32 * ncoef;                       // [32][2]: n, 1/tau
+    NodeDF* sIn = reinterpret_cast<NodeDF*>(sNT + 64);   // [32]
+    float2* sRecF = reinterpret_cast<float2*>(sRec);
+    float2* sTF = reinterpret_cast<float2*>(sT);
+    float2* sGF = reinterpret_cast<float2*>(sG);
+    if (df) {
+        for (int i = tid; i < nrec; i += bs) sRecF[i] = g.recf[i];
+        for (int i = tid; i < nT; i += bs) sTF[i] = g.Tf[i];
+    } else {
+        for (int i = tid; i < nrec; i += bs) sRec[i] = g.rec[i];
+        for (int i = tid; i < nT; i += bs) sT[i] = g.Td[i];
+    }
     __syncthreads();
     const double* sTx = sT;
     const double* sTy = sTx + g.Qx * (Nx + 1);
     const double* sTz = sTy + VY * (Ny + 1);
+    const float2* sTxF = sTF;
+    const float2* sTyF = sTxF + g.Qx * (Nx + 1);
+    const float2* sTzF = sTyF + VY * (Ny + 1);
     R* coef = static_cast<R*>(g.coef);
     const int nf = QX2 + VY + VZ;
-
-    for (int base = blockIdx.x * kNodeBatch; base < g.nnodes; base += gridDim.x * kNodeBatch) {
-        const int nb = min(kNodeBatch, g.nnodes - base);
-        // 1. moment sums: one warp per node, FP32 lanes, pairwise tree
-        for (int k = warp; k < nb; k += nw) {
-            const int node = base + k;
+    const int nbatches = (g.nnodes + 31) / 32;
+    for (int bt = blockIdx.x * nw + warp; bt < nbatches; bt += gridDim.x * nw) {
+        const int base = bt * 32;
+        const int nb = min(32, g.nnodes - base);
+        // 1. lane = node: n, u, T, 1/tau; the recurrences' FP64 inputs
+        bool active = false;
+        if (lane < nb) {
+            const int node = base + lane;
             const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
-            const InstDev& I = g.inst[ii];
-            const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
-            R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-            for (int v = lane; v < V; v += 32) {
-                const R val = f[v];
-                const R* mw = sM + 4 * v;
-                a0 += val;
-                a1 += mw[0] * val;
-                a2 += mw[1] * val;
-                a3 += mw[2] * val;
-                a4 += mw[3] * val;
-            }
-            a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
-            if (lane == 0) {
-                double* sm = sSum + 5 * k;
-                sm[0] = a0; sm[1] = a1; sm[2] = a2; sm[3] = a3; sm[4] = a4;
-            }
-        }
-        __syncthreads();
-        // 2. n, u, T, 1/tau per node (one lane per node)
-        if (tid < nb) {
-            const int node = base + tid;
-            const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
-            const double* sm = sSum + 5 * tid;
-            const double n = sm[0];
-            const double ux = sm[1] / n, uy = sm[2] / n, uz = sm[3] / n;
-            double* st = sState + 6 * tid;
-            st[0] = n; st[1] = ux; st[2] = uy; st[3] = uz;
-            st[4] = (sm[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
-            st[5] = n * g.inst[ii].inv_Kn;
-        }
-        __syncthreads();
-        // 3. coefficients: lane per (node, role); roles 0/1 = half-range G^{+-},
-        //    2 = full-range p_y, 3 = p_z.  Consecutive lanes share a role.
-        for (int t = tid; t < 4 * nb; t += bs) {
-            const int role = t / nb, k = t - role * nb;
-            const double* st = sState + 6 * k;
-            if (st[5] != 0.0) node_coefficients(g, role, st[1], st[2], st[3], st[4], sRec, sG + k * ncoef);
-        }
-        __syncthreads();
-        // 4. factor lines: lane per (node, output)
-        for (int t = tid; t < nb * (nf + 1); t += bs) {
-            const int k = t / (nf + 1), o = t - k * (nf + 1);
-            const double* st = sState + 6 * k;
-            const double* G = sG + k * ncoef;
-            R* line = coef + (size_t)(base + k) * g.ncp;
-            double acc = 0.0;
-            if (st[5] == 0.0) {                  // collisionless: no equilibrium at all
-                acc = 0.0;
-            } else if (o < QX2) {
-                const int kk = o % g.Qx, sg = o / g.Qx;
-                const double* Gs = G + sg * (Nx + 1);
-                for (int l = 0; l <= Nx; ++l) acc += sTx[kk * (Nx + 1) + l] * Gs[l];
-                acc *= st[0];
-            } else if (o < QX2 + VY) {
-                const int j = o - QX2;
-                if (g.Qy) {
-                    const double* Gy = G + 2 * (Nx + 1);
-                    for (int l = 0; l <= Ny; ++l) acc += sTy[j * (Ny + 1) + l] * Gy[l];
-                } else {
-                    acc = 1.0;
-                }
-            } else if (o < nf) {
-                const int j = o - QX2 - VY;
-                if (g.Qz) {
-                    const double* Gz = G + 2 * (Nx + 1) + (Ny + 1);
-                    for (int l = 0; l <= Nz; ++l) acc += sTz[j * (Nz + 1) + l] * Gz[l];
-                } else {
-                    acc = 1.0;
-                }
+            const double inv_Kn = g.inst[ii].inv_Kn;
+            const R* sm = sums + (size_t)node * 8;
+            active = inv_Kn != 0.0;
+            double ux, uy, uz, T, n;
+            if (df) {
+                const float nf32 = (float)sm[0];
+                const float fx = (float)sm[1] / nf32, fy = (float)sm[2] / nf32, fz = (float)sm[3] / nf32;
+                const float fT = ((float)sm[4] - nf32 * (fx * fx + fy * fy + fz * fz)) / (g.D * nf32);
+                n = nf32; ux = fx; uy = fy; uz = fz; T = fT;
             } else {
-                acc = st[5];
+                n = (double)sm[0];
+                ux = (double)sm[1] / n; uy = (double)sm[2] / n; uz = (double)sm[3] / n;
+                T = ((double)sm[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
             }
-            line[o] = (R)acc;
+            sNT[2 * lane] = n;
+            sNT[2 * lane + 1] = n * inv_Kn;
+            if (active) {
+                if (df) {
+                    node_inputs_df(n, ux, uy, uz, T, sIn[lane]);
+                    for (int role = 0; role < 4; ++role)
+                        node_coefficients_df(g, role, sIn[lane], sRecF, sGF + lane * ncoef);
+                } else {
+                    for (int role = 0; role < 4; ++role)
+                        node_coefficients(g, role, ux, uy, uz, T, sRec, sG + lane * ncoef);
+                }
+            }
         }
-        __syncthreads();
+        __syncwarp();
+        // 2. factor lines: lanes over (node, output), one loop per output kind
+        //    so that the lanes of a warp follow the same path
+        for (int t = lane; t < nb * QX2; t += 32) {          // n g_x
+            const int k = t / QX2, o = t - k * QX2;
+            R* line = coef + (size_t)(base + k) * g.ncp;
+            if (sNT[2 * k + 1] == 0.0) { line[o] = R(0); continue; }
+            const int kk = o % g.Qx, sg = o / g.Qx;
+            if (df) {
+                const float2* Gs = sGF + k * ncoef + sg * (Nx + 1);
+                const float2* Tr = sTxF + kk * (Nx + 1);
+                float2 acc = df_mul(Tr[0], Gs[0]);
+                for (int l = 1; l <= Nx; ++l) acc = df_add(acc, df_mul(Tr[l], Gs[l]));
+                acc = df_mul(acc, sIn[k].n);
+                line[o] = (R)(acc.x + acc.y);
+            } else {
+                const double* Gs = sG + k * ncoef + sg * (Nx + 1);
+                const double* Tr = sTx + kk * (Nx + 1);
+                double acc = 0.0;
+                for (int l = 0; l <= Nx; ++l) acc += Tr[l] * Gs[l];
+                line[o] = (R)(acc * sNT[2 * k]);
+            }
+        }
+        for (int t = lane; t < nb * VY; t += 32) {           // g_y
+            const int k = t / VY, j = t - k * VY;
+            R* line = coef + (size_t)(base + k) * g.ncp + QX2;
+            if (sNT[2 * k + 1] == 0.0) { line[j] = R(0); continue; }
+            if (!g.Qy) { line[j] = R(1); continue; }
+            if (df) {
+                const float2* Gy = sGF + k * ncoef + 2 * (Nx + 1);
+                const float2* Tr = sTyF + j * (Ny + 1);
+                float2 acc = df_mul(Tr[0], Gy[0]);
+                for (int l = 1; l <= Ny; ++l) acc = df_add(acc, df_mul(Tr[l], Gy[l]));
+                line[j] = (R)(acc.x + acc.y);
+            } else {
+                const double* Gy = sG + k * ncoef + 2 * (Nx + 1);
+                const double* Tr = sTy + j * (Ny + 1);
+                double acc = 0.0;
+                for (int l = 0; l <= Ny; ++l) acc += Tr[l] * Gy[l];
+                line[j] = (R)acc;
+            }
+        }
+        for (int t = lane; t < nb * VZ; t += 32) {           // g_z
+            const int k = t / VZ, j = t - k * VZ;
+            R* line = coef + (size_t)(base + k) * g.ncp + QX2 + VY;
+            if (sNT[2 * k + 1] == 0.0) { line[j] = R(0); continue; }
+            if (!g.Qz) { line[j] = R(1); continue; }
+            if (df) {
+                const float2* Gz = sGF + k * ncoef + 2 * (Nx + 1) + (Ny + 1);
+                const float2* Tr = sTzF + j * (Nz + 1);
+                float2 acc = df_mul(Tr[0], Gz[0]);
+                for (int l = 1; l <= Nz; ++l) acc = df_add(acc, df_mul(Tr[l], Gz[l]));
+                line[j] = (R)(acc.x + acc.y);
+            } else {
+                const double* Gz = sG + k * ncoef + 2 * (Nx + 1) + (Ny + 1);
+                const double* Tr = sTz + j * (Nz + 1);
+                double acc = 0.0;
+                for (int l = 0; l <= Nz; ++l) acc += Tr[l] * Gz[l];
+                line[j] = (R)acc;
+            }
+        }
+        if (lane < nb) coef[(size_t)(base + lane) * g.ncp + nf] = (R)sNT[2 * lane + 1];   // 1/tau
+        __syncwarp();
     }
 }
 
@@ -405,7 +496,7 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
 // holds values pre-multiplied by the population's inverse weight so that
 // every WENO evaluation reads scaled stencils directly.
 template <int ADV, int QX2, int VY>
-__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? 4 : 1)))
+__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? 5 : 1)))
 march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
               const float* __restrict__ fn, float* __restrict__ fo, int stage) {
     constexpr int TY = 2;
@@ -420,20 +511,35 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     const Work W = works[blockIdx.x];
     const InstDev& I = g.inst[W.inst];
     const int t = threadIdx.x;
-    const int ix = t % QX2, jy = t / QX2, kz = W.kz;
+    // Thread -> velocity: when a sign quadrant of (p_x, p_y) fills whole warps,
+    // each warp takes one quadrant, so the stencil orientation below is
+    // warp-uniform; otherwise ix runs fastest.
+    constexpr int QH = QX2 / 2, YH = VY >= 2 ? VY / 2 : 1;
+    constexpr bool kQuad = VY >= 2 && (QH * YH) % 32 == 0;
+    int ix, jy;
+    if (kQuad) {
+        const int q = t / (QH * YH), rr = t % (QH * YH);
+        ix = (q >> 1) * QH + rr % QH;
+        jy = (q & 1) * YH + rr / QH;
+    } else {
+        ix = t % QX2;
+        jy = t / QX2;
+    }
+    const int kz = W.kz;
+    const int vl = jy * QX2 + ix;                  // velocity within the slab
     const int V = g.V, nx = I.nx, ny = I.ny, ncp = g.ncp;
-    const int v = (kz * VY + jy) * QX2 + ix;
+    const int v = kz * S + vl;
     const float* P = static_cast<const float*>(g.p);
     const float vx = P[ix], vy = P[QX2 + jy];
     const bool xpos = ix < QX, ypos = vy > 0.0f;
     const float sv = static_cast<const float*>(g.wscale)[v];
     const float isv = 1.0f / sv;
     const float* K = static_cast<const float*>(g.K);
-    float2 kx[QX2], ky[VY];
+    float kx[QX2], ky[VY];
 #pragma unroll
-    for (int i = 0; i < QX2; ++i) kx[i] = f2(K[ix * QX2 + i]);
+    for (int i = 0; i < QX2; ++i) kx[i] = K[ix * QX2 + i];
 #pragma unroll
-    for (int j = 0; j < VY; ++j) ky[j] = f2(K[QX2 * QX2 + jy * VY + j]);
+    for (int j = 0; j < VY; ++j) ky[j] = K[QX2 * QX2 + jy * VY + j];
     const float2 ax2 = f2((float)I.ax), ay2 = f2((float)I.ay), dt2 = f2((float)I.dt);
     const float2 vxs = f2(vx * isv), vys = f2(vy * isv * (float)I.inv_dy), isv2 = f2(isv);
     const float* invdx = static_cast<const float*>(g.inv_dx) + I.dx_off;
@@ -524,9 +630,11 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
 #pragma unroll
     for (int j = 0; j < 6; ++j) w[j] = make_float2(wr[0][j], wr[1][j]);
     auto xface = [&](const float2* c) -> float2 {
-        const float2 a = xpos ? c[0] : c[5], b = xpos ? c[1] : c[4], cc = xpos ? c[2] : c[3],
-                     d = xpos ? c[3] : c[2], e = xpos ? c[4] : c[1];
-        return ADV == HLB_WENO5_ ? weno5_scaled2(a, b, cc, d, e) : upwind2_face2(b, cc);
+        if (ADV == HLB_WENO5_) {
+            if (xpos) return weno5_scaled2(c[0], c[1], c[2], c[3], c[4]);
+            return weno5_scaled2(c[5], c[4], c[3], c[2], c[1]);
+        }
+        return xpos ? upwind2_face2(c[1], c[2]) : upwind2_face2(c[4], c[3]);
     };
     float2 Fm = __fmul2_rn(vxs, xface(w));
 
@@ -539,14 +647,14 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
 #pragma unroll
         for (int j = 0; j < 5; ++j) w[j] = w[j + 1];
         const int h = x + 3;
-        if (h < nx) w[5] = __fmul2_rn(make_float2(B.head[0][t], B.head[1][t]), f2(sv));
+        if (h < nx) w[5] = __fmul2_rn(make_float2(B.head[0][vl], B.head[1][vl]), f2(sv));
         else if (!xpos) w[5] = make_float2(nwr_g[0], nwr_g[1]);
         else if (h == nx) w[5] = __ffma2_rn(f2(3.0f), __fadd2_rn(w[4], __fmul2_rn(f2(-1.0f), w[3])), w[2]);
         else if (h == nx + 1)
             w[5] = __ffma2_rn(f2(6.0f), w[3], __ffma2_rn(f2(-8.0f), w[2], __fmul2_rn(f2(3.0f), w[1])));
         else w[5] = f2(0.0f);
         const float2 fc = __fmul2_rn(w[2], isv2);
-        sF[b * S + t] = fc;
+        sF[b * S + vl] = fc;
         // x faces
         const float2 Fp = __fmul2_rn(vxs, xface(w));
         const float2 divx = __fmul2_rn(__fadd2_rn(Fp, __fmul2_rn(f2(-1.0f), Fm)), f2(invdx[x]));
@@ -554,11 +662,11 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
         // y faces (periodic): rows y0-3 .. y0+4 of column x, scaled
         float col[8];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) col[k] = B.halo[k][t] * sv;
+        for (int k = 0; k < 3; ++k) col[k] = B.halo[k][vl] * sv;
         col[3] = w[2].x;
         col[4] = w[2].y;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) col[5 + k] = B.halo[3 + k][t] * sv;
+        for (int k = 0; k < 3; ++k) col[5 + k] = B.halo[3 + k][vl] * sv;
         float2 G01;
         float G2;
         if (ADV == HLB_WENO5_) {
@@ -586,9 +694,17 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
         const float2* fr = sF + b * S;
         float2 kxf = f2(0.0f), kyf = f2(0.0f);
 #pragma unroll
-        for (int i = 0; i < QX2; ++i) kxf = __ffma2_rn(kx[i], fr[jy * QX2 + i], kxf);
+        for (int i = 0; i < QX2; ++i) {
+            const float2 fv = fr[jy * QX2 + i];
+            kxf.x = fmaf(kx[i], fv.x, kxf.x);
+            kxf.y = fmaf(kx[i], fv.y, kxf.y);
+        }
 #pragma unroll
-        for (int j = 0; j < VY; ++j) kyf = __ffma2_rn(ky[j], fr[j * QX2 + ix], kyf);
+        for (int j = 0; j < VY; ++j) {
+            const float2 fv = fr[j * QX2 + ix];
+            kyf.x = fmaf(ky[j], fv.x, kyf.x);
+            kyf.y = fmaf(ky[j], fv.y, kyf.y);
+        }
         const float* c0 = B.coef[0];
         const float* c1 = B.coef[1];
         const float2 feq = make_float2(c0[ix] * c0[QX2 + jy] * c0[csrc_z], c1[ix] * c1[QX2 + jy] * c1[csrc_z]);
@@ -603,7 +719,7 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
         if (stage == 0) {
             out = __ffma2_rn(dt2, L, fc);
         } else {
-            const float2 fo_n = make_float2(B.fnr[0][t], B.fnr[1][t]);
+            const float2 fo_n = make_float2(B.fnr[0][vl], B.fnr[1][vl]);
             if (stage == 1)
                 out = __ffma2_rn(f2(0.75f), fo_n, __fmul2_rn(f2(0.25f), __ffma2_rn(dt2, L, fc)));
             else
@@ -619,17 +735,38 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t prepare_node() {
+    cudaError_t e = cudaFuncSetAttribute(coef_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sums_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sums_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+}
+
+// Node pass of a stage: the quadrature sums of every node, then the factor
+// lines.  The sums live in the first 8 R of each node's factor line slot of
+// an auxiliary buffer (g.sums).
 void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t st) {
-    const int block = 256;
+    const size_t es = precision == HLB_FP64_ ? 8 : 4;
+    const size_t smem_a = 4 * (g.V + g.VY * g.VZ) * es;
+    const int blocks_a = (g.nnodes + 7) / 8 < 152 * 16 ? (g.nnodes + 7) / 8 : 152 * 16;
     const int nrec = 5 * g.Nx + 1;
     const int nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
     const int ncoef = 2 * (g.Nx + 1) + (g.Ny + 1) + (g.Nz + 1);
-    const size_t smem = (4 * g.V * (precision == HLB_FP64_ ? 8 : 4) + 7) / 8 * 8 +
-                        sizeof(double) * (nrec + nT + kNodeBatch * (5 + 6 + ncoef));
-    const int batches = (g.nnodes + kNodeBatch - 1) / kNodeBatch;
-    const int grid = batches < 152 * 8 ? batches : 152 * 8;
-    if (precision == HLB_FP64_) node_kernel<double><<<grid, block, smem, st>>>(g, (const double*)fs);
-    else node_kernel<float><<<grid, block, smem, st>>>(g, (const float*)fs);
+    const int block_b = 32;
+    const size_t per_warp = 8 * (32 * ncoef + 64) + 32 * sizeof(NodeDF);
+    const size_t smem_b = 8 * (nrec + nT) + (block_b / 32) * per_warp;
+    const int batches = (g.nnodes + 31) / 32;
+    const int blocks_b = batches;
+    if (precision == HLB_FP64_) {
+        sums_kernel<double><<<blocks_a, 256, smem_a, st>>>(g, (const double*)fs, (double*)g.sums);
+        coef_kernel<double><<<blocks_b, block_b, smem_b, st>>>(g, (const double*)g.sums);
+    } else {
+        sums_kernel<float><<<blocks_a, 256, smem_a, st>>>(g, (const float*)fs, (float*)g.sums);
+        coef_kernel<float><<<blocks_b, block_b, smem_b, st>>>(g, (const float*)g.sums);
+    }
 }
 
 #define HLB_MARCH_LIST(X)                                                              \
