@@ -37,7 +37,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("hlb_kernels.cu", "hlb_internal.h"):
+    for name in ("hlb_march.cu", "hlb_device.cuh", "hlb_internal.h"):
         with open(os.path.join(ROOT, "paper_1708_03249_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -120,12 +120,12 @@ def oracle_sample(steps: int = 1, nx: int = 32, ny: int = 32):
     s = Solver(config_from(cfg))
     s.init_equilibrium(1.0, 0.05, -0.02, 1.2)
     s.f *= W.perturbation(s.f.shape, seed=3, amplitude=0.02)
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     s.step(steps)
-    dt = time.perf_counter() - t0
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
     nv = nx * ny * s.vs.V * steps
     desc = f"{nx}x{ny} nodes of the workload's velocity set x {steps} RK-3 step(s), FP64 numpy oracle"
-    return nv / dt, dt, desc
+    return nv / dt, dt, desc, max(1, round(cpu / dt))
 
 
 def run_reference(args):
@@ -134,8 +134,9 @@ def run_reference(args):
         return
     total_nv, total_t = 0.0, 0.0
     desc = ""
+    cores = 1
     for i in range(args.warmup + args.steps):
-        rate, secs, desc = oracle_sample(steps=1)
+        rate, secs, desc, cores = oracle_sample(steps=1)
         if i >= args.warmup:
             total_nv += rate * secs
             total_t += secs
@@ -146,7 +147,7 @@ def run_reference(args):
         "ms_per_step": 1e3 * total_t / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": desc},
-        "cpu_baseline": {"value": value, "unit": "node-velocity updates/s", "cores": 1,
+        "cpu_baseline": {"value": value, "unit": "node-velocity updates/s", "cores": cores,
                          "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "node-velocity updates/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -179,6 +180,12 @@ def run_gpu(args):
             dist.barrier()
     stream = torch.cuda.Stream()
     cfg = W.LARGE_2D
+    workload = WORKLOAD
+    if args.nx or args.ny:        # a smaller grid of the same workload (profiling captures)
+        nx = args.nx or cfg["nx"]
+        ny = args.ny or cfg["ny"]
+        cfg = W.scaled(cfg, nx=nx, ny=ny, Ly=cfg["Ly"] * ny / cfg["ny"], Lx=cfg["Lx"] * nx / cfg["nx"])
+        workload = f"{WORKLOAD}_grid{nx}x{ny}"
     h = hlb.Handle(cfg, stream=stream.cuda_stream)
     nodes, values, state_bytes = h.nodes, h.values, h.state_bytes
     V = values // nodes
@@ -193,6 +200,7 @@ def run_gpu(args):
     h.step(args.warmup)
     torch.cuda.synchronize()
     h.kernel_times(reset=True)
+    h.launch_count(reset=True)
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -206,6 +214,7 @@ def run_gpu(args):
     barrier()
     ms = e0.elapsed_time(e1)
     kt = h.kernel_times(reset=True)
+    launches = h.launch_count(reset=True)
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -254,35 +263,99 @@ def run_gpu(args):
             prof = json.load(fh)
         if prof.get("kernel_hash") == kernel_source_hash():
             traffic = prof.get("dram_bytes_per_launch")
-    cpu_rate, cpu_secs, cpu_desc = oracle_sample(steps=3)
+    cpu_rate, cpu_secs, cpu_desc, cpu_cores = oracle_sample(steps=3)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": "node-velocity updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": cfg["nx"], "ny": cfg["ny"], "velocities": V,
+        "config": {"workload": workload, "nx": cfg["nx"], "ny": cfg["ny"], "velocities": V,
                    "nodes": nodes, "values_per_copy": values, "precision": "fp32",
                    "advection": "weno5", "parallelism": f"replicas{world}",
-                   "l2": "state (2.15 GB per copy) larger than L2; no flush needed",
+                   "l2": f"state ({state_bytes / 1e9:.2f} GB per copy) larger than L2; no flush needed",
                    "moments_finite": finite},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "stage_kernel<float, WENO5>",
+                     "kernel": "march_pair_kernel<WENO5, 16, 8>",
                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                      "stage_avg_ms": stage_avg_ms,
                      "stage_share": kt["stage_ms"] / max(kt["stage_ms"] + kt["wall_ms"], 1e-9),
                      "bytes_per_unit": BYTES_PER_NV_STAGE, "unit_desc": "node-velocity per stage launch"},
-        "cpu_baseline": {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": 1,
+        "cpu_baseline": {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": cpu_cores,
                          "kind": "oracle", "sample": cpu_desc},
         "e2e": {"value": e2e_value, "unit": "node-velocity updates/s",
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": 6 * 8 * nodes},
-        "gpu_launches": kt["stage_launches"] + kt["wall_launches"],
+        "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------
+# batched channels: one handle for all instances (FP32) vs per-instance FP64
+# ------------------------------------------------------------------------------
+def run_batched(args):
+    """4096 independent 1D channels (SplitMix64 draws) advanced together in
+    FP32, against the plain per-instance FP64 solve on the same GPU (a sample
+    of instances, each its own FP64 handle stepped on its own)."""
+    import numpy as np
+    import torch
+
+    from paper_1708_03249_gb300 import build as hbuild
+    from paper_1708_03249_gb300 import hlb
+
+    torch.cuda.set_device(0)
+    if not os.path.exists(hlb.LIB_PATH):
+        hbuild.build()
+    insts = W.batched_instances(args.ninst)
+    stream = torch.cuda.Stream()
+    h = hlb.Handle(insts, stream=stream.cuda_stream)
+    h.init_equilibrium()
+    h.set_options(use_graphs=True, time_kernels=False)
+    h.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nv = h.values
+    rate32 = nv * args.steps / (ms * 1e-3)
+    n, u, T, q = h.moments()
+    finite = bool(np.isfinite(n).all() and np.isfinite(T).all())
+    h.close()
+    # per-instance FP64 solves of a sample (every 64th instance)
+    sample = insts[:: max(1, len(insts) // args.fp64_sample)][: args.fp64_sample]
+    total_nv, total_ms = 0, 0.0
+    for c in sample:
+        c64 = dict(c, precision=W.FP64)
+        hh = hlb.Handle(c64, stream=stream.cuda_stream)
+        hh.init_equilibrium()
+        hh.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        hh.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        total_nv += hh.values * args.steps
+        hh.close()
+    rate64 = total_nv / (total_ms * 1e-3)
+    line = {"metric": METRIC, "value": rate32, "unit": "node-velocity updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched_{args.ninst}_channels_splitmix64_seed{W.BATCH_SEED}",
+                       "values_per_copy": nv, "moments_finite": finite},
+            "fp64_per_instance": {"value": rate64, "unit": "node-velocity updates/s",
+                                  "instances": len(sample), "dtype": "f64",
+                                  "desc": "each sampled instance its own FP64 handle, stepped alone"},
+            "batched_fp32_over_fp64_per_instance": rate32 / rate64}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -291,9 +364,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="large2d", choices=["large2d", "batched"],
+                    help="large2d: the JSON line of record; batched: the 4096-channel batch vs per-instance FP64")
+    ap.add_argument("--ninst", type=int, default=4096)
+    ap.add_argument("--nx", type=int, default=0, help="profiling: the large 2D workload on a smaller grid")
+    ap.add_argument("--ny", type=int, default=0)
+    ap.add_argument("--fp64-sample", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 

@@ -199,12 +199,30 @@ hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g);
 
 /* Enable (1) / disable (0) CUDA-graph replay in hlb_step, and per-launch
  * CUDA-event timing (timing forces eager launches).  hlb_kernel_times
- * returns the accumulated device time (ms) and launch counts of the stage
- * and wall kernels since the last reset (reset != 0 clears them after
- * reading).  Synchronises. */
+ * returns the accumulated device time (ms) and counts of the timed intervals
+ * since the last reset (reset != 0 clears them after reading): "stage" is
+ * the stage kernel of each RK-3 stage alone, "wall" everything the stage
+ * launches before it (the node pass, when the marching kernel runs, and the
+ * wall kernel).  Synchronises. */
 hlb_status hlb_set_options(hlb_handle* h, int use_graphs, int time_kernels);
 hlb_status hlb_kernel_times(hlb_handle* h, double* stage_ms, long long* stage_launches,
                             double* wall_ms, long long* wall_launches, int reset);
+
+/* Number of kernels hlb_step has enqueued (CUDA-graph replays counted by the
+ * kernels they hold) since the handle was created or last reset (reset != 0
+ * clears the count after reading).  Host-only; does not synchronise. */
+hlb_status hlb_launch_count(hlb_handle* h, long long* launches, int reset);
+
+/* Test hook of the bounded device waits (no counterpart in the paper).  Every
+ * wait of the marching stage kernels on its bulk-copy pipeline gives up after
+ * wait_limit_s seconds (0: the default, 1 s; at most 60), records
+ * HLB_ETIMEOUT in the handle's device error word and ends its CTA's loop at
+ * the next barrier.  withhold_copies != 0 makes every marching CTA skip the
+ * copies of its second pipeline step, so that those waits run out: the next
+ * hlb_moments / hlb_get_state / hlb_diag (total_N) returns HLB_ETIMEOUT and the state
+ * is invalid (re-initialise it).  Steps that do not use the marching kernels
+ * are unaffected.  Synchronises if a CUDA graph has to be re-captured. */
+hlb_status hlb_set_wait_test(hlb_handle* h, int withhold_copies, double wait_limit_s);
 
 /* Message of the calling thread's last failing call ("" if none). */
 const char* hlb_last_error(void);

@@ -84,6 +84,7 @@ struct hlb_handle {
     KernelTimer timer;
     double stage_ms = 0, wall_ms = 0;
     long long stage_n = 0, wall_n = 0;
+    long long launches = 0;                  // kernels enqueued by hlb_step (graph replays included)
     bool have_residual = false;
     size_t esize = 4;
 };
@@ -175,6 +176,8 @@ hlb_status refresh_walls(hlb_handle* h, Group& G) {
     return upload_inst(G);
 }
 
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;   // 1 s
+
 void fill_dev(Group& G) {
     hlb::GroupDev& d = G.dev;
     d.V = G.V; d.QX2 = G.QX2; d.VY = G.VY; d.VZ = G.VZ; d.Qx = G.Qx;
@@ -200,6 +203,8 @@ void fill_dev(Group& G) {
     d.recf = (const float2*)G.d_recf.p;
     d.Tf = (const float2*)G.d_Tf.p;
     d.use_df = (G.precision == HLB_FP32 && G.Nx <= 11) ? 1 : 0;
+    d.wait_ns = kDefaultWaitNs;
+    d.inject_stall = 0;
 }
 
 hlb_status build_group(hlb_handle* h, Group& G) {
@@ -435,6 +440,14 @@ void enqueue_group_step(hlb_handle* h, Group& G) {
 
 void enqueue_step(hlb_handle* h) {
     for (auto& G : h->groups) enqueue_group_step(h, *G);
+}
+
+// Kernels one RK-3 step launches: per stage the node pass (sums, factor
+// lines) when the marching kernel runs, the wall kernel and the stage kernel.
+long long kernels_per_step(hlb_handle* h) {
+    long long n = 0;
+    for (auto& G : h->groups) n += 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2);
+    return n;
 }
 
 hlb_status collect_timer(hlb_handle* h) {
@@ -675,6 +688,7 @@ hlb_status hlb_step(hlb_handle* h, long nsteps) {
             }
             if (left >= h->graph_steps) {
                 HLB_CUDA(cudaGraphLaunch(h->graph, h->stream));
+                h->launches += h->graph_steps * kernels_per_step(h);
                 for (auto& G : h->groups) { G->prev = (G->cur + 2) % 3; }   // cur returns to 0
                 left -= h->graph_steps;
                 h->nsteps += h->graph_steps;
@@ -683,6 +697,7 @@ hlb_status hlb_step(hlb_handle* h, long nsteps) {
         }
         enqueue_step(h);
         HLB_CUDA(cudaGetLastError());
+        h->launches += kernels_per_step(h);
         left -= 1;
         h->nsteps += 1;
     }
@@ -902,6 +917,29 @@ hlb_status hlb_kernel_times(hlb_handle* h, double* stage_ms, long long* stage_la
     if (wall_ms) *wall_ms = h->wall_ms;
     if (wall_launches) *wall_launches = h->wall_n;
     if (reset) { h->stage_ms = h->wall_ms = 0; h->stage_n = h->wall_n = 0; }
+    return HLB_OK;
+}
+
+hlb_status hlb_launch_count(hlb_handle* h, long long* launches, int reset) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (launches) *launches = h->launches;
+    if (reset) h->launches = 0;
+    return HLB_OK;
+}
+
+hlb_status hlb_set_wait_test(hlb_handle* h, int withhold_copies, double wait_limit_s) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (!(wait_limit_s >= 0) || wait_limit_s > 60.0) return fail(HLB_EINVAL, "wait_limit_s must be in [0, 60]");
+    const unsigned long long ns = wait_limit_s > 0 ? (unsigned long long)(wait_limit_s * 1e9) : kDefaultWaitNs;
+    for (auto& G : h->groups) {
+        G->dev.wait_ns = ns;
+        G->dev.inject_stall = withhold_copies ? 1 : 0;
+    }
+    if (h->graph) {                      // the kernels' parameters changed: re-capture
+        HLB_CUDA(cudaStreamSynchronize(h->stream));
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     return HLB_OK;
 }
 

@@ -101,65 +101,78 @@ __device__ __forceinline__ float weno5_face_sv<float>(float a, float b, float c,
 template <typename R>
 __device__ __forceinline__ R upwind2_face(R b, R c) { return R(1.5) * c - R(0.5) * b; }
 
-// ---------------------------------------------------------------------------
-// WENO-5 on pre-scaled stencils (values already multiplied by the
-// population's inverse weight), branch-free.  Clamping every sigma at 1e-30
-// before forming delta_q (sigma_min/sigma_q)^2 reproduces all zero-set rows of
-// Tab. "weno": vanishing sigmas tie at the clamp and share weight in the
-// ratio of their delta_q, and the others get (1e-30/sigma)^2 ~ 0.
-// ---------------------------------------------------------------------------
-// 1/x on the special-function unit (|x| in [1e-30, 1e30] here).
+// 1/x on the special-function unit (x >= 1e-30 here; beyond 1e38 it flushes to 0).
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
+// WENO-5 face value from a stencil already divided by the population's
+// weight (values O(1) wherever the population matters), without epsilon.
+// Reassociated from Sec. IV.C.2: the candidates come pre-multiplied by their
+// linear weights, G_k = d_k q_k; the smoothness indicators are scaled by
+// 12/13 (B_k = t_k^2 + (3/13) s_k^2; a common factor leaves the weights
+// unchanged) and carry an additive floor of 1e-30, below which FP32 cannot
+// resolve them anyway; the nonlinear weights are formed from the ratios
+// u_k = min_j B_j / B_k in (0, 1], so nothing overflows, and a zero B_k
+// takes the limit of Tab. "weno" (the zero-indicator stencils share the
+// weight in proportion to d_k).
 __device__ __forceinline__ float weno5_scaled(float a, float b, float c, float d, float e) {
-    const float F1 = fmaf(11.0f / 6.0f, c, fmaf(-7.0f / 6.0f, b, (1.0f / 3.0f) * a));
-    const float F2 = fmaf(1.0f / 3.0f, d, fmaf(5.0f / 6.0f, c, (-1.0f / 6.0f) * b));
-    const float F3 = fmaf(-1.0f / 6.0f, e, fmaf(5.0f / 6.0f, d, (1.0f / 3.0f) * c));
-    const float t1 = fmaf(-2.0f, b, a) + c, t2 = fmaf(3.0f, c, fmaf(-4.0f, b, a));
-    const float t3 = fmaf(-2.0f, c, b) + d, t4 = b - d;
-    const float t5 = fmaf(-2.0f, d, c) + e, t6 = fmaf(-4.0f, d, fmaf(3.0f, c, e));
-    const float s1 = fmaxf(fmaf(13.0f / 12.0f * t1, t1, 0.25f * t2 * t2), 1e-30f);
-    const float s2 = fmaxf(fmaf(13.0f / 12.0f * t3, t3, 0.25f * t4 * t4), 1e-30f);
-    const float s3 = fmaxf(fmaf(13.0f / 12.0f * t5, t5, 0.25f * t6 * t6), 1e-30f);
-    const float m = fminf(s1, fminf(s2, s3));
-    const float u1 = m * rcp_approx(s1), u2 = m * rcp_approx(s2), u3 = m * rcp_approx(s3);
-    const float w1 = 0.1f * u1 * u1, w2 = 0.6f * u2 * u2, w3 = 0.3f * u3 * u3;
-    return fmaf(w1, F1, fmaf(w2, F2, w3 * F3)) * rcp_approx(w1 + w2 + w3);
+    const float G1 = fmaf(11.0f / 60.0f, c, fmaf(-7.0f / 60.0f, b, (1.0f / 30.0f) * a));
+    const float G2 = fmaf(0.2f, d, fmaf(0.5f, c, -0.1f * b));
+    const float G3 = fmaf(-0.05f, e, fmaf(0.25f, d, 0.1f * c));
+    const float t1 = fmaf(-2.0f, b, a + c), s1 = fmaf(-4.0f, b, fmaf(3.0f, c, a));
+    const float t2 = fmaf(-2.0f, c, b + d), s2 = b - d;
+    const float t3 = fmaf(-2.0f, d, c + e), s3 = fmaf(-4.0f, d, fmaf(3.0f, c, e));
+    constexpr float k = 3.0f / 13.0f;
+    const float B1 = fmaf(t1, t1, fmaf(k * s1, s1, 1e-30f));
+    const float B2 = fmaf(t2, t2, fmaf(k * s2, s2, 1e-30f));
+    const float B3 = fmaf(t3, t3, fmaf(k * s3, s3, 1e-30f));
+    const float m = fminf(B1, fminf(B2, B3));
+    const float u1 = m * rcp_approx(B1), u2 = m * rcp_approx(B2), u3 = m * rcp_approx(B3);
+    const float v1 = u1 * u1, v2 = u2 * u2, v3 = u3 * u3;
+    const float den = fmaf(0.1f, v1, fmaf(0.6f, v2, 0.3f * v3));
+    return fmaf(v1, G1, fmaf(v2, G2, v3 * G3)) * rcp_approx(den);
 }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
-// Two independent faces at once in the packed FP32 pipe (f32x2 on sm_100+).
+// a - b in the packed FP32 pipe
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+
+// Two independent faces at once in the packed FP32 pipe (f32x2 on sm_100+);
+// the same arithmetic as weno5_scaled.
 __device__ __forceinline__ float2 weno5_scaled2(float2 a, float2 b, float2 c, float2 d, float2 e) {
-    const float2 F1 = __ffma2_rn(f2(11.0f / 6.0f), c, __ffma2_rn(f2(-7.0f / 6.0f), b, __fmul2_rn(f2(1.0f / 3.0f), a)));
-    const float2 F2 = __ffma2_rn(f2(1.0f / 3.0f), d, __ffma2_rn(f2(5.0f / 6.0f), c, __fmul2_rn(f2(-1.0f / 6.0f), b)));
-    const float2 F3 = __ffma2_rn(f2(-1.0f / 6.0f), e, __ffma2_rn(f2(5.0f / 6.0f), d, __fmul2_rn(f2(1.0f / 3.0f), c)));
-    const float2 t1 = __fadd2_rn(__ffma2_rn(f2(-2.0f), b, a), c);
-    const float2 t2 = __ffma2_rn(f2(3.0f), c, __ffma2_rn(f2(-4.0f), b, a));
-    const float2 t3 = __fadd2_rn(__ffma2_rn(f2(-2.0f), c, b), d);
-    const float2 t4 = __fadd2_rn(b, __fmul2_rn(f2(-1.0f), d));
-    const float2 t5 = __fadd2_rn(__ffma2_rn(f2(-2.0f), d, c), e);
-    const float2 t6 = __ffma2_rn(f2(-4.0f), d, __ffma2_rn(f2(3.0f), c, e));
-    const float2 q1 = __ffma2_rn(__fmul2_rn(f2(13.0f / 12.0f), t1), t1, __fmul2_rn(__fmul2_rn(f2(0.25f), t2), t2));
-    const float2 q2 = __ffma2_rn(__fmul2_rn(f2(13.0f / 12.0f), t3), t3, __fmul2_rn(__fmul2_rn(f2(0.25f), t4), t4));
-    const float2 q3 = __ffma2_rn(__fmul2_rn(f2(13.0f / 12.0f), t5), t5, __fmul2_rn(__fmul2_rn(f2(0.25f), t6), t6));
-    const float2 s1 = make_float2(fmaxf(q1.x, 1e-30f), fmaxf(q1.y, 1e-30f));
-    const float2 s2 = make_float2(fmaxf(q2.x, 1e-30f), fmaxf(q2.y, 1e-30f));
-    const float2 s3 = make_float2(fmaxf(q3.x, 1e-30f), fmaxf(q3.y, 1e-30f));
-    const float2 m = make_float2(fminf(s1.x, fminf(s2.x, s3.x)), fminf(s1.y, fminf(s2.y, s3.y)));
-    const float2 u1 = __fmul2_rn(m, make_float2(rcp_approx(s1.x), rcp_approx(s1.y)));
-    const float2 u2 = __fmul2_rn(m, make_float2(rcp_approx(s2.x), rcp_approx(s2.y)));
-    const float2 u3 = __fmul2_rn(m, make_float2(rcp_approx(s3.x), rcp_approx(s3.y)));
-    const float2 w1 = __fmul2_rn(__fmul2_rn(f2(0.1f), u1), u1);
-    const float2 w2 = __fmul2_rn(__fmul2_rn(f2(0.6f), u2), u2);
-    const float2 w3 = __fmul2_rn(__fmul2_rn(f2(0.3f), u3), u3);
-    const float2 ws = __fadd2_rn(__fadd2_rn(w1, w2), w3);
-    const float2 num = __ffma2_rn(w1, F1, __ffma2_rn(w2, F2, __fmul2_rn(w3, F3)));
-    return __fmul2_rn(num, make_float2(rcp_approx(ws.x), rcp_approx(ws.y)));
+    const float2 G1 = __ffma2_rn(f2(11.0f / 60.0f), c, __ffma2_rn(f2(-7.0f / 60.0f), b, __fmul2_rn(f2(1.0f / 30.0f), a)));
+    const float2 G2 = __ffma2_rn(f2(0.2f), d, __ffma2_rn(f2(0.5f), c, __fmul2_rn(f2(-0.1f), b)));
+    const float2 G3 = __ffma2_rn(f2(-0.05f), e, __ffma2_rn(f2(0.25f), d, __fmul2_rn(f2(0.1f), c)));
+    const float2 t1 = __ffma2_rn(f2(-2.0f), b, __fadd2_rn(a, c));
+    const float2 s1 = __ffma2_rn(f2(-4.0f), b, __ffma2_rn(f2(3.0f), c, a));
+    const float2 t2 = __ffma2_rn(f2(-2.0f), c, __fadd2_rn(b, d));
+    const float2 s2 = fsub2(b, d);
+    const float2 t3 = __ffma2_rn(f2(-2.0f), d, __fadd2_rn(c, e));
+    const float2 s3 = __ffma2_rn(f2(-4.0f), d, __ffma2_rn(f2(3.0f), c, e));
+    const float2 k = f2(3.0f / 13.0f), fl = f2(1e-30f);
+    const float2 B1 = __ffma2_rn(t1, t1, __ffma2_rn(__fmul2_rn(k, s1), s1, fl));
+    const float2 B2 = __ffma2_rn(t2, t2, __ffma2_rn(__fmul2_rn(k, s2), s2, fl));
+    const float2 B3 = __ffma2_rn(t3, t3, __ffma2_rn(__fmul2_rn(k, s3), s3, fl));
+    const float2 m = make_float2(fminf(B1.x, fminf(B2.x, B3.x)), fminf(B1.y, fminf(B2.y, B3.y)));
+    const float2 u1 = __fmul2_rn(m, make_float2(rcp_approx(B1.x), rcp_approx(B1.y)));
+    const float2 u2 = __fmul2_rn(m, make_float2(rcp_approx(B2.x), rcp_approx(B2.y)));
+    const float2 u3 = __fmul2_rn(m, make_float2(rcp_approx(B3.x), rcp_approx(B3.y)));
+    const float2 v1 = __fmul2_rn(u1, u1), v2 = __fmul2_rn(u2, u2), v3 = __fmul2_rn(u3, u3);
+    const float2 den = __ffma2_rn(f2(0.1f), v1, __ffma2_rn(f2(0.6f), v2, __fmul2_rn(f2(0.3f), v3)));
+    const float2 num = __ffma2_rn(v1, G1, __ffma2_rn(v2, G2, __fmul2_rn(v3, G3)));
+    return __fmul2_rn(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
 }
 
 __device__ __forceinline__ float2 upwind2_face2(float2 b, float2 c) {
@@ -270,6 +283,12 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t
                  : "memory");
 }
 
+// Plain arrival (release at CTA scope): the arriving thread's earlier
+// shared-memory writes are visible to threads that then see the phase complete.
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Orders this thread's earlier generic-proxy shared-memory accesses before
 // its later async-proxy (bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -283,6 +302,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// src 16-byte aligned; bytes a multiple of 16.  A hint: no completion to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
@@ -303,21 +327,46 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Bounded wait: gives up after about one second, records HLB_ETIMEOUT in
-// *err and returns false.  The caller carries on with whatever the buffer
-// holds, so that no barrier of the CTA is left waiting.
-constexpr unsigned long long kWaitNs = 1000000000ull;
+// try_wait that may suspend the thread for up to hint_ns while the phase is
+// incomplete (the thread resumes when it completes), so that a waiting warp
+// does not spin through issue slots.
+__device__ __forceinline__ bool mbar_try_wait_hint(unsigned long long* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* err) {
+// Bounded wait: gives up after wait_ns nanoseconds, records HLB_ETIMEOUT in
+// *err and returns false.  The caller then leaves its loop, so that no wait
+// of the CTA is left pending.
+constexpr uint32_t kSuspendHintNs = 100000;
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, int* err,
+                                          unsigned long long wait_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > kWaitNs) {
+    while (!mbar_try_wait_hint(bar, parity, kSuspendHintNs)) {
+        if (global_ns() - t0 > wait_ns) {
             atomicExch(err, 4);   // HLB_ETIMEOUT
             return false;
         }
     }
     return true;
+}
+
+// After a wait ran out: wait, again at most wait_ns, for the phase of the
+// given parity (the bulk copies it tracks) to complete; records nothing.
+__device__ __forceinline__ void mbar_drain(unsigned long long* bar, uint32_t parity, unsigned long long wait_ns) {
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > wait_ns) return;
+    }
 }
 
 // The half-range coefficients G^{+-}_l (roles 0, 1) and the full-range ones

@@ -285,7 +285,7 @@ constexpr int kDepth = 4;    // x-steps in flight
 
 template <typename R, int QX2, int VY, int TY>
 constexpr size_t march_smem_bytes() {
-    return kDepth * sizeof(StepBuf<R, QX2, VY, TY>) + 2 * TY * QX2 * VY * sizeof(R) + kDepth * 8 + 16;
+    return kDepth * sizeof(StepBuf<R, QX2, VY, TY>) + 2 * TY * QX2 * VY * sizeof(R) + kDepth * 8 + 16;   // + abort flag
 }
 
 // The marching kernel.  Offsets inside an instance are 32-bit (the host
@@ -301,6 +301,7 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
     Buf* buf = reinterpret_cast<Buf*>(msm);
     R* sF = reinterpret_cast<R*>(msm + kDepth * sizeof(Buf));              // [2][TY][S]
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(sF + 2 * TY * S);
+    int* sAbort = reinterpret_cast<int*>(bars + kDepth);
 
     const Work W = works[blockIdx.x];
     const InstDev& I = g.inst[W.inst];
@@ -348,6 +349,7 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
     // producer (thread 0): the copies of step xs into buffer (xs - xa) % kDepth
     auto issue = [&](int xs) {
         if (xs >= xb) return;
+        if (g.inject_stall && xs == xa + 1) return;     // bounded-wait test: this step's copies never come
         Buf& B = buf[(xs - xa) % kDepth];
         unsigned long long* bar = &bars[(xs - xa) % kDepth];
         const uint32_t row_bytes = S * sizeof(R);
@@ -376,6 +378,7 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
 
     if (t == 0) {
         for (int d = 0; d < kDepth; ++d) mbar_init(&bars[d], 1);
+        *sAbort = 0;
         mbar_init_fence();
     }
     __syncthreads();
@@ -410,11 +413,13 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
         Fm[r] = vx * face_value<R, ADV>(xpos, sv, w[r][0], w[r][1], w[r][2], w[r][3], w[r][4], w[r][5]);
     }
 
+    int xab = xa;
 #pragma unroll 1
     for (int x = xa; x < xb; ++x) {
         const int step = x - xa;
         const Buf& B = buf[step % kDepth];
-        mbar_wait(&bars[step % kDepth], (step / kDepth) & 1, g.err);
+        if (!mbar_wait(&bars[step % kDepth], (step / kDepth) & 1, g.err, g.wait_ns)) *sAbort = 1;
+        xab = x;
         const int b = x & 1;
         R fc[TY];
 #pragma unroll
@@ -462,6 +467,7 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
             for (int r = 0; r < TY; ++r) divy[r] = (Gf[r + 1] - Gf[r]) * inv_dy;
         }
         __syncthreads();
+        if (*sAbort) break;
         if (t == 0) issue(x + kDepth - 1);
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
@@ -489,31 +495,56 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
             if (valid[r]) fov[roff[r] + x * V] = out;
         }
     }
+    if (*sAbort && t == 0) {
+        // a wait ran out at step xab: let the copies issued since land before the CTA exits
+        for (int s2 = xab - xa; s2 < xb - xa && s2 < xab - xa + kDepth - 1; ++s2)
+            mbar_drain(&bars[s2 % kDepth], (s2 / kDepth) & 1, g.wait_ns);
+    }
 }
 
-// FP32, two strip rows packed into the lanes of f32x2 registers (x = row y0,
-// y = row y0+1).  Same pipeline and arithmetic as march_kernel; the window
-// holds values pre-multiplied by the population's inverse weight so that
-// every WENO evaluation reads scaled stencils directly.
+// FP32 pair kernel: each iteration advances two strip rows by two cells.
+// The x faces pack the two rows into the lanes of f32x2 registers, the y faces
+// pack the two cells, so every WENO evaluation is a full f32x2 one.  The
+// window holds values pre-multiplied by the population's inverse weight, so
+// that every WENO evaluation reads scaled stencils directly.
+template <int QX2, int VY>
+struct PairBuf {
+    static constexpr int S = QX2 * VY;
+    static constexpr int NCPMAX = (QX2 + VY + 32 + 1 + 3) / 4 * 4;
+    float head[2][2][S];        // [cell x0+3+i][row]
+    float halo[2][6][S];        // [cell x0+i][halo row y0-3, y0-2, y0-1, y0+2, y0+3, y0+4]
+    float fnr[2][2][S];         // [cell x0+i][row]: f^n (stages 2, 3)
+    float coef[2][2 * NCPMAX];  // [row]: factor lines of cells x0, x0+1
+};
+
+constexpr int kPairDepth = 4;   // pairs of cells in flight (copy buffers)
+
+template <int QX2, int VY>
+constexpr size_t pair_smem_bytes() {
+    return kPairDepth * sizeof(PairBuf<QX2, VY>) + 2 * VY * (QX2 + 1) * sizeof(float4) + (kPairDepth + 2) * 8 + 16;
+}
+
 template <int ADV, int QX2, int VY>
-__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? 5 : 1)))
-march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
-              const float* __restrict__ fn, float* __restrict__ fo, int stage) {
-    constexpr int TY = 2;
+__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? 4 : 1)))
+march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
+                  const float* __restrict__ fn, float* __restrict__ fo, int stage) {
     constexpr int S = QX2 * VY;
     constexpr int QX = QX2 / 2;
-    using Buf = StepBuf<float, QX2, VY, TY>;
+    constexpr int SP = QX2 + 1;            // padded sF row: the K_x reads of a warp hit distinct banks
+    using Buf = PairBuf<QX2, VY>;
     extern __shared__ __align__(128) unsigned char msm[];
     Buf* buf = reinterpret_cast<Buf*>(msm);
-    float2* sF = reinterpret_cast<float2*>(msm + kDepth * sizeof(Buf));     // [2][S] (row0, row1)
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sF + 2 * S);
+    float4* sF = reinterpret_cast<float4*>(msm + kPairDepth * sizeof(Buf));   // [2][VY][SP]: (r0 x0, r1 x0, r0 x1, r1 x1)
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sF + 2 * VY * SP);   // bulk-copy pipeline
+    unsigned long long* xch = bars + kPairDepth;       // [2]: sF[b] written by every warp
+    int* sAbort = reinterpret_cast<int*>(xch + 2);
 
     const Work W = works[blockIdx.x];
     const InstDev& I = g.inst[W.inst];
     const int t = threadIdx.x;
     // Thread -> velocity: when a sign quadrant of (p_x, p_y) fills whole warps,
-    // each warp takes one quadrant, so the stencil orientation below is
-    // warp-uniform; otherwise ix runs fastest.
+    // each warp takes one quadrant, so the stencil orientation is warp-uniform;
+    // otherwise ix runs fastest.
     constexpr int QH = QX2 / 2, YH = VY >= 2 ? VY / 2 : 1;
     constexpr bool kQuad = VY >= 2 && (QH * YH) % 32 == 0;
     int ix, jy;
@@ -541,7 +572,7 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
 #pragma unroll
     for (int j = 0; j < VY; ++j) ky[j] = K[QX2 * QX2 + jy * VY + j];
     const float2 ax2 = f2((float)I.ax), ay2 = f2((float)I.ay), dt2 = f2((float)I.dt);
-    const float2 vxs = f2(vx * isv), vys = f2(vy * isv * (float)I.inv_dy), isv2 = f2(isv);
+    const float2 vxs = f2(vx * isv), vys = f2(vy * isv * (float)I.inv_dy), isv2 = f2(isv), sv2 = f2(sv);
     const float* invdx = static_cast<const float*>(g.inv_dx) + I.dx_off;
     const int rs = nx * V;
     const float* fsI = fs + I.f_off;
@@ -551,11 +582,11 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     const int csrc_z = QX2 + VY + kz, csrc_t = QX2 + VY + g.VZ;
     const float* gw = static_cast<const float*>(g.gw) + I.gw_off;
     const float gwl = gw[v] * sv, gwr = gw[V + v] * sv;
-    int roff[TY], crow[TY];
-    bool valid[TY];
-    float nwl_g[TY], nwr_g[TY];        // scaled emitted ghosts
+    int roff[2], crow[2];
+    bool valid[2];
+    float nwl_g[2], nwr_g[2];          // scaled emitted ghosts
 #pragma unroll
-    for (int r = 0; r < TY; ++r) {
+    for (int r = 0; r < 2; ++r) {
         const int y = W.y0 + r;
         valid[r] = y < ny;
         const int yy = y % ny;
@@ -565,168 +596,237 @@ march2_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
         nwr_g[r] = (float)g.nw[(size_t)(I.row_off + yy) * 2 + 1] * gwr;
     }
     const int xa = W.xa, xb = W.xb;
+    const int npairs = (xb - xa + 1) >> 1;
     const int slab = kz * S;
+    const uint32_t row_bytes = S * sizeof(float);
 
-    auto issue = [&](int xs) {
-        if (xs >= xb) return;
-        Buf& B = buf[(xs - xa) % kDepth];
-        unsigned long long* bar = &bars[(xs - xa) % kDepth];
-        const uint32_t row_bytes = S * sizeof(float);
-        uint32_t bytes = TY * ncp * sizeof(float) + 6 * row_bytes;
-        if (xs + 3 < nx) bytes += TY * row_bytes;
-        if (stage > 0) bytes += TY * row_bytes;
+    // producer (warp 0, one copy per lane): the inputs of pair p into buffer p % kPairDepth
+    // Copy `lane` of pair p (22 lanes: 12 halo rows, 4 head rows, 4 f^n rows,
+    // 2 factor-line runs): source, bytes and destination in B; false if the
+    // lane has none for this pair.
+    auto copy_of = [&](int lane, int p, Buf& B, const float*& src, uint32_t& bytes, float*& dst) -> bool {
+        const int x0 = xa + 2 * p;
+        const int n2 = min(2, xb - x0);
+        bytes = row_bytes;
+        if (lane < 12) {                                   // halo rows of cells x0, x0+1
+            const int i = lane / 6, k = lane % 6;
+            const int yk = k < 3 ? ((W.y0 - 3 + k) % ny + ny) % ny : (W.y0 + k - 1) % ny;
+            src = fsI + yk * rs + (x0 + i) * V + slab;
+            dst = B.halo[i][k];
+            return i < n2;
+        } else if (lane < 16) {                            // head cells x0+3, x0+4
+            const int i = (lane - 12) >> 1, r = lane & 1;
+            src = fsI + roff[r] + (x0 + 3 + i) * V + slab;
+            dst = B.head[i][r];
+            return i < n2 && x0 + 3 + i < nx;
+        } else if (lane < 20) {                            // f^n of cells x0, x0+1
+            const int i = (lane - 16) >> 1, r = lane & 1;
+            src = fnI + roff[r] + (x0 + i) * V + slab;
+            dst = B.fnr[i][r];
+            return stage > 0 && i < n2;
+        } else if (lane < 22) {                            // factor lines
+            const int r = lane - 20;
+            src = cI + (size_t)(crow[r] + x0) * ncp;
+            bytes = n2 * ncp * (uint32_t)sizeof(float);
+            dst = B.coef[r];
+            return true;
+        }
+        return false;
+    };
+    // The copies are spread over the warps so that no warp carries them all:
+    // with four or more warps, warps 0 and 1 take the halo rows of cells x0
+    // and x0+1, warp 2 the head rows and factor lines, warp 3 the f^n rows; a
+    // single warp takes all 22.  Thread 0 registers each pair's byte count
+    // (arrive.expect_tx) before any warp can issue that pair's copies.
+    const int warp = t >> 5, lane = t & 31;
+    int my_copy = -1;
+    if (S / 32 >= 4) {
+        if (warp < 2 && lane < 6) my_copy = 6 * warp + lane;
+        else if (warp == 2 && lane < 6) my_copy = lane < 4 ? 12 + lane : 16 + lane;    // 12..15, 20..21
+        else if (warp == 3 && lane < 4) my_copy = 16 + lane;
+    } else if (warp == 0 && lane < 22) {
+        my_copy = lane;
+    }
+    auto expect = [&](int p) {                     // thread 0 only
+        if (p >= npairs || (g.inject_stall && p == 1)) return;   // test hook: pair 1 never arrives
+        const int x0 = xa + 2 * p;
+        const int n2 = min(2, xb - x0);
+        const int nhead = (x0 + 3 < nx) + (n2 > 1 && x0 + 4 < nx);
+        uint32_t bytes = n2 * (6 * row_bytes + 2 * ncp * (uint32_t)sizeof(float)) + 2 * nhead * row_bytes;
+        if (stage > 0) bytes += 2 * n2 * row_bytes;
+        mbar_expect_tx(&bars[p % kPairDepth], bytes);
+    };
+    auto issue = [&](int p) {
+        if (my_copy < 0 || p >= npairs || (g.inject_stall && p == 1)) return;
+        Buf& B = buf[p % kPairDepth];
+        const float* src;
+        uint32_t bytes;
+        float* dst;
         fence_proxy_async_smem();
-        mbar_expect_tx(bar, bytes);
-#pragma unroll
-        for (int r = 0; r < TY; ++r) {
-            if (xs + 3 < nx) bulk_g2s(B.head[r], fsI + roff[r] + (xs + 3) * V + slab, row_bytes, bar);
-            if (stage > 0) bulk_g2s(B.fnr[r], fnI + roff[r] + xs * V + slab, row_bytes, bar);
-            bulk_g2s(B.coef[r], cI + (crow[r] + xs) * ncp, ncp * sizeof(float), bar);
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int ylo = ((W.y0 - 3 + k) % ny + ny) % ny;
-            const int yhi = (W.y0 + TY + k) % ny;
-            bulk_g2s(B.halo[k], fsI + ylo * rs + xs * V + slab, row_bytes, bar);
-            bulk_g2s(B.halo[3 + k], fsI + yhi * rs + xs * V + slab, row_bytes, bar);
-        }
+        if (copy_of(my_copy, p, B, src, bytes, dst)) bulk_g2s(dst, src, bytes, &bars[p % kPairDepth]);
     };
 
     if (t == 0) {
-        for (int d = 0; d < kDepth; ++d) mbar_init(&bars[d], 1);
+        for (int d = 0; d < kPairDepth; ++d) mbar_init(&bars[d], 1);
+        mbar_init(&xch[0], S / 32);
+        mbar_init(&xch[1], S / 32);
+        *sAbort = 0;
         mbar_init_fence();
+        for (int p = 0; p < kPairDepth - 1; ++p) expect(p);
     }
     __syncthreads();
-    if (t == 0)
-        for (int xs = xa; xs < xa + kDepth - 1; ++xs) issue(xs);
+    for (int p = 0; p < kPairDepth - 1; ++p) issue(p);
 
-    // scaled window of cells xa-3 .. xa+2 (wall ghosts of Sec. IV.C.3)
-    float wr[TY][6];
+    // scaled window of cells xa-3 .. xa+4 (wall ghosts of Sec. IV.C.3); w[0..5] filled here
+    float2 w[8];
+    {
+        float wr[2][6];
 #pragma unroll
-    for (int r = 0; r < TY; ++r) {
-        const float* f = fsI + v + roff[r];
+        for (int r = 0; r < 2; ++r) {
+            const float* f = fsI + v + roff[r];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            const int x = xa - 3 + j;
-            float val;
-            if (x >= 0 && x < nx) val = f[x * V] * sv;
-            else if (x < 0) {
-                if (xpos) val = nwl_g[r];
-                else if (x < -2) val = 0.0f;          // never read by a negative velocity
+            for (int j = 0; j < 6; ++j) {
+                const int x = xa - 3 + j;
+                float val;
+                if (x >= 0 && x < nx) val = f[x * V] * sv;
+                else if (x < 0) {
+                    if (xpos) val = nwl_g[r];
+                    else if (x < -2) val = 0.0f;          // never read by a negative velocity
+                    else {
+                        const float f0 = f[0] * sv, f1 = f[V] * sv, f2v = f[2 * V] * sv;
+                        val = x == -1 ? 3.0f * f0 - 3.0f * f1 + f2v : 6.0f * f0 - 8.0f * f1 + 3.0f * f2v;
+                    }
+                } else if (!xpos) val = nwr_g[r];
+                else if (x > nx + 1) val = 0.0f;          // never read by a positive velocity
                 else {
-                    const float f0 = f[0] * sv, f1 = f[V] * sv, f2v = f[2 * V] * sv;
-                    val = x == -1 ? 3.0f * f0 - 3.0f * f1 + f2v : 6.0f * f0 - 8.0f * f1 + 3.0f * f2v;
+                    const float f0 = f[(nx - 1) * V] * sv, f1 = f[(nx - 2) * V] * sv, f2v = f[(nx - 3) * V] * sv;
+                    val = x == nx ? 3.0f * f0 - 3.0f * f1 + f2v : 6.0f * f0 - 8.0f * f1 + 3.0f * f2v;
                 }
-            } else if (!xpos) val = nwr_g[r];
-            else if (x > nx + 1) val = 0.0f;          // never read by a positive velocity
-            else {
-                const float f0 = f[(nx - 1) * V] * sv, f1 = f[(nx - 2) * V] * sv, f2v = f[(nx - 3) * V] * sv;
-                val = x == nx ? 3.0f * f0 - 3.0f * f1 + f2v : 6.0f * f0 - 8.0f * f1 + 3.0f * f2v;
+                wr[r][j] = val;
             }
-            wr[r][j] = val;
         }
-    }
-    float2 w[6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) w[j] = make_float2(wr[0][j], wr[1][j]);
-    auto xface = [&](const float2* c) -> float2 {
+        for (int j = 0; j < 6; ++j) w[j] = make_float2(wr[0][j], wr[1][j]);
+        w[6] = w[7] = f2(0.0f);
+    }
+    // flux per unit velocity at the face between c[2] and c[3] of c[0..5]
+    auto face = [&](bool pos, const float2* c) -> float2 {
         if (ADV == HLB_WENO5_) {
-            if (xpos) return weno5_scaled2(c[0], c[1], c[2], c[3], c[4]);
+            if (pos) return weno5_scaled2(c[0], c[1], c[2], c[3], c[4]);
             return weno5_scaled2(c[5], c[4], c[3], c[2], c[1]);
         }
-        return xpos ? upwind2_face2(c[1], c[2]) : upwind2_face2(c[4], c[3]);
+        return pos ? upwind2_face2(c[1], c[2]) : upwind2_face2(c[4], c[3]);
     };
-    float2 Fm = __fmul2_rn(vxs, xface(w));
+    // a cell entering the window at position e (head row pair hd; right-wall
+    // ghosts from the cells nx-1, nx-2, nx-3 already in the window)
+    auto enter = [&](int h, const float* hd0, const float* hd1, float2 m1, float2 m2, float2 m3,
+                     float2 m4) -> float2 {
+        if (h < nx) return __fmul2_rn(make_float2(hd0[vl], hd1[vl]), sv2);
+        if (!xpos) return make_float2(nwr_g[0], nwr_g[1]);                     // emitted at the right wall
+        if (h == nx) return __ffma2_rn(f2(3.0f), __fadd2_rn(m1, __fmul2_rn(f2(-1.0f), m2)), m3);
+        if (h == nx + 1) return __ffma2_rn(f2(6.0f), m2, __ffma2_rn(f2(-8.0f), m3, __fmul2_rn(f2(3.0f), m4)));
+        return f2(0.0f);                                                        // never read by v > 0
+    };
+    float2 Fm = __fmul2_rn(vxs, face(xpos, w));
 
+    // Per pair: wait for its copies; write the centre values to sF[b] and
+    // arrive on xch[b]; evaluate the faces (the other warps catch up
+    // meanwhile); wait on xch[b]; then the force term, which reads every
+    // warp's sF[b].  Passing xch[b] of pair p also means every warp is done
+    // with pair p-1, so its copy buffer is refilled then.  Every wait is
+    // bounded, so no warp can be left waiting for good.
+    int pa = 0, slot = 0;
+    uint32_t phase = 0;
 #pragma unroll 1
-    for (int x = xa; x < xb; ++x) {
-        const int step = x - xa;
-        const Buf& B = buf[step % kDepth];
-        mbar_wait(&bars[step % kDepth], (step / kDepth) & 1, g.err);
-        const int b = x & 1;
+    for (int p = 0; p < npairs; ++p) {
+        const int x0 = xa + 2 * p;
+        const bool two = x0 + 1 < xb;
+        pa = p;
+        const Buf& B = buf[slot];
+        if (!mbar_wait(&bars[slot], phase, g.err, g.wait_ns)) *sAbort = 1;
+        if (t == 0) expect(p + kPairDepth - 1);     // its slot's previous phase (pair p-1) is complete
+        const int b = p & 1;
+        w[6] = enter(x0 + 3, B.head[0][0], B.head[0][1], w[5], w[4], w[3], w[2]);
+        w[7] = enter(x0 + 4, B.head[1][0], B.head[1][1], w[6], w[5], w[4], w[3]);
+        const float2 fc0 = __fmul2_rn(w[3], isv2), fc1 = __fmul2_rn(w[4], isv2);
+        sF[(b * VY + jy) * SP + ix] = make_float4(fc0.x, fc0.y, fc1.x, fc1.y);
+        __syncwarp();
+        if ((t & 31) == 0) mbar_arrive(&xch[b]);
+        // x faces x0+1/2, x0+3/2 (rows packed); x0-1/2 carried
+        const float2 Fp0 = __fmul2_rn(vxs, face(xpos, w + 1));
+        const float2 Fp1 = __fmul2_rn(vxs, face(xpos, w + 2));
+        const float2 divx0 = __fmul2_rn(fsub2(Fp0, Fm), f2(invdx[x0]));
+        const float2 divx1 = __fmul2_rn(fsub2(Fp1, Fp0), f2(two ? invdx[x0 + 1] : 0.0f));
+        Fm = Fp1;
+        // y faces (periodic), cells packed: rows y0-3 .. y0+4 of columns x0, x0+1
+        float2 col[8];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) w[j] = w[j + 1];
-        const int h = x + 3;
-        if (h < nx) w[5] = __fmul2_rn(make_float2(B.head[0][vl], B.head[1][vl]), f2(sv));
-        else if (!xpos) w[5] = make_float2(nwr_g[0], nwr_g[1]);
-        else if (h == nx) w[5] = __ffma2_rn(f2(3.0f), __fadd2_rn(w[4], __fmul2_rn(f2(-1.0f), w[3])), w[2]);
-        else if (h == nx + 1)
-            w[5] = __ffma2_rn(f2(6.0f), w[3], __ffma2_rn(f2(-8.0f), w[2], __fmul2_rn(f2(3.0f), w[1])));
-        else w[5] = f2(0.0f);
-        const float2 fc = __fmul2_rn(w[2], isv2);
-        sF[b * S + vl] = fc;
-        // x faces
-        const float2 Fp = __fmul2_rn(vxs, xface(w));
-        const float2 divx = __fmul2_rn(__fadd2_rn(Fp, __fmul2_rn(f2(-1.0f), Fm)), f2(invdx[x]));
-        Fm = Fp;
-        // y faces (periodic): rows y0-3 .. y0+4 of column x, scaled
-        float col[8];
+        for (int k = 0; k < 3; ++k) col[k] = __fmul2_rn(make_float2(B.halo[0][k][vl], B.halo[1][k][vl]), sv2);
+        col[3] = make_float2(w[3].x, w[4].x);
+        col[4] = make_float2(w[3].y, w[4].y);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) col[k] = B.halo[k][vl] * sv;
-        col[3] = w[2].x;
-        col[4] = w[2].y;
+        for (int k = 0; k < 3; ++k) col[5 + k] = __fmul2_rn(make_float2(B.halo[0][3 + k][vl], B.halo[1][3 + k][vl]), sv2);
+        const float2 G0 = face(ypos, col), G1 = face(ypos, col + 1), G2 = face(ypos, col + 2);
+        const float2 dy0 = __fmul2_rn(vys, fsub2(G1, G0));   // row y0, cells x0, x0+1
+        const float2 dy1 = __fmul2_rn(vys, fsub2(G2, G1));   // row y0+1
+        // shift the window by two cells
 #pragma unroll
-        for (int k = 0; k < 3; ++k) col[5 + k] = B.halo[3 + k][vl] * sv;
-        float2 G01;
-        float G2;
-        if (ADV == HLB_WENO5_) {
-            if (ypos) {
-                G01 = weno5_scaled2(make_float2(col[0], col[1]), make_float2(col[1], col[2]), make_float2(col[2], col[3]),
-                                    make_float2(col[3], col[4]), make_float2(col[4], col[5]));
-                G2 = weno5_scaled(col[2], col[3], col[4], col[5], col[6]);
-            } else {
-                G01 = weno5_scaled2(make_float2(col[5], col[6]), make_float2(col[4], col[5]), make_float2(col[3], col[4]),
-                                    make_float2(col[2], col[3]), make_float2(col[1], col[2]));
-                G2 = weno5_scaled(col[7], col[6], col[5], col[4], col[3]);
-            }
-        } else {
-            if (ypos) {
-                G01 = upwind2_face2(make_float2(col[1], col[2]), make_float2(col[2], col[3]));
-                G2 = upwind2_face(col[3], col[4]);
-            } else {
-                G01 = upwind2_face2(make_float2(col[4], col[5]), make_float2(col[3], col[4]));
-                G2 = upwind2_face(col[6], col[5]);
-            }
-        }
-        const float2 divy = __fmul2_rn(vys, make_float2(G01.y - G01.x, G2 - G01.y));
-        __syncthreads();
-        if (t == 0) issue(x + kDepth - 1);
-        const float2* fr = sF + b * S;
-        float2 kxf = f2(0.0f), kyf = f2(0.0f);
+        for (int j = 0; j < 6; ++j) w[j] = w[j + 2];
+        if (!mbar_wait(&xch[b], (p >> 1) & 1, g.err, g.wait_ns)) *sAbort = 1;
+        if (*sAbort) break;
+        issue(p + kPairDepth - 1);
+        // force term: K_x f and K_y f at both cells (rows packed)
+        const float4* fr = sF + b * VY * SP;
+        float2 kx0 = f2(0.0f), kx1 = f2(0.0f), ky0 = f2(0.0f), ky1 = f2(0.0f);
 #pragma unroll
         for (int i = 0; i < QX2; ++i) {
-            const float2 fv = fr[jy * QX2 + i];
-            kxf.x = fmaf(kx[i], fv.x, kxf.x);
-            kxf.y = fmaf(kx[i], fv.y, kxf.y);
+            const float4 fv = fr[jy * SP + i];
+            kx0 = __ffma2_rn(f2(kx[i]), make_float2(fv.x, fv.y), kx0);
+            kx1 = __ffma2_rn(f2(kx[i]), make_float2(fv.z, fv.w), kx1);
         }
 #pragma unroll
         for (int j = 0; j < VY; ++j) {
-            const float2 fv = fr[j * QX2 + ix];
-            kyf.x = fmaf(ky[j], fv.x, kyf.x);
-            kyf.y = fmaf(ky[j], fv.y, kyf.y);
+            const float4 fv = fr[j * SP + ix];
+            ky0 = __ffma2_rn(f2(ky[j]), make_float2(fv.x, fv.y), ky0);
+            ky1 = __ffma2_rn(f2(ky[j]), make_float2(fv.z, fv.w), ky1);
         }
-        const float* c0 = B.coef[0];
-        const float* c1 = B.coef[1];
-        const float2 feq = make_float2(c0[ix] * c0[QX2 + jy] * c0[csrc_z], c1[ix] * c1[QX2 + jy] * c1[csrc_z]);
-        const float2 itau = make_float2(c0[csrc_t], c1[csrc_t]);
-        // L = -div_x - div_y - (a_x K_x f + a_y K_y f) - (f - feq)/tau
-        float2 L = __fadd2_rn(divx, divy);
-        L = __ffma2_rn(ax2, kxf, L);
-        L = __ffma2_rn(ay2, kyf, L);
-        L = __ffma2_rn(__fadd2_rn(fc, __fmul2_rn(f2(-1.0f), feq)), itau, L);
-        L = __fmul2_rn(f2(-1.0f), L);
-        float2 out;
-        if (stage == 0) {
-            out = __ffma2_rn(dt2, L, fc);
-        } else {
-            const float2 fo_n = make_float2(B.fnr[0][vl], B.fnr[1][vl]);
-            if (stage == 1)
-                out = __ffma2_rn(f2(0.75f), fo_n, __fmul2_rn(f2(0.25f), __ffma2_rn(dt2, L, fc)));
-            else
-                out = __ffma2_rn(f2(1.0f / 3.0f), fo_n, __fmul2_rn(f2(2.0f / 3.0f), __ffma2_rn(dt2, L, fc)));
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (i == 1 && !two) break;
+            const float* c0 = B.coef[0] + i * ncp;
+            const float* c1 = B.coef[1] + i * ncp;
+            const float2 feq = __fmul2_rn(__fmul2_rn(make_float2(c0[ix], c1[ix]), make_float2(c0[QX2 + jy], c1[QX2 + jy])),
+                                          make_float2(c0[csrc_z], c1[csrc_z]));
+            const float2 itau = make_float2(c0[csrc_t], c1[csrc_t]);
+            const float2 fc = i ? fc1 : fc0;
+            const float2 divx = i ? divx1 : divx0;
+            const float2 divy = i ? make_float2(dy0.y, dy1.y) : make_float2(dy0.x, dy1.x);
+            // L = -div_x - div_y - (a_x K_x f + a_y K_y f) - (f - feq)/tau
+            float2 L = __fadd2_rn(divx, divy);
+            L = __ffma2_rn(ax2, i ? kx1 : kx0, L);
+            L = __ffma2_rn(ay2, i ? ky1 : ky0, L);
+            L = __ffma2_rn(fsub2(fc, feq), itau, L);
+            float2 out;      // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
+            if (stage == 0) {
+                out = fsub2(fc, __fmul2_rn(dt2, L));
+            } else {
+                const float2 fo_n = make_float2(B.fnr[i][0][vl], B.fnr[i][1][vl]);
+                if (stage == 1)
+                    out = __ffma2_rn(f2(0.75f), fo_n, __fmul2_rn(f2(0.25f), fsub2(fc, __fmul2_rn(dt2, L))));
+                else
+                    out = __ffma2_rn(f2(1.0f / 3.0f), fo_n, __fmul2_rn(f2(2.0f / 3.0f), fsub2(fc, __fmul2_rn(dt2, L))));
+            }
+            const int x = x0 + i;
+            if (valid[0]) fov[roff[0] + x * V] = out.x;
+            if (valid[1]) fov[roff[1] + x * V] = out.y;
         }
-        if (valid[0]) fov[roff[0] + x * V] = out.x;
-        if (valid[1]) fov[roff[1] + x * V] = out.y;
+        if (++slot == kPairDepth) { slot = 0; phase ^= 1u; }
+    }
+    if (*sAbort && t == 0) {
+        // a wait ran out at pair pa: let the copies of the pairs issued since
+        // (pa .. pa + kPairDepth - 2) land before the CTA exits
+        for (int s2 = pa; s2 < npairs && s2 < pa + kPairDepth - 1; ++s2)
+            mbar_drain(&bars[s2 % kPairDepth], (s2 / kPairDepth) & 1, g.wait_ns);
     }
 }
 
@@ -779,7 +879,7 @@ template <typename R, int ADV, int QX2, int VY, int TY>
 static void launch_one(const GroupDev& g, const Work* works, int nworks, const void* fs, const void* fn,
                        void* fo, int stage, cudaStream_t st) {
     if constexpr (sizeof(R) == 4 && TY == 2) {
-        march2_kernel<ADV, QX2, VY><<<nworks, QX2 * VY, march_smem_bytes<R, QX2, VY, TY>(), st>>>(
+        march_pair_kernel<ADV, QX2, VY><<<nworks, QX2 * VY, pair_smem_bytes<QX2, VY>(), st>>>(
             g, works, (const float*)fs, (const float*)fn, (float*)fo, stage);
     } else {
         march_kernel<R, ADV, QX2, VY, TY><<<nworks, QX2 * VY, march_smem_bytes<R, QX2, VY, TY>(), st>>>(
@@ -790,10 +890,11 @@ static void launch_one(const GroupDev& g, const Work* works, int nworks, const v
 template <typename R, int ADV, int QX2, int VY, int TY>
 static cudaError_t prepare_one() {
     if constexpr (sizeof(R) == 4 && TY == 2)
-        return cudaFuncSetAttribute(march2_kernel<ADV, QX2, VY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(march_pair_kernel<ADV, QX2, VY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)pair_smem_bytes<QX2, VY>());
+    else
+        return cudaFuncSetAttribute(march_kernel<R, ADV, QX2, VY, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)march_smem_bytes<R, QX2, VY, TY>());
-    return cudaFuncSetAttribute(march_kernel<R, ADV, QX2, VY, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)march_smem_bytes<R, QX2, VY, TY>());
 }
 
 bool march_available(int precision, int adv, int QX2, int VY, int TY) {

@@ -70,6 +70,8 @@ SIGNATURES = {
     "hlb_axis": (C.c_int, [C.c_int, C.c_int, _D, _D, _D]),
     "hlb_set_options": (C.c_int, [_P, C.c_int, C.c_int]),
     "hlb_kernel_times": (C.c_int, [_P, _D, _LL, _D, _LL, C.c_int]),
+    "hlb_launch_count": (C.c_int, [_P, _LL, C.c_int]),
+    "hlb_set_wait_test": (C.c_int, [_P, C.c_int, C.c_double]),
     "hlb_last_error": (C.c_char_p, []),
     "hlb_version": (C.c_char_p, []),
 }
@@ -227,6 +229,14 @@ class Handle:
         sn, wn = C.c_longlong(), C.c_longlong()
         _check(lib().hlb_kernel_times(self._h, C.byref(sm), C.byref(sn), C.byref(wm), C.byref(wn), int(reset)))
         return dict(stage_ms=sm.value, stage_launches=sn.value, wall_ms=wm.value, wall_launches=wn.value)
+
+    def launch_count(self, reset=True) -> int:
+        n = C.c_longlong()
+        _check(lib().hlb_launch_count(self._h, C.byref(n), int(reset)))
+        return n.value
+
+    def set_wait_test(self, withhold_copies: bool, wait_limit_s: float = 0.0):
+        _check(lib().hlb_set_wait_test(self._h, int(bool(withhold_copies)), float(wait_limit_s)))
 
 
 def equilibrium_x(Qx: int, u: float, T: float, Nx_eq: int = -1) -> np.ndarray:

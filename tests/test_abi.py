@@ -91,3 +91,17 @@ def test_invalid_axis_and_equilibrium_arguments(hlb_lib):
         hlb.axis(3, False)            # odd full-range order (Sec. IV.A.1)
     with pytest.raises(hlb.HlbError):
         hlb.equilibrium_x(4, 0.0, -1.0)
+
+
+def test_null_handle_is_rejected(hlb_lib):
+    # every handle-taking entry point answers HLB_EINVAL for NULL before any CUDA call
+    import ctypes as C
+    L = hlb_lib
+    LL = C.c_longlong()
+    D = C.c_double()
+    assert L.hlb_step(None, 1) == hlb.HLB_EINVAL
+    assert L.hlb_set_options(None, 1, 0) == hlb.HLB_EINVAL
+    assert L.hlb_launch_count(None, C.byref(LL), 0) == hlb.HLB_EINVAL
+    assert L.hlb_set_wait_test(None, 1, 0.01) == hlb.HLB_EINVAL
+    assert L.hlb_get_dt(None, 0, C.byref(D)) == hlb.HLB_EINVAL
+    L.hlb_destroy(None)                      # a no-op

@@ -182,6 +182,26 @@ def test_fp32_large_2d_1024_velocities(adv):
     _check_fp32(got, mom, refs)
 
 
+@pytest.mark.parametrize("nx", [13, 31, 55])
+def test_fp32_2d_ragged_pairs(nx):
+    # The pair kernel advances two cells per iteration: segments of odd length
+    # (nx = 13: one segment; 31, 55: a full segment of 24 and a ragged one)
+    # end on a single cell.  Stretched grid, walls at different temperatures,
+    # forces along p_x and p_y.
+    cfg = W.make(Qx=4, Qy=4, nx=nx, ny=5, Ly=0.25, stretch_A=0.6, advection=W.WENO5, precision=W.FP32,
+                 T_left=0.8, T_right=1.4, ax=-0.3, ay=0.2, Kn=0.1)
+    got, mom, N, refs = run_pair(cfg, 6, init=(1.0, 0.05, -0.03, 1.0))
+    _check_fp32(got, mom, refs)
+
+
+@pytest.mark.parametrize("adv", [W.WENO5, W.UPWIND2])
+def test_fp32_2d_q8_16x8(adv):
+    cfg = W.make(Qx=8, Qy=8, nx=27, ny=6, Ly=0.3, advection=adv, precision=W.FP32,
+                 T_left=1.0, T_right=2.0, ax=-0.3, ay=-0.3, Kn=0.5)
+    got, mom, N, refs = run_pair(cfg, 4)
+    _check_fp32(got, mom, refs)
+
+
 def test_fp32_batched_mixed_instances():
     insts = W.batched_instances(6)
     insts = [W.scaled(c, nx=min(c["nx"], 40)) for c in insts]
