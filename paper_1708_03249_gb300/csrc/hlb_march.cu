@@ -517,7 +517,13 @@ struct PairBuf {
     float coef[2][2 * NCPMAX];  // [row]: factor lines of cells x0, x0+1
 };
 
-constexpr int kPairDepth = 4;   // pairs of cells in flight (copy buffers)
+#ifndef HLB_PAIR_DEPTH
+#define HLB_PAIR_DEPTH 3
+#endif
+#ifndef HLB_PAIR_MIN_BLOCKS
+#define HLB_PAIR_MIN_BLOCKS 5
+#endif
+constexpr int kPairDepth = HLB_PAIR_DEPTH;   // pairs of cells in flight (copy buffers)
 
 template <int QX2, int VY>
 constexpr size_t pair_smem_bytes() {
@@ -525,7 +531,7 @@ constexpr size_t pair_smem_bytes() {
 }
 
 template <int ADV, int QX2, int VY>
-__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? 4 : 1)))
+__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? HLB_PAIR_MIN_BLOCKS : 1)))
 march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
                   const float* __restrict__ fn, float* __restrict__ fo, int stage) {
     constexpr int S = QX2 * VY;
