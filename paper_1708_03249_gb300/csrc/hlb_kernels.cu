@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "hlb_internal.h"
 #include "hlb_device.cuh"
@@ -323,19 +324,31 @@ wall_kernel(const GroupDev g, const R* __restrict__ fs) {
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
         const int ix = v % QX2;
         const double px = g.pd[ix];
-        double f0, f1, f2;
-        if (px < 0) {       // incident on the left wall: face -1/2
-            f0 = frow[v]; f1 = frow[(size_t)V + v]; f2 = frow[2 * (size_t)V + v];
-        } else {            // incident on the right wall: face nx-1/2
-            f0 = frow[(size_t)(nx - 1) * V + v]; f1 = frow[(size_t)(nx - 2) * V + v];
-            f2 = frow[(size_t)(nx - 3) * V + v];
-        }
+        const size_t a = px < 0 ? 0 : (size_t)(nx - 1) * V, step = px < 0 ? (size_t)V : (size_t)0 - (size_t)V;
+        // incident on the left wall (face -1/2) or on the right one (face nx-1/2):
+        // f0 the wall cell, f1 and f2 the next two inward
         double F;
-        if (ADV == HLB_WENO5_) {
-            const double d = 3.0 * f0 - 3.0 * f1 + f2, e = 6.0 * f0 - 8.0 * f1 + 3.0 * f2;
-            F = px * weno5_face<double>(f2, f1, f0, d, e);
+        if constexpr (sizeof(R) == 4) {
+            // the stage kernels' FP32 face: stencil scaled by 1/w, ghosts
+            // extrapolated from the scaled values
+            const float sv = static_cast<const float*>(g.wscale)[v];
+            const float f0 = frow[a + v] * sv, f1 = frow[a + step + v] * sv, f2 = frow[a + 2 * step + v] * sv;
+            float face;
+            if (ADV == HLB_WENO5_) {
+                const float d = 3.0f * f0 - 3.0f * f1 + f2, e = 6.0f * f0 - 8.0f * f1 + 3.0f * f2;
+                face = weno5_scaled(f2, f1, f0, d, e);
+            } else {
+                face = upwind2_face<float>(f1, f0);
+            }
+            F = (double)(((float)px * (1.0f / sv)) * face);
         } else {
-            F = px * upwind2_face<double>(f1, f0);
+            const double f0 = frow[a + v], f1 = frow[a + step + v], f2 = frow[a + 2 * step + v];
+            if (ADV == HLB_WENO5_) {
+                const double d = 3.0 * f0 - 3.0 * f1 + f2, e = 6.0 * f0 - 8.0 * f1 + 3.0 * f2;
+                F = px * weno5_face<double>(f2, f1, f0, d, e);
+            } else {
+                F = px * upwind2_face<double>(f1, f0);
+            }
         }
         if (px < 0) accL += F; else accR += F;
     }
@@ -362,45 +375,66 @@ __global__ void broadcast_kernel(R* __restrict__ f, const R* __restrict__ g, lon
         f[i] = g[i % V];
 }
 
-// One warp per node; two passes (mean velocity, then central moments).
-template <typename R>
-__global__ void moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double* u_out,
-                               double* T_out, double* q_out, int node_base) {
+// One warp per node; two passes over the node's values (mean velocity, then
+// central moments; the second pass re-reads them from L1).  Lanes accumulate
+// in the state's precision from a shared table of (p_x, p_y, p_z) per
+// velocity; the warp sums and everything after them are FP64.
+template <typename R, typename R4>
+__device__ __forceinline__ R4 velocity_of(const R* P, int v, int QX2, int VY) {
+    R4 m;
+    m.x = P[v % QX2]; m.y = P[QX2 + (v / QX2) % VY]; m.z = P[QX2 + VY + v / (QX2 * VY)]; m.w = R(0);
+    return m;
+}
+
+// kTable: (p_x, p_y, p_z) of every velocity staged in shared memory (sets of
+// up to kMomentTableMax velocities); otherwise formed per value.
+constexpr int kMomentTableMax = 1536;
+
+template <typename R, bool kTable>
+__global__ void __launch_bounds__(256)
+moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double* u_out,
+               double* T_out, double* q_out, int node_base) {
+    using R4 = typename std::conditional<sizeof(R) == 4, float4, double4>::type;
+    extern __shared__ __align__(16) unsigned char mom_smem[];
+    R4* sP = reinterpret_cast<R4*>(mom_smem);            // [V]: p_x, p_y, p_z
+    const int V = g.V, QX2 = g.QX2, VY = g.VY;
+    const R* P = static_cast<const R*>(g.p);
+    if (kTable) {
+        for (int v = threadIdx.x; v < V; v += blockDim.x) sP[v] = velocity_of<R, R4>(P, v, QX2, VY);
+        __syncthreads();
+    }
+    auto pv = [&](int v) -> R4 { return kTable ? sP[v] : velocity_of<R, R4>(P, v, QX2, VY); };
     const int warps = (blockDim.x >> 5) * gridDim.x;
     const int lane = threadIdx.x & 31;
     for (int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); node < g.nnodes; node += warps) {
         const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
-        const InstDev I = g.inst[ii];
-        const int local = node - I.node_off;
-        const R* f = fs + (size_t)I.f_off + (size_t)local * g.V;
-        const double* px = g.pd;
-        const double* py = g.pd + g.QX2;
-        const double* pz = py + g.VY;
-        double n = 0, jx = 0, jy = 0, jz = 0;
-        for (int v = lane; v < g.V; v += 32) {
-            const int ix = v % g.QX2, j = (v / g.QX2) % g.VY, k = v / (g.QX2 * g.VY);
-            const double val = f[v];
-            n += val; jx += px[ix] * val; jy += py[j] * val; jz += pz[k] * val;
+        const InstDev& I = g.inst[ii];
+        const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int v = lane; v < V; v += 32) {
+            const R val = f[v];
+            const R4 p = pv(v);
+            a0 += val; a1 += p.x * val; a2 += p.y * val; a3 += p.z * val;
         }
-        n = warp_sum(n); jx = warp_sum(jx); jy = warp_sum(jy); jz = warp_sum(jz);
-        const double ux = jx / n, uy = jy / n, uz = jz / n;
-        double e = 0, q = 0;
-        for (int v = lane; v < g.V; v += 32) {
-            const int ix = v % g.QX2, j = (v / g.QX2) % g.VY, k = v / (g.QX2 * g.VY);
-            const double val = f[v];
-            const double cx = px[ix] - ux, cy = py[j] - uy, cz = pz[k] - uz;
-            const double c2 = cx * cx + cy * cy + cz * cz;
-            e += c2 * val;
-            q += cx * c2 * val;
+        const double n = warp_sum((double)a0);
+        const double ux = warp_sum((double)a1) / n, uy = warp_sum((double)a2) / n, uz = warp_sum((double)a3) / n;
+        const R rux = (R)ux, ruy = (R)uy, ruz = (R)uz;
+        R e = 0, q = 0;
+        for (int v = lane; v < V; v += 32) {
+            const R val = f[v];
+            const R4 p = pv(v);
+            const R cx = p.x - rux, cy = p.y - ruy, cz = p.z - ruz;
+            const R c2v = (cx * cx + cy * cy + cz * cz) * val;
+            e += c2v;
+            q += cx * c2v;
         }
-        e = warp_sum(e);
-        q = warp_sum(q);
+        const double E = warp_sum((double)e), Q = warp_sum((double)q);
         if (lane == 0) {
             const long long o = node_base + node;
             if (n_out) n_out[o] = n;
             if (u_out) { u_out[3 * o] = ux; u_out[3 * o + 1] = uy; u_out[3 * o + 2] = uz; }
-            if (T_out) T_out[o] = e / (g.D * n);
-            if (q_out) q_out[o] = 0.5 * q;
+            if (T_out) T_out[o] = E / (g.D * n);
+            if (q_out) q_out[o] = 0.5 * Q;
         }
     }
 }
@@ -495,9 +529,15 @@ void launch_broadcast(int precision, void* f, const void* gvec, long long nvalue
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
                     double* q, int node_base, cudaStream_t st) {
     const int block = 256;
-    const int grid = (g.nnodes + 7) / 8 < 4096 ? (g.nnodes + 7) / 8 : 4096;
-    if (precision == HLB_FP64_) moments_kernel<double><<<grid, block, 0, st>>>(g, (const double*)fs, n, u, T, q, node_base);
-    else moments_kernel<float><<<grid, block, 0, st>>>(g, (const float*)fs, n, u, T, q, node_base);
+    const int grid = (g.nnodes + 7) / 8 < 152 * 8 ? (g.nnodes + 7) / 8 : 152 * 8;
+    const bool table = g.V <= kMomentTableMax;
+    if (precision == HLB_FP64_) {
+        if (table) moments_kernel<double, true><<<grid, block, g.V * sizeof(double4), st>>>(g, (const double*)fs, n, u, T, q, node_base);
+        else moments_kernel<double, false><<<grid, block, 0, st>>>(g, (const double*)fs, n, u, T, q, node_base);
+    } else {
+        if (table) moments_kernel<float, true><<<grid, block, g.V * sizeof(float4), st>>>(g, (const float*)fs, n, u, T, q, node_base);
+        else moments_kernel<float, false><<<grid, block, 0, st>>>(g, (const float*)fs, n, u, T, q, node_base);
+    }
 }
 
 void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out, cudaStream_t st) {

@@ -249,6 +249,129 @@ __global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __r
     }
 }
 
+// FP32 groups whose equilibrium orders are all below NM (double-float path):
+// one thread per node, coefficients in registers.  The FP64 prelude (erf,
+// exp, sqrt) runs once per node on full warps; each role's recurrence is
+// followed at once by its dot products with the quadrature tables (broadcast
+// reads from shared memory); a warp's 32 factor lines are assembled in shared
+// memory and written out contiguously.
+template <int NM>
+__device__ __forceinline__ void half_range_G_df(int r, const NodeDF& in, const float2* recf, int Nx, float2 (&G)[NM]) {
+    const float2* ra = recf;
+    const float2* rb = recf + Nx;
+    const float2* rc = recf + 2 * Nx;
+    const float2* h0 = recf + 3 * Nx;
+    const float2* inv_ra = recf + 4 * Nx + 1;
+    const float sg = r ? -1.0f : 1.0f;
+    const float2 us = make_float2(sg * in.ux.x, sg * in.ux.y);
+    const float2 half = df_add(make_float2(0.5f, 0.0f), make_float2(0.5f * sg * in.erf_z.x, 0.5f * sg * in.erf_z.y));
+    G[0] = df_mul(h0[0], half);
+    const float2 m_om0 = make_float2(-3.989422917e-01f, 1.133517014e-08f);   // -1/sqrt(2 pi)
+    float2 S = make_float2(0.0f, 0.0f), gm1 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int l = 0; l < NM - 1; ++l) {
+        if (l < Nx) {
+            float2 ig = df_mul(df_mul(m_om0, h0[l]), S);
+            if (l) ig = df_add(ig, df_mul(gm1, inv_ra[l - 1]));
+            const float2 pg = df_add(df_mul(us, G[l]), df_mul(in.T, df_add(df_mul(in.g0, h0[l]), ig)));
+            G[l + 1] = df_add(df_add(df_mul(ra[l], pg), df_mul(rb[l], G[l])), df_mul(rc[l], gm1));
+            S = df_add(S, df_mul(h0[l], G[l]));
+            gm1 = G[l];
+        }
+    }
+}
+
+template <int NM>
+__device__ __forceinline__ void full_range_G_df(float2 u, float2 Tm1, int N, float2 (&G)[NM]) {
+    G[0] = make_float2(1.0f, 0.0f);
+    G[1] = u;
+#pragma unroll
+    for (int l = 1; l < NM - 1; ++l)
+        if (l < N) G[l + 1] = df_add(df_mul(u, G[l]), df_mul(df_mul(make_float2((float)l, 0.0f), Tm1), G[l - 1]));
+}
+
+template <int NM>
+__device__ __forceinline__ float2 dot_df(const float2* Trow, const float2 (&G)[NM], int N) {
+    float2 acc = df_mul(Trow[0], G[0]);
+#pragma unroll
+    for (int l = 1; l < NM; ++l)
+        if (l <= N) acc = df_add(acc, df_mul(Trow[l], G[l]));
+    return acc;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const float* __restrict__ sums) {
+    extern __shared__ __align__(16) float2 cdf[];
+    const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz, Qx = g.Qx, QX2 = g.QX2, VY = g.VY, VZ = g.VZ, ncp = g.ncp;
+    const int nrec = 5 * Nx + 1;
+    const int nT = Qx * (Nx + 1) + VY * (Ny + 1) + VZ * (Nz + 1);
+    float2* sRec = cdf;
+    float2* sT = sRec + nrec;
+    float* sLine = reinterpret_cast<float*>(cdf + ((nrec + nT + 1) & ~1)) + (threadIdx.x >> 5) * 32 * ncp;   // [32][ncp] per warp
+    for (int i = threadIdx.x; i < nrec; i += blockDim.x) sRec[i] = g.recf[i];
+    for (int i = threadIdx.x; i < nT; i += blockDim.x) sT[i] = g.Tf[i];
+    __syncthreads();
+    const float2* sTx = sT;
+    const float2* sTy = sTx + Qx * (Nx + 1);
+    const float2* sTz = sTy + VY * (Ny + 1);
+    const int lane = threadIdx.x & 31;
+    const int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    const int node = base + lane;
+    float* line = sLine + lane * ncp;
+    if (node < g.nnodes) {
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const double inv_Kn = g.inst[ii].inv_Kn;
+        const float* sm = sums + (size_t)node * 8;
+        const float n = sm[0];
+        const float ux = sm[1] / n, uy = sm[2] / n, uz = sm[3] / n;
+        const float T = (sm[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
+        const double itau = (double)n * inv_Kn;
+        for (int o = QX2 + VY + VZ; o < ncp; ++o) line[o] = 0.0f;
+        line[QX2 + VY + VZ] = (float)itau;
+        if (itau == 0.0) {
+            for (int o = 0; o < QX2 + VY + VZ; ++o) line[o] = 0.0f;
+        } else {
+            NodeDF in;
+            node_inputs_df(n, ux, uy, uz, T, in);
+            float2 G[NM];
+#pragma unroll 1
+            for (int r = 0; r < 2; ++r) {                    // n g_x, p_x > 0 then p_x < 0
+                half_range_G_df<NM>(r, in, sRec, Nx, G);
+                for (int kk = 0; kk < Qx; ++kk) {
+                    const float2 v = df_mul(dot_df<NM>(sTx + kk * (Nx + 1), G, Nx), in.n);
+                    line[r * Qx + kk] = v.x + v.y;
+                }
+            }
+            if (g.Qy) {
+                full_range_G_df<NM>(in.uy, in.Tm1, Ny, G);
+                for (int j = 0; j < VY; ++j) {
+                    const float2 v = dot_df<NM>(sTy + j * (Ny + 1), G, Ny);
+                    line[QX2 + j] = v.x + v.y;
+                }
+            } else {
+                line[QX2] = 1.0f;
+            }
+            if (g.Qz) {
+                full_range_G_df<NM>(in.uz, in.Tm1, Nz, G);
+                for (int j = 0; j < VZ; ++j) {
+                    const float2 v = dot_df<NM>(sTz + j * (Nz + 1), G, Nz);
+                    line[QX2 + VY + j] = v.x + v.y;
+                }
+            } else {
+                line[QX2 + VY] = 1.0f;
+            }
+        }
+    }
+    __syncwarp();
+    // the warp's lines are contiguous in the factor-line buffer
+    const int nb = min(32, g.nnodes - base);
+    if (nb > 0) {
+        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(g.coef) + (size_t)base * ncp);
+        const float4* src = reinterpret_cast<const float4*>(sLine);
+        for (int i = lane; i < nb * ncp / 4; i += 32) dst[i] = src[i];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // march kernel
 // ---------------------------------------------------------------------------
@@ -846,6 +969,10 @@ cudaError_t prepare_node() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(coef_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_df_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_df_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sums_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sums_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
@@ -871,7 +998,16 @@ void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t 
         coef_kernel<double><<<blocks_b, block_b, smem_b, st>>>(g, (const double*)g.sums);
     } else {
         sums_kernel<float><<<blocks_a, 256, smem_a, st>>>(g, (const float*)fs, (float*)g.sums);
-        coef_kernel<float><<<blocks_b, block_b, smem_b, st>>>(g, (const float*)g.sums);
+        const int nmax = max(g.Nx, max(g.Ny, g.Nz));
+        if (g.use_df && nmax < 12) {
+            const int nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
+            const size_t smem_c = 8 * ((size_t)nrec + nT + 1) + 4 * 32 * (size_t)g.ncp * 4;
+            const int blocks_c = (g.nnodes + 127) / 128;
+            if (nmax < 8) coef_df_kernel<8><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
+            else coef_df_kernel<12><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
+        } else {
+            coef_kernel<float><<<blocks_b, block_b, smem_b, st>>>(g, (const float*)g.sums);
+        }
     }
 }
 
