@@ -648,9 +648,52 @@ struct PairBuf {
 #endif
 constexpr int kPairDepth = HLB_PAIR_DEPTH;   // pairs of cells in flight (copy buffers)
 
+// The force term by warp-level tensor-core products when both contractions
+// tile into 16 x 8 x 8 blocks.
+template <int QX2, int VY>
+// HLB_PAIR_MMA=1 takes the force term to the tensor cores (mma.sync, three
+// TF32 products); on the 1024 x 512 channel with 16 x 8 x 8 velocities it
+// measured 4.27 ms per stage launch against 3.87 ms for the FP32 FMA loop
+// (the fragment loads, splits and stores cost more issue slots than the
+// packed FMAs they replace), so it is off by default.
+#ifndef HLB_PAIR_MMA
+#define HLB_PAIR_MMA 0
+#endif
+__host__ __device__ constexpr bool pair_uses_mma() { return HLB_PAIR_MMA && QX2 % 8 == 0 && VY % 8 == 0; }
+
 template <int QX2, int VY>
 constexpr size_t pair_smem_bytes() {
-    return kPairDepth * sizeof(PairBuf<QX2, VY>) + 2 * VY * (QX2 + 1) * sizeof(float4) + (kPairDepth + 2) * 8 + 16;
+    return kPairDepth * sizeof(PairBuf<QX2, VY>) + (pair_uses_mma<QX2, VY>() ? 4 : 2) * VY * (QX2 + 1) * sizeof(float4) +
+           (kPairDepth + 3) * 8 + 16;
+}
+
+// D += A B on the tensor cores, TF32 operands, FP32 accumulation
+// (m16n8k8; A row-major 16 x 8, B column-major 8 x 8).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// x = hi + lo with hi a TF32 value (round to nearest); lo keeps the rest
+// (its own low bits are dropped by the tensor core).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+// D += A B in three TF32 products (A_lo B_hi + A_hi B_lo + A_hi B_hi), close
+// to an FP32 product; a[k] are FP32 values, b{0,1}{h,l} split fragments.
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&a)[4], uint32_t b0h, uint32_t b0l,
+                                           uint32_t b1h, uint32_t b1l) {
+    uint32_t ah[4], al[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) split_tf32(a[k], ah[k], al[k]);
+    mma_tf32(d, al[0], al[1], al[2], al[3], b0h, b1h);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0l, b1l);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0h, b1h);
 }
 
 template <int ADV, int QX2, int VY>
@@ -663,10 +706,15 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     using Buf = PairBuf<QX2, VY>;
     extern __shared__ __align__(128) unsigned char msm[];
     Buf* buf = reinterpret_cast<Buf*>(msm);
+    constexpr bool kMMA = pair_uses_mma<QX2, VY>();
     float4* sF = reinterpret_cast<float4*>(msm + kPairDepth * sizeof(Buf));   // [2][VY][SP]: (r0 x0, r1 x0, r0 x1, r1 x1)
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sF + 2 * VY * SP);   // bulk-copy pipeline
+    float4* sKx = sF + 2 * VY * SP;                   // [VY][SP]: a_x K_x f, same layout (tensor-core path)
+    float4* sKy = sKx + VY * SP;                      // [VY][SP]: a_y K_y f
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(sF + (kMMA ? 4 : 2) * VY * SP);   // bulk-copy pipeline
     unsigned long long* xch = bars + kPairDepth;       // [2]: sF[b] written by every warp
-    int* sAbort = reinterpret_cast<int*>(xch + 2);
+    unsigned long long* xch2 = xch + 2;                // sKx, sKy written by every warp
+    int* sAbort = reinterpret_cast<int*>(xch2 + 1);
 
     const Work W = works[blockIdx.x];
     const InstDev& I = g.inst[W.inst];
@@ -695,11 +743,37 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     const float sv = static_cast<const float*>(g.wscale)[v];
     const float isv = 1.0f / sv;
     const float* K = static_cast<const float*>(g.K);
-    float kx[QX2], ky[VY];
+    const int warp = t >> 5, lane = t & 31;
+    // FMA path: this thread's rows of K_x and K_y.  Tensor-core path: warp w
+    // computes one 16 x 8 tile of (a_x K_x f)^T and one of (a_y K_y f)^T, the
+    // contractions written as F^T K^T with F^T rows (j_y, cell/row) resp.
+    // (i_x, cell/row); the B fragments (a K)^T stay in registers, split hi/lo.
+    constexpr int KX = kMMA ? 1 : QX2, KY = kMMA ? 1 : VY;
+    float kx[KX], ky[KY];
+    constexpr int XS = QX2 / 8, YS = VY / 8;        // k-steps (tensor-core path)
+    uint32_t bxh[kMMA ? XS : 1][2], bxl[kMMA ? XS : 1][2], byh[kMMA ? YS : 1][2], byl[kMMA ? YS : 1][2];
+    const int mX = warp / (QX2 / 8 > 0 ? QX2 / 8 : 1), nX = warp % (QX2 / 8 > 0 ? QX2 / 8 : 1);
+    const int mY = warp / (VY / 8 > 0 ? VY / 8 : 1), nY = warp % (VY / 8 > 0 ? VY / 8 : 1);
+    const int gq = lane >> 2, tq = lane & 3;
+    if constexpr (kMMA) {
+        const float axf = (float)I.ax, ayf = (float)I.ay;
 #pragma unroll
-    for (int i = 0; i < QX2; ++i) kx[i] = K[ix * QX2 + i];
+        for (int ks = 0; ks < XS; ++ks)
 #pragma unroll
-    for (int j = 0; j < VY; ++j) ky[j] = K[QX2 * QX2 + jy * VY + j];
+            for (int h = 0; h < 2; ++h)      // B[k][n] = a_x K_x[8 nX + n][8 ks + k]
+                split_tf32(axf * K[(8 * nX + gq) * QX2 + 8 * ks + tq + 4 * h], bxh[ks][h], bxl[ks][h]);
+#pragma unroll
+        for (int ks = 0; ks < YS; ++ks)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)      // B[k][n] = a_y K_y[8 nY + n][8 ks + k]
+                split_tf32(ayf * K[QX2 * QX2 + (8 * nY + gq) * VY + 8 * ks + tq + 4 * h], byh[ks][h], byl[ks][h]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < QX2; ++i) kx[i] = K[ix * QX2 + i];
+#pragma unroll
+        for (int j = 0; j < VY; ++j) ky[j] = K[QX2 * QX2 + jy * VY + j];
+    }
+    (void)kx; (void)ky; (void)bxh; (void)bxl; (void)byh; (void)byl; (void)mX; (void)nX; (void)mY; (void)nY;
     const float2 ax2 = f2((float)I.ax), ay2 = f2((float)I.ay), dt2 = f2((float)I.dt);
     const float2 vxs = f2(vx * isv), vys = f2(vy * isv * (float)I.inv_dy), isv2 = f2(isv), sv2 = f2(sv);
     const float* invdx = static_cast<const float*>(g.inv_dx) + I.dx_off;
@@ -767,7 +841,6 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     // and x0+1, warp 2 the head rows and factor lines, warp 3 the f^n rows; a
     // single warp takes all 22.  Thread 0 registers each pair's byte count
     // (arrive.expect_tx) before any warp can issue that pair's copies.
-    const int warp = t >> 5, lane = t & 31;
     int my_copy = -1;
     if (S / 32 >= 4) {
         if (warp < 2 && lane < 6) my_copy = 6 * warp + lane;
@@ -799,6 +872,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
         for (int d = 0; d < kPairDepth; ++d) mbar_init(&bars[d], 1);
         mbar_init(&xch[0], S / 32);
         mbar_init(&xch[1], S / 32);
+        mbar_init(xch2, S / 32);
         *sAbort = 0;
         mbar_init_fence();
         for (int p = 0; p < kPairDepth - 1; ++p) expect(p);
@@ -858,12 +932,52 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     };
     float2 Fm = __fmul2_rn(vxs, face(xpos, w));
 
+    // a_x K_x f and a_y K_y f of one pair on the tensor cores: warp w takes
+    // the X tile (rows 16 mX.., columns 8 nX..) of (K_x-contraction)^T and the
+    // Y tile (rows 16 mY.., columns 8 nY..) of (K_y-contraction)^T and stores
+    // them in the layout of sF.
+    auto force_mma = [&](const float4* fr) {
+        const float* ff = reinterpret_cast<const float*>(fr);
+        float* kxo = reinterpret_cast<float*>(sKx);
+        float* kyo = reinterpret_cast<float*>(sKy);
+        const int R0 = 16 * mX + gq, jy0 = R0 >> 2, rx = R0 & 3;       // X rows: (j_y, cell/row)
+        float dx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < XS; ++ks) {
+            const int i0 = 8 * ks + tq;
+            const float a[4] = {ff[(jy0 * SP + i0) * 4 + rx], ff[((jy0 + 2) * SP + i0) * 4 + rx],
+                                ff[(jy0 * SP + i0 + 4) * 4 + rx], ff[((jy0 + 2) * SP + i0 + 4) * 4 + rx]};
+            mma_3xtf32(dx, a, bxh[ks][0], bxl[ks][0], bxh[ks][1], bxl[ks][1]);
+        }
+        const int ixo = 8 * nX + 2 * tq;
+        kxo[(jy0 * SP + ixo) * 4 + rx] = dx[0];
+        kxo[(jy0 * SP + ixo + 1) * 4 + rx] = dx[1];
+        kxo[((jy0 + 2) * SP + ixo) * 4 + rx] = dx[2];
+        kxo[((jy0 + 2) * SP + ixo + 1) * 4 + rx] = dx[3];
+        const int Q0 = 16 * mY + gq, ix0 = Q0 >> 2, ry = Q0 & 3;       // Y rows: (i_x, cell/row)
+        float dy[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < YS; ++ks) {
+            const int j0 = 8 * ks + tq;
+            const float a[4] = {ff[(j0 * SP + ix0) * 4 + ry], ff[(j0 * SP + ix0 + 2) * 4 + ry],
+                                ff[((j0 + 4) * SP + ix0) * 4 + ry], ff[((j0 + 4) * SP + ix0 + 2) * 4 + ry]};
+            mma_3xtf32(dy, a, byh[ks][0], byl[ks][0], byh[ks][1], byl[ks][1]);
+        }
+        const int jyo = 8 * nY + 2 * tq;
+        kyo[(jyo * SP + ix0) * 4 + ry] = dy[0];
+        kyo[((jyo + 1) * SP + ix0) * 4 + ry] = dy[1];
+        kyo[(jyo * SP + ix0 + 2) * 4 + ry] = dy[2];
+        kyo[((jyo + 1) * SP + ix0 + 2) * 4 + ry] = dy[3];
+    };
+
     // Per pair: wait for its copies; write the centre values to sF[b] and
     // arrive on xch[b]; evaluate the faces (the other warps catch up
     // meanwhile); wait on xch[b]; then the force term, which reads every
-    // warp's sF[b].  Passing xch[b] of pair p also means every warp is done
-    // with pair p-1, so its copy buffer is refilled then.  Every wait is
-    // bounded, so no warp can be left waiting for good.
+    // warp's sF[b].  On the tensor-core path the force term sits between the
+    // x and the y faces and its tiles are exchanged through xch2.  Passing
+    // xch[b] of pair p also means every warp is done with pair p-1, so its
+    // copy buffer is refilled then.  Every wait is bounded, so no warp can be
+    // left waiting for good.
     int pa = 0, slot = 0;
     uint32_t phase = 0;
 #pragma unroll 1
@@ -880,13 +994,21 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
         const float2 fc0 = __fmul2_rn(w[3], isv2), fc1 = __fmul2_rn(w[4], isv2);
         sF[(b * VY + jy) * SP + ix] = make_float4(fc0.x, fc0.y, fc1.x, fc1.y);
         __syncwarp();
-        if ((t & 31) == 0) mbar_arrive(&xch[b]);
+        if (lane == 0) mbar_arrive(&xch[b]);
         // x faces x0+1/2, x0+3/2 (rows packed); x0-1/2 carried
         const float2 Fp0 = __fmul2_rn(vxs, face(xpos, w + 1));
         const float2 Fp1 = __fmul2_rn(vxs, face(xpos, w + 2));
         const float2 divx0 = __fmul2_rn(fsub2(Fp0, Fm), f2(invdx[x0]));
         const float2 divx1 = __fmul2_rn(fsub2(Fp1, Fp0), f2(two ? invdx[x0 + 1] : 0.0f));
         Fm = Fp1;
+        if constexpr (kMMA) {
+            if (!mbar_wait(&xch[b], (p >> 1) & 1, g.err, g.wait_ns)) *sAbort = 1;
+            if (*sAbort) break;
+            issue(p + kPairDepth - 1);
+            force_mma(sF + b * VY * SP);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(xch2);
+        }
         // y faces (periodic), cells packed: rows y0-3 .. y0+4 of columns x0, x0+1
         float2 col[8];
 #pragma unroll
@@ -901,23 +1023,33 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
         // shift the window by two cells
 #pragma unroll
         for (int j = 0; j < 6; ++j) w[j] = w[j + 2];
-        if (!mbar_wait(&xch[b], (p >> 1) & 1, g.err, g.wait_ns)) *sAbort = 1;
-        if (*sAbort) break;
-        issue(p + kPairDepth - 1);
-        // force term: K_x f and K_y f at both cells (rows packed)
-        const float4* fr = sF + b * VY * SP;
-        float2 kx0 = f2(0.0f), kx1 = f2(0.0f), ky0 = f2(0.0f), ky1 = f2(0.0f);
+        // force term at both cells (rows packed): a_x K_x f + a_y K_y f
+        float2 fk0, fk1;
+        if constexpr (kMMA) {
+            if (!mbar_wait(xch2, p & 1, g.err, g.wait_ns)) *sAbort = 1;
+            const float4 ex = sKx[jy * SP + ix], ey = sKy[jy * SP + ix];
+            fk0 = __fadd2_rn(make_float2(ex.x, ex.y), make_float2(ey.x, ey.y));
+            fk1 = __fadd2_rn(make_float2(ex.z, ex.w), make_float2(ey.z, ey.w));
+        } else {
+            if (!mbar_wait(&xch[b], (p >> 1) & 1, g.err, g.wait_ns)) *sAbort = 1;
+            if (*sAbort) break;
+            issue(p + kPairDepth - 1);
+            const float4* fr = sF + b * VY * SP;
+            float2 kx0 = f2(0.0f), kx1 = f2(0.0f), ky0 = f2(0.0f), ky1 = f2(0.0f);
 #pragma unroll
-        for (int i = 0; i < QX2; ++i) {
-            const float4 fv = fr[jy * SP + i];
-            kx0 = __ffma2_rn(f2(kx[i]), make_float2(fv.x, fv.y), kx0);
-            kx1 = __ffma2_rn(f2(kx[i]), make_float2(fv.z, fv.w), kx1);
-        }
+            for (int i = 0; i < QX2; ++i) {
+                const float4 fv = fr[jy * SP + i];
+                kx0 = __ffma2_rn(f2(kx[i]), make_float2(fv.x, fv.y), kx0);
+                kx1 = __ffma2_rn(f2(kx[i]), make_float2(fv.z, fv.w), kx1);
+            }
 #pragma unroll
-        for (int j = 0; j < VY; ++j) {
-            const float4 fv = fr[j * SP + ix];
-            ky0 = __ffma2_rn(f2(ky[j]), make_float2(fv.x, fv.y), ky0);
-            ky1 = __ffma2_rn(f2(ky[j]), make_float2(fv.z, fv.w), ky1);
+            for (int j = 0; j < VY; ++j) {
+                const float4 fv = fr[j * SP + ix];
+                ky0 = __ffma2_rn(f2(ky[j]), make_float2(fv.x, fv.y), ky0);
+                ky1 = __ffma2_rn(f2(ky[j]), make_float2(fv.z, fv.w), ky1);
+            }
+            fk0 = __ffma2_rn(ax2, kx0, __fmul2_rn(ay2, ky0));
+            fk1 = __ffma2_rn(ax2, kx1, __fmul2_rn(ay2, ky1));
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -931,9 +1063,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             const float2 divx = i ? divx1 : divx0;
             const float2 divy = i ? make_float2(dy0.y, dy1.y) : make_float2(dy0.x, dy1.x);
             // L = -div_x - div_y - (a_x K_x f + a_y K_y f) - (f - feq)/tau
-            float2 L = __fadd2_rn(divx, divy);
-            L = __ffma2_rn(ax2, i ? kx1 : kx0, L);
-            L = __ffma2_rn(ay2, i ? ky1 : ky0, L);
+            float2 L = __fadd2_rn(__fadd2_rn(divx, divy), i ? fk1 : fk0);
             L = __ffma2_rn(fsub2(fc, feq), itau, L);
             float2 out;      // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
             if (stage == 0) {
