@@ -410,23 +410,40 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
         const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
         const InstDev& I = g.inst[ii];
         const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
+        // 4-vector loads (V a multiple of 4 keeps every node 16-byte aligned),
+        // several in flight per lane
+        const bool vec = kTable && (V & 3) == 0;
         R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int v = lane; v < V; v += 32) {
-            const R val = f[v];
-            const R4 p = pv(v);
-            a0 += val; a1 += p.x * val; a2 += p.y * val; a3 += p.z * val;
+        auto acc1 = [&](R val, const R4& p) { a0 += val; a1 += p.x * val; a2 += p.y * val; a3 += p.z * val; };
+        if (vec) {
+            const R4* f4 = reinterpret_cast<const R4*>(f);
+#pragma unroll 4
+            for (int k = lane; k < (V >> 2); k += 32) {
+                const R4 x = f4[k];
+                acc1(x.x, sP[4 * k]); acc1(x.y, sP[4 * k + 1]); acc1(x.z, sP[4 * k + 2]); acc1(x.w, sP[4 * k + 3]);
+            }
+        } else {
+            for (int v = lane; v < V; v += 32) acc1(f[v], pv(v));
         }
         const double n = warp_sum((double)a0);
         const double ux = warp_sum((double)a1) / n, uy = warp_sum((double)a2) / n, uz = warp_sum((double)a3) / n;
         const R rux = (R)ux, ruy = (R)uy, ruz = (R)uz;
         R e = 0, q = 0;
-        for (int v = lane; v < V; v += 32) {
-            const R val = f[v];
-            const R4 p = pv(v);
+        auto acc2 = [&](R val, const R4& p) {
             const R cx = p.x - rux, cy = p.y - ruy, cz = p.z - ruz;
             const R c2v = (cx * cx + cy * cy + cz * cz) * val;
             e += c2v;
             q += cx * c2v;
+        };
+        if (vec) {
+            const R4* f4 = reinterpret_cast<const R4*>(f);
+#pragma unroll 4
+            for (int k = lane; k < (V >> 2); k += 32) {
+                const R4 x = f4[k];
+                acc2(x.x, sP[4 * k]); acc2(x.y, sP[4 * k + 1]); acc2(x.z, sP[4 * k + 2]); acc2(x.w, sP[4 * k + 3]);
+            }
+        } else {
+            for (int v = lane; v < V; v += 32) acc2(f[v], pv(v));
         }
         const double E = warp_sum((double)e), Q = warp_sum((double)q);
         if (lane == 0) {
