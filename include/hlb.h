@@ -118,20 +118,25 @@ hlb_status hlb_set_Kn(hlb_handle* h, int inst, double Kn);
 hlb_status hlb_init_equilibrium(hlb_handle* h, double n, double ux, double uy, double T);
 
 /* Enqueue `nsteps` RK-3 steps (Eq. "eq:rk3") on the handle's stream and
- * return without waiting.  Each step runs, per stage: the wall kernel (the
- * emitted densities n_w from the incident fluxes, FP64 balance) and the
- * fused stage kernel (moments, equilibrium, force, BGK, advection, RK
- * combination).  With graphs enabled (default) the steps are replayed from a
- * captured CUDA graph.  Errors: HLB_EINVAL (nsteps < 0), HLB_ECUDA. */
+ * return without waiting.  Each step runs, per stage: the node pass (moment
+ * sums, then n, u, T, 1/tau and the equilibrium factors per node, Eqs.
+ * "eq:fmoms", "eq:hh_gk", "eq:H_gk"), the wall kernel (the emitted densities
+ * n_w from the incident fluxes, FP64 balance) and the stage kernel (force,
+ * BGK, advection, RK combination).  Groups with a force along p_z and Q_z > 0
+ * run a fused per-node stage kernel instead of the first and last.  With
+ * graphs enabled (default) the steps are replayed from a captured CUDA graph.
+ * Errors: HLB_EINVAL (nsteps < 0), HLB_ECUDA. */
 hlb_status hlb_step(hlb_handle* h, long nsteps);
 
 /* Macroscopic moments of the current state (Eq. "eq:fmoms", App. A), in
  * FP64, for all nodes of all instances in state order.  n, T, q: one value
  * per node; u: 3 values per node (u_x, u_y, u_z).  T = sum |p-u|^2 f/(D n)
  * with D the number of momentum axes; q = q_x = sum (p_x-u_x)|p-u|^2 f/2.
- * Any output pointer may be NULL.  Synchronises the handle's stream.
- * Errors: HLB_ECUDA, HLB_ENONFINITE (a non-finite n or T; outputs are
- * still written). */
+ * Any output pointer may be NULL.  The values are copied from device memory
+ * straight into the caller's arrays (page-locked arrays avoid a staging
+ * copy).  Synchronises the handle's stream.  Errors: HLB_ECUDA, HLB_ETIMEOUT
+ * (a bounded device wait ran out since the last check), HLB_ENOMEM,
+ * HLB_ENONFINITE (a non-finite n or T; outputs are still written). */
 hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q);
 
 /* Same as hlb_moments, but the outputs are device arrays (each may be NULL);

@@ -36,6 +36,12 @@ struct DevBuf {
     ~DevBuf() { if (p) cudaFree(p); }
 };
 
+struct PinnedBuf {                           // page-locked host memory
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~PinnedBuf() { if (p) cudaFreeHost(p); }
+};
+
 struct Group {
     int precision = HLB_FP32, adv = HLB_WENO5;
     int Qx = 0, Qy = 0, Qz = 0, Nx = 0, Ny = 0, Nz = 0;
@@ -52,6 +58,7 @@ struct Group {
     int cur = 0, prev = -1;
     DevBuf d_inst, d_node_start, d_row_start, d_K, d_p, d_pd, d_T, d_rec, d_dx, d_gw, d_nw, d_resid;
     DevBuf d_mom;                            // moments scratch: 6 doubles per node
+    PinnedBuf h_mom;                         // pinned word for the non-finite flag (hlb_moments), first use
     DevBuf d_Td, d_invdx, d_wscale, d_coef, d_works, d_err, d_recf, d_Tf, d_sums;
     hlb::GroupDev dev{};
     int block = 256, grid = 1;
@@ -200,6 +207,7 @@ void fill_dev(Group& G) {
     d.sums = G.d_sums.p;
     d.ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
     d.err = (int*)G.d_err.p;
+    d.nonfinite = (int*)G.d_err.p + 1;
     d.recf = (const float2*)G.d_recf.p;
     d.Tf = (const float2*)G.d_Tf.p;
     d.use_df = (G.precision == HLB_FP32 && G.Nx <= 11) ? 1 : 0;
@@ -734,32 +742,45 @@ hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q
         hlb_status e = check_device_error(h);
         if (e != HLB_OK) return e;
     }
-    bool finite = true;
+    // every group: clear its non-finite flag, launch the moments kernel, copy
+    // each instance's moments straight into the caller's arrays (direct DMA
+    // when they are page-locked) and the flag into a small pinned word; then
+    // one synchronisation
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
+        if (!G.h_mom.p) {
+            if (cudaMallocHost(&G.h_mom.p, 16) != cudaSuccess) {
+                cudaGetLastError();
+                G.h_mom.p = nullptr;
+                return fail(HLB_ENOMEM, "cudaMallocHost of the moments flag failed");
+            }
+            G.h_mom.bytes = 16;
+        }
         double* m = (double*)G.d_mom.p;
+        HLB_CUDA(cudaMemsetAsync(G.dev.nonfinite, 0, sizeof(int), h->stream));
         hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + G.nnodes, m + 4LL * G.nnodes,
                             m + 5LL * G.nnodes, 0, h->stream);
         HLB_CUDA(cudaGetLastError());
-        std::vector<double> host((size_t)G.nnodes * 6);
-        HLB_CUDA(cudaMemcpyAsync(host.data(), m, host.size() * 8, cudaMemcpyDeviceToHost, h->stream));
-        HLB_CUDA(cudaStreamSynchronize(h->stream));
-        const double* hn = host.data();
-        const double* hu = hn + G.nnodes;
-        const double* hT = hn + 4LL * G.nnodes;
-        const double* hq = hn + 5LL * G.nnodes;
+        const double* dn = m;
+        const double* du = m + G.nnodes;
+        const double* dT = m + 4LL * G.nnodes;
+        const double* dq = m + 5LL * G.nnodes;
         for (size_t k = 0; k < G.members.size(); ++k) {
             const long long go = h->inst_node_off[G.members[k]];
-            for (int j = G.node_start[k]; j < G.node_start[k + 1]; ++j) {
-                const long long o = go + (j - G.node_start[k]);
-                if (n) n[o] = hn[j];
-                if (u) { u[3 * o] = hu[3 * j]; u[3 * o + 1] = hu[3 * j + 1]; u[3 * o + 2] = hu[3 * j + 2]; }
-                if (T) T[o] = hT[j];
-                if (q) q[o] = hq[j];
-                if (!std::isfinite(hn[j]) || !std::isfinite(hT[j])) finite = false;
-            }
+            const int j0 = G.node_start[k];
+            const size_t cnt = (size_t)(G.node_start[k + 1] - j0);
+            const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+            if (n) HLB_CUDA(cudaMemcpyAsync(n + go, dn + j0, cnt * 8, d2h, h->stream));
+            if (u) HLB_CUDA(cudaMemcpyAsync(u + 3 * go, du + 3LL * j0, 3 * cnt * 8, d2h, h->stream));
+            if (T) HLB_CUDA(cudaMemcpyAsync(T + go, dT + j0, cnt * 8, d2h, h->stream));
+            if (q) HLB_CUDA(cudaMemcpyAsync(q + go, dq + j0, cnt * 8, d2h, h->stream));
         }
+        HLB_CUDA(cudaMemcpyAsync(G.h_mom.p, G.dev.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     }
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    bool finite = true;
+    for (auto& Gp : h->groups)
+        if (*(const int*)Gp->h_mom.p) finite = false;
     if (!finite) return fail(HLB_ENONFINITE, "non-finite moments in the state");
     return HLB_OK;
 }

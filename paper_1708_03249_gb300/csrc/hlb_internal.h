@@ -90,6 +90,7 @@ struct GroupDev {
     const void* gw;          // R: wall Maxwellians
     double* nw;              // FP64 [nrows][2] emitted densities
     int* err;                // device error word (0 = ok; else an hlb_status)
+    int* nonfinite;          // set by the moments kernel when a node's n or T is not finite
     unsigned long long wait_ns;   // bound of every pipeline wait in the marching kernels
     int inject_stall;        // test hook: nonzero withholds the copies of a marching CTA's second step
 };

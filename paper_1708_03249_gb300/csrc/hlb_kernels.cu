@@ -375,10 +375,17 @@ __global__ void broadcast_kernel(R* __restrict__ f, const R* __restrict__ g, lon
         f[i] = g[i % V];
 }
 
-// One warp per node; two passes over the node's values (mean velocity, then
-// central moments; the second pass re-reads them from L1).  Lanes accumulate
-// in the state's precision from a shared table of (p_x, p_y, p_z) per
-// velocity; the warp sums and everything after them are FP64.
+// One warp per node, one pass over the node's values: the raw quadrature sums
+// n, j, P_xa = sum p_x p_a f, E = sum |p|^2 f and Q = sum p_x |p|^2 f, from which
+// (FP64, per node)
+//   u = j/n,  T = (E - n|u|^2)/(D n),
+//   q_x = (1/2) sum (p_x - u_x)|p - u|^2 f
+//       = (1/2) [Q - 2 (u_x P_xx + u_y P_xy + u_z P_xz) - u_x E + 2 n u_x |u|^2].
+// Lanes and the warp tree accumulate in the state's precision; the per-node
+// combination is FP64.  With
+// 4 | 2Q_x and 2Q_x | 128 the lanes read 4-vectors whose p_x are fixed per
+// lane (as in sums_kernel); otherwise a shared table of (p_x, p_y, p_z) per
+// velocity (up to kMomentTableMax velocities) or per-value index arithmetic.
 template <typename R, typename R4>
 __device__ __forceinline__ R4 velocity_of(const R* P, int v, int QX2, int VY) {
     R4 m;
@@ -386,8 +393,6 @@ __device__ __forceinline__ R4 velocity_of(const R* P, int v, int QX2, int VY) {
     return m;
 }
 
-// kTable: (p_x, p_y, p_z) of every velocity staged in shared memory (sets of
-// up to kMomentTableMax velocities); otherwise formed per value.
 constexpr int kMomentTableMax = 1536;
 
 template <typename R, bool kTable>
@@ -396,62 +401,93 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
                double* T_out, double* q_out, int node_base) {
     using R4 = typename std::conditional<sizeof(R) == 4, float4, double4>::type;
     extern __shared__ __align__(16) unsigned char mom_smem[];
-    R4* sP = reinterpret_cast<R4*>(mom_smem);            // [V]: p_x, p_y, p_z
-    const int V = g.V, QX2 = g.QX2, VY = g.VY;
+    R4* sP = reinterpret_cast<R4*>(mom_smem);            // [V]: p_x, p_y, p_z   (kTable)
+    R4* sYZ = sP + (kTable ? g.V : 0);                   // [VY VZ]: p_y, p_z, p_y^2 + p_z^2
+    const int V = g.V, QX2 = g.QX2, VY = g.VY, VZ = g.VZ;
     const R* P = static_cast<const R*>(g.p);
+    const bool vec4 = (QX2 & 3) == 0 && (QX2 & (QX2 - 1)) == 0 && QX2 <= 128;
     if (kTable) {
         for (int v = threadIdx.x; v < V; v += blockDim.x) sP[v] = velocity_of<R, R4>(P, v, QX2, VY);
+        for (int k = threadIdx.x; k < VY * VZ; k += blockDim.x) {
+            R4 y;
+            y.x = P[QX2 + k % VY]; y.y = P[QX2 + VY + k / VY]; y.z = y.x * y.x + y.y * y.y; y.w = R(0);
+            sYZ[k] = y;
+        }
         __syncthreads();
     }
-    auto pv = [&](int v) -> R4 { return kTable ? sP[v] : velocity_of<R, R4>(P, v, QX2, VY); };
+    // Nodes go to warps in batches of 32: the warp forms the sums of each node
+    // of its batch together (butterfly sums leave them in every lane) and lane
+    // k keeps node k's; then every lane finishes its own node in FP64 (on full
+    // warps: a lone lane's FP64 instruction costs a whole warp's) and the
+    // outputs are written coalesced.
     const int warps = (blockDim.x >> 5) * gridDim.x;
     const int lane = threadIdx.x & 31;
-    for (int node = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); node < g.nnodes; node += warps) {
-        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
-        const InstDev& I = g.inst[ii];
-        const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
-        // 4-vector loads (V a multiple of 4 keeps every node 16-byte aligned),
-        // several in flight per lane
-        const bool vec = kTable && (V & 3) == 0;
-        R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        auto acc1 = [&](R val, const R4& p) { a0 += val; a1 += p.x * val; a2 += p.y * val; a3 += p.z * val; };
-        if (vec) {
-            const R4* f4 = reinterpret_cast<const R4*>(f);
-#pragma unroll 4
-            for (int k = lane; k < (V >> 2); k += 32) {
-                const R4 x = f4[k];
-                acc1(x.x, sP[4 * k]); acc1(x.y, sP[4 * k + 1]); acc1(x.z, sP[4 * k + 2]); acc1(x.w, sP[4 * k + 3]);
+    for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < g.nnodes; base += warps * 32) {
+        const int nb = min(32, g.nnodes - base);
+        R mine[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) mine[k] = R(0);
+        for (int kn = 0; kn < nb; ++kn) {
+            const int node = base + kn;
+            const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+            const InstDev& I = g.inst[ii];
+            const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
+            // n, j_x, j_y, j_z, P_xx, E - P_xx, P_xy, P_xz, Q
+            R a[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+            if (kTable && vec4) {
+                const R4* f4 = reinterpret_cast<const R4*>(f);
+                const int x0 = (4 * lane) % QX2;
+                R px[4], px2[4], px3[4];
+    #pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    px[e] = P[x0 + e]; px2[e] = px[e] * px[e]; px3[e] = px2[e] * px[e];
+                }
+    #pragma unroll 4
+                for (int k = lane; k < (V >> 2); k += 32) {
+                    const R4 x = f4[k];
+                    const R4 yz = sYZ[(k << 2) / QX2];
+                    const R sm = (x.x + x.y) + (x.z + x.w);
+                    const R jx = px[0] * x.x + px[1] * x.y + px[2] * x.z + px[3] * x.w;
+                    const R pxx = px2[0] * x.x + px2[1] * x.y + px2[2] * x.z + px2[3] * x.w;
+                    const R pxxx = px3[0] * x.x + px3[1] * x.y + px3[2] * x.z + px3[3] * x.w;
+                    a[0] += sm; a[1] += jx; a[2] += yz.x * sm; a[3] += yz.y * sm;
+                    a[4] += pxx; a[5] += yz.z * sm; a[6] += yz.x * jx; a[7] += yz.y * jx;
+                    a[8] += pxxx + yz.z * jx;
+                }
+            } else {
+                for (int v = lane; v < V; v += 32) {
+                    const R val = f[v];
+                    const R4 p = kTable ? sP[v] : velocity_of<R, R4>(P, v, QX2, VY);
+                    const R jx = p.x * val, yz2 = p.y * p.y + p.z * p.z;
+                    a[0] += val; a[1] += jx; a[2] += p.y * val; a[3] += p.z * val;
+                    a[4] += p.x * jx; a[5] += yz2 * val; a[6] += p.y * jx; a[7] += p.z * jx;
+                    a[8] += (p.x * p.x + yz2) * jx;
+                }
             }
-        } else {
-            for (int v = lane; v < V; v += 32) acc1(f[v], pv(v));
-        }
-        const double n = warp_sum((double)a0);
-        const double ux = warp_sum((double)a1) / n, uy = warp_sum((double)a2) / n, uz = warp_sum((double)a3) / n;
-        const R rux = (R)ux, ruy = (R)uy, ruz = (R)uz;
-        R e = 0, q = 0;
-        auto acc2 = [&](R val, const R4& p) {
-            const R cx = p.x - rux, cy = p.y - ruy, cz = p.z - ruz;
-            const R c2v = (cx * cx + cy * cy + cz * cz) * val;
-            e += c2v;
-            q += cx * c2v;
-        };
-        if (vec) {
-            const R4* f4 = reinterpret_cast<const R4*>(f);
-#pragma unroll 4
-            for (int k = lane; k < (V >> 2); k += 32) {
-                const R4 x = f4[k];
-                acc2(x.x, sP[4 * k]); acc2(x.y, sP[4 * k + 1]); acc2(x.z, sP[4 * k + 2]); acc2(x.w, sP[4 * k + 3]);
+            // warp sums in the state's precision (FP64 adds run at 1/64 of FP32 here)
+    #pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const R sk = warp_sum(a[k]);
+                if (lane == kn) mine[k] = sk;
             }
-        } else {
-            for (int v = lane; v < V; v += 32) acc2(f[v], pv(v));
         }
-        const double E = warp_sum((double)e), Q = warp_sum((double)q);
-        if (lane == 0) {
+        if (lane < nb) {
+            const int node = base + lane;
+            double d[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) d[k] = (double)mine[k];
+            const double n = d[0];
+            const double ux = d[1] / n, uy = d[2] / n, uz = d[3] / n;
+            const double u2 = ux * ux + uy * uy + uz * uz;
+            const double E = d[4] + d[5];
+            const double Tn = (E - n * u2) / (g.D * n);
+            const double qx = 0.5 * (d[8] - 2.0 * (ux * d[4] + uy * d[6] + uz * d[7]) - ux * E + 2.0 * n * ux * u2);
             const long long o = node_base + node;
             if (n_out) n_out[o] = n;
             if (u_out) { u_out[3 * o] = ux; u_out[3 * o + 1] = uy; u_out[3 * o + 2] = uz; }
-            if (T_out) T_out[o] = E / (g.D * n);
-            if (q_out) q_out[o] = 0.5 * Q;
+            if (T_out) T_out[o] = Tn;
+            if (q_out) q_out[o] = qx;
+            if (!(isfinite(n) && isfinite(Tn))) *g.nonfinite = 1;
         }
     }
 }
@@ -545,14 +581,14 @@ void launch_broadcast(int precision, void* f, const void* gvec, long long nvalue
 
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
                     double* q, int node_base, cudaStream_t st) {
-    const int block = 256;
-    const int grid = (g.nnodes + 7) / 8 < 152 * 8 ? (g.nnodes + 7) / 8 : 152 * 8;
-    const bool table = g.V <= kMomentTableMax;
+    const int block = 256;                               // 8 warps, 32 nodes per warp and batch
+    const int grid = (g.nnodes + 255) / 256 < 152 * 8 ? (g.nnodes + 255) / 256 : 152 * 8;
+    const bool table = g.V + g.VY * g.VZ <= kMomentTableMax;
     if (precision == HLB_FP64_) {
-        if (table) moments_kernel<double, true><<<grid, block, g.V * sizeof(double4), st>>>(g, (const double*)fs, n, u, T, q, node_base);
+        if (table) moments_kernel<double, true><<<grid, block, (g.V + g.VY * g.VZ) * sizeof(double4), st>>>(g, (const double*)fs, n, u, T, q, node_base);
         else moments_kernel<double, false><<<grid, block, 0, st>>>(g, (const double*)fs, n, u, T, q, node_base);
     } else {
-        if (table) moments_kernel<float, true><<<grid, block, g.V * sizeof(float4), st>>>(g, (const float*)fs, n, u, T, q, node_base);
+        if (table) moments_kernel<float, true><<<grid, block, (g.V + g.VY * g.VZ) * sizeof(float4), st>>>(g, (const float*)fs, n, u, T, q, node_base);
         else moments_kernel<float, false><<<grid, block, 0, st>>>(g, (const float*)fs, n, u, T, q, node_base);
     }
 }
