@@ -641,10 +641,10 @@ struct PairBuf {
 };
 
 #ifndef HLB_PAIR_DEPTH
-#define HLB_PAIR_DEPTH 3
+#define HLB_PAIR_DEPTH 2
 #endif
 #ifndef HLB_PAIR_MIN_BLOCKS
-#define HLB_PAIR_MIN_BLOCKS 5
+#define HLB_PAIR_MIN_BLOCKS 7
 #endif
 constexpr int kPairDepth = HLB_PAIR_DEPTH;   // pairs of cells in flight (copy buffers)
 
@@ -661,10 +661,16 @@ template <int QX2, int VY>
 #endif
 __host__ __device__ constexpr bool pair_uses_mma() { return HLB_PAIR_MMA && QX2 % 8 == 0 && VY % 8 == 0; }
 
+// FMA path: a_x K_x and a_y K_y rows in shared memory, every entry duplicated
+// into an f32x2 pair, rows padded by two pairs (a warp's eight rows fall in
+// distinct banks).
+template <int QX2, int VY>
+__host__ __device__ constexpr int pair_kdup_pairs() { return QX2 * (QX2 + 2) + VY * (VY + 2); }
+
 template <int QX2, int VY>
 constexpr size_t pair_smem_bytes() {
     return kPairDepth * sizeof(PairBuf<QX2, VY>) + (pair_uses_mma<QX2, VY>() ? 4 : 2) * VY * (QX2 + 1) * sizeof(float4) +
-           (kPairDepth + 3) * 8 + 16;
+           (pair_uses_mma<QX2, VY>() ? 0 : pair_kdup_pairs<QX2, VY>() * sizeof(float2)) + (kPairDepth + 3) * 8 + 16;
 }
 
 // D += A B on the tensor cores, TF32 operands, FP32 accumulation
@@ -710,8 +716,10 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     float4* sF = reinterpret_cast<float4*>(msm + kPairDepth * sizeof(Buf));   // [2][VY][SP]: (r0 x0, r1 x0, r0 x1, r1 x1)
     float4* sKx = sF + 2 * VY * SP;                   // [VY][SP]: a_x K_x f, same layout (tensor-core path)
     float4* sKy = sKx + VY * SP;                      // [VY][SP]: a_y K_y f
+    float2* sKd = reinterpret_cast<float2*>(sF + (kMMA ? 4 : 2) * VY * SP);    // FMA path: duplicated a K rows
+    constexpr int KXR = QX2 + 2, KYR = VY + 2;        // padded row lengths (pairs)
     unsigned long long* bars =
-        reinterpret_cast<unsigned long long*>(sF + (kMMA ? 4 : 2) * VY * SP);   // bulk-copy pipeline
+        reinterpret_cast<unsigned long long*>(sKd + (kMMA ? 0 : pair_kdup_pairs<QX2, VY>()));   // bulk-copy pipeline
     unsigned long long* xch = bars + kPairDepth;       // [2]: sF[b] written by every warp
     unsigned long long* xch2 = xch + 2;                // sKx, sKy written by every warp
     int* sAbort = reinterpret_cast<int*>(xch2 + 1);
@@ -748,8 +756,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     // computes one 16 x 8 tile of (a_x K_x f)^T and one of (a_y K_y f)^T, the
     // contractions written as F^T K^T with F^T rows (j_y, cell/row) resp.
     // (i_x, cell/row); the B fragments (a K)^T stay in registers, split hi/lo.
-    constexpr int KX = kMMA ? 1 : QX2, KY = kMMA ? 1 : VY;
-    float kx[KX], ky[KY];
+
     constexpr int XS = QX2 / 8, YS = VY / 8;        // k-steps (tensor-core path)
     uint32_t bxh[kMMA ? XS : 1][2], bxl[kMMA ? XS : 1][2], byh[kMMA ? YS : 1][2], byl[kMMA ? YS : 1][2];
     const int mX = warp / (QX2 / 8 > 0 ? QX2 / 8 : 1), nX = warp % (QX2 / 8 > 0 ? QX2 / 8 : 1);
@@ -768,13 +775,12 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             for (int h = 0; h < 2; ++h)      // B[k][n] = a_y K_y[8 nY + n][8 ks + k]
                 split_tf32(ayf * K[QX2 * QX2 + (8 * nY + gq) * VY + 8 * ks + tq + 4 * h], byh[ks][h], byl[ks][h]);
     } else {
-#pragma unroll
-        for (int i = 0; i < QX2; ++i) kx[i] = K[ix * QX2 + i];
-#pragma unroll
-        for (int j = 0; j < VY; ++j) ky[j] = K[QX2 * QX2 + jy * VY + j];
+        const float axf = (float)I.ax, ayf = (float)I.ay;
+        for (int e = t; e < QX2 * QX2; e += S) sKd[(e / QX2) * KXR + e % QX2] = f2(axf * K[e]);
+        for (int e = t; e < VY * VY; e += S) sKd[QX2 * KXR + (e / VY) * KYR + e % VY] = f2(ayf * K[QX2 * QX2 + e]);
     }
-    (void)kx; (void)ky; (void)bxh; (void)bxl; (void)byh; (void)byl; (void)mX; (void)nX; (void)mY; (void)nY;
-    const float2 ax2 = f2((float)I.ax), ay2 = f2((float)I.ay), dt2 = f2((float)I.dt);
+    (void)bxh; (void)bxl; (void)byh; (void)byl; (void)mX; (void)nX; (void)mY; (void)nY;
+    const float2 dt2 = f2((float)I.dt);
     const float2 vxs = f2(vx * isv), vys = f2(vy * isv * (float)I.inv_dy), isv2 = f2(isv), sv2 = f2(sv);
     const float* invdx = static_cast<const float*>(g.inv_dx) + I.dx_off;
     const int rs = nx * V;
@@ -1035,21 +1041,28 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             if (*sAbort) break;
             issue(p + kPairDepth - 1);
             const float4* fr = sF + b * VY * SP;
-            float2 kx0 = f2(0.0f), kx1 = f2(0.0f), ky0 = f2(0.0f), ky1 = f2(0.0f);
+            const float4* kxr = reinterpret_cast<const float4*>(sKd + ix * KXR);            // (k, k) pairs, two per load
+            const float4* kyr = reinterpret_cast<const float4*>(sKd + QX2 * KXR + jy * KYR);
+            fk0 = f2(0.0f);
+            fk1 = f2(0.0f);
 #pragma unroll
-            for (int i = 0; i < QX2; ++i) {
-                const float4 fv = fr[jy * SP + i];
-                kx0 = __ffma2_rn(f2(kx[i]), make_float2(fv.x, fv.y), kx0);
-                kx1 = __ffma2_rn(f2(kx[i]), make_float2(fv.z, fv.w), kx1);
+            for (int i = 0; i < QX2; i += 2) {
+                const float4 kk = kxr[i >> 1];
+                const float4 fa = fr[jy * SP + i], fb = fr[jy * SP + i + 1];
+                fk0 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), fk0);
+                fk1 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), fk1);
+                fk0 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), fk0);
+                fk1 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), fk1);
             }
 #pragma unroll
-            for (int j = 0; j < VY; ++j) {
-                const float4 fv = fr[j * SP + ix];
-                ky0 = __ffma2_rn(f2(ky[j]), make_float2(fv.x, fv.y), ky0);
-                ky1 = __ffma2_rn(f2(ky[j]), make_float2(fv.z, fv.w), ky1);
+            for (int j = 0; j < VY; j += 2) {
+                const float4 kk = kyr[j >> 1];
+                const float4 fa = fr[j * SP + ix], fb = fr[(j + 1) * SP + ix];
+                fk0 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), fk0);
+                fk1 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), fk1);
+                fk0 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), fk0);
+                fk1 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), fk1);
             }
-            fk0 = __ffma2_rn(ax2, kx0, __fmul2_rn(ay2, ky0));
-            fk1 = __ffma2_rn(ax2, kx1, __fmul2_rn(ay2, ky1));
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
