@@ -168,6 +168,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's);
+    x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each did units_per_rank
+    units in at most `seconds` (max over ranks)."""
+    return world * units_per_rank / seconds
+
+
 def roofline_of(hbm_achieved, hbm_peak, peak_kind, alu_achieved, alu_peak, sm_mhz, traffic, stage_avg_ms, kt,
                 flop_nv):
     """Both roofs of the stage kernel; the binding one (the larger fraction)
@@ -246,13 +263,10 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     kt = h.kernel_times(reset=True)
     launches = h.launch_count(reset=True)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     n, u, T, q = h.moments()
     finite = bool(np.isfinite(n).all() and np.isfinite(T).all())
-    value = world * nodes * V * args.steps / (ms * 1e-3)
+    value = job_rate(nodes * V * args.steps, world, ms * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D of the state from
     # pinned memory, one RK-3 step, D2H of the moments, every iteration
@@ -273,12 +287,8 @@ def run_gpu(args):
         hlb._check(lib.hlb_set_state(h._h, pinned.data_ptr(), state_bytes))
         h.step(1)
         hlb._check(lib.hlb_moments(h._h, *ptrs))
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * nodes * V * e2e_iters / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_rate(nodes * V * e2e_iters, world, e2e_s)
     h.close()
 
     if rank != 0:
