@@ -210,7 +210,7 @@ void fill_dev(Group& G) {
     d.nonfinite = (int*)G.d_err.p + 1;
     d.recf = (const float2*)G.d_recf.p;
     d.Tf = (const float2*)G.d_Tf.p;
-    d.use_df = (G.precision == HLB_FP32 && G.Nx <= 11) ? 1 : 0;
+    d.use_df = (G.precision == HLB_FP32 && G.Nx <= 15) ? 1 : 0;
     d.wait_ns = kDefaultWaitNs;
     d.inject_stall = 0;
 }

@@ -40,7 +40,7 @@ namespace {
 //                 line (dot products shared across the warp).
 // FP64 runs at 1/64 of FP32 here and a warp instruction costs the same
 // whatever its mask, so every FP64 instruction runs on full warps; FP32
-// groups with Nx <= 11 run the recurrences and dot products in double-float
+// groups with Nx <= 15 run the recurrences and dot products in double-float
 // (FP64 only for erf, exp, sqrt, once per node).
 template <typename R>
 __global__ void __launch_bounds__(256) sums_kernel(const GroupDev g, const R* __restrict__ fs, R* __restrict__ sums) {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __r
     }
 }
 
-// FP32 groups whose equilibrium orders are all below NM (double-float path):
+// FP32 groups whose equilibrium orders are all below NM (double-float path, orders up to 15):
 // one thread per node, coefficients in registers.  The FP64 prelude (erf,
 // exp, sqrt) runs once per node on full warps; each role's recurrence is
 // followed at once by its dot products with the quadrature tables (broadcast
@@ -1116,6 +1116,8 @@ cudaError_t prepare_node() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(coef_df_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_df_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sums_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sums_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
@@ -1142,12 +1144,13 @@ void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t 
     } else {
         sums_kernel<float><<<blocks_a, 256, smem_a, st>>>(g, (const float*)fs, (float*)g.sums);
         const int nmax = max(g.Nx, max(g.Ny, g.Nz));
-        if (g.use_df && nmax < 12) {
+        if (g.use_df && nmax < 16) {
             const int nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
             const size_t smem_c = 8 * ((size_t)nrec + nT + 1) + 4 * 32 * (size_t)g.ncp * 4;
             const int blocks_c = (g.nnodes + 127) / 128;
             if (nmax < 8) coef_df_kernel<8><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
-            else coef_df_kernel<12><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
+            else if (nmax < 12) coef_df_kernel<12><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
+            else coef_df_kernel<16><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
         } else {
             coef_kernel<float><<<blocks_b, block_b, smem_b, st>>>(g, (const float*)g.sums);
         }

@@ -169,6 +169,15 @@ def test_fp32_stretched_channel(Kn):
     _check_fp32(got, mom, refs)
 
 
+@pytest.mark.parametrize("TL,TR", [(0.5, 2.0), (1.0, 0.5)])
+def test_fp32_channel_q16(TL, TR):
+    # order 15 along p_x: the per-node equilibrium runs in double-float
+    cfg = W.make(Qx=16, Qy=16, nx=48, advection=W.WENO5, precision=W.FP32, T_left=TL, T_right=TR,
+                 Kn=0.1, **W.gravity(0.7, 60.0))
+    got, mom, N, refs = run_pair(cfg, 20, init=(1.0, 0.1, -0.1, 0.9))
+    _check_fp32(got, mom, refs)
+
+
 def test_fp32_box_2d_q16():
     cfg = W.scaled(W.BOX_2D, nx=12, ny=6)
     got, mom, N, refs = run_pair(cfg, 4)
