@@ -50,7 +50,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("hlb_march.cu", "hlb_device.cuh", "hlb_internal.h"):
+    for name in ("hlb_pair.cu", "hlb_device.cuh", "hlb_internal.h"):
         with open(os.path.join(ROOT, "paper_1708_03249_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -370,8 +370,11 @@ hlb_status build_group(hlb_handle* h, Group& G) {
         }
         G.march_ok = !small_ny && !big && hlb::march_available(G.precision, G.adv, G.QX2, G.VY, G.TY);
         if (G.march_ok) {
+            // segment length: about 4096 CTAs in 2D (strips of two rows), about
+            // 1216 (8 per SM) over the rows of 1D instances; at least 24 cells
+            // so that a CTA's window and table set-up is amortised, at most 512
             const long long rows = xwork / std::max(1LL, (long long)G.TY);
-            long long sx = rows / 4096;
+            long long sx = rows / (two_d ? 4096 : 1216);
             sx = std::max(24LL, std::min(512LL, (sx + 5) / 6 * 6));
             G.SX = (int)sx;
             std::vector<hlb::Work> works;

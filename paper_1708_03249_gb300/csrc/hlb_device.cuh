@@ -101,6 +101,12 @@ __device__ __forceinline__ float weno5_face_sv<float>(float a, float b, float c,
 template <typename R>
 __device__ __forceinline__ R upwind2_face(R b, R c) { return R(1.5) * c - R(0.5) * b; }
 
+// Shared-memory footprint, in f32x2 pairs, of the a_x K_x and a_y K_y rows of
+// the FP32 marching kernels: every entry duplicated into a pair, rows padded
+// by two pairs so that a warp's rows fall in distinct banks.
+template <int QX2, int VY>
+__host__ __device__ constexpr int pair_kdup_pairs() { return QX2 * (QX2 + 2) + VY * (VY + 2); }
+
 // 1/x on the special-function unit (x >= 1e-30 here; beyond 1e38 it flushes to 0).
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;

@@ -97,7 +97,7 @@ struct GroupDev {
 
 }  // namespace hlb
 
-// Launchers (hlb_kernels.cu).
+// Launchers (hlb_kernels.cu, hlb_node.cu, hlb_march.cu, hlb_pair.cu, hlb_line.cu).
 #include <cuda_runtime.h>
 namespace hlb {
 size_t stage_smem_bytes(const GroupDev& g, int precision, int block);
@@ -113,6 +113,16 @@ bool march_available(int precision, int adv, int QX2, int VY, int TY);
 cudaError_t prepare_march(int precision, int adv, int QX2, int VY, int TY);
 void launch_march(int precision, int adv, int QX2, int VY, int TY, const GroupDev& g, const Work* works,
                   int nworks, const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
+// FP32 marching kernels of hlb_pair.cu (2D strips of two rows) and
+// hlb_line.cu (1D rows).
+bool line_available(int QX2, int VY);
+cudaError_t prepare_line(int adv, int QX2, int VY);
+void launch_line(int adv, int QX2, int VY, const GroupDev& g, const Work* works, int nworks, const void* fs,
+                 const void* fn, void* fo, int stage, cudaStream_t st);
+bool pair_available(int QX2, int VY);
+cudaError_t prepare_pair(int adv, int QX2, int VY);
+void launch_pair(int adv, int QX2, int VY, const GroupDev& g, const Work* works, int nworks, const void* fs,
+                 const void* fn, void* fo, int stage, cudaStream_t st);
 void launch_broadcast(int precision, void* f, const void* gvec, long long nvalues, int V, cudaStream_t st);
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
                     double* q, int node_base, cudaStream_t st);

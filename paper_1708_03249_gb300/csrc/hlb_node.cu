@@ -1,0 +1,413 @@
+// Node pass of an RK-3 stage (sm_103a): the quadrature sums of every node
+// (Eq. "eq:fmoms"), then n, u, T, 1/tau and the per-node equilibrium factor
+// line coef[node] = { n g_x (2Qx), g_y (Qy), g_z (Qz), 1/tau } (Eqs.
+// "eq:hh_gk", "eq:H_gk", App. A; half-range recurrence in the orthonormal
+// basis, full-range Hermite recurrence).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "hlb_device.cuh"
+#include "hlb_internal.h"
+
+namespace hlb {
+namespace {
+
+// ---------------------------------------------------------------------------
+// node kernel
+// ---------------------------------------------------------------------------
+// Per-node equilibrium factors, in two passes with no block-wide barrier:
+//   sums_kernel   streams the stage input once (one warp per node) and writes
+//                 the five quadrature sums n, j_x, j_y, j_z, E per node;
+//   coef_kernel   one warp per 32 nodes, one lane per node: n, u, T, then the
+//                 coefficient recurrences of all four roles, then the factor
+//                 line (dot products shared across the warp).
+// FP64 runs at 1/64 of FP32 here and a warp instruction costs the same
+// whatever its mask, so every FP64 instruction runs on full warps; FP32
+// groups with Nx <= 15 run the recurrences and dot products in double-float
+// (FP64 only for erf, exp, sqrt, once per node).
+template <typename R>
+__global__ void __launch_bounds__(256) sums_kernel(const GroupDev g, const R* __restrict__ fs, R* __restrict__ sums) {
+    extern __shared__ __align__(16) double ssm[];
+    using R4 = typename std::conditional<sizeof(R) == 4, float4, double4>::type;
+    const int QX2 = g.QX2, VY = g.VY, VZ = g.VZ, V = g.V;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = bs >> 5;
+    R4* sM = reinterpret_cast<R4*>(ssm);                 // [V]: p_x, p_y, p_z, |p|^2
+    R4* sYZ = sM + V;                                    // [VY * VZ]: p_y, p_z, p_y^2 + p_z^2
+    const R* px = static_cast<const R*>(g.p);
+    const R* py = px + QX2;
+    const R* pz = py + VY;
+    for (int v = tid; v < V; v += bs) {
+        const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
+        const R a = px[ix], b = py[jy], c = pz[kz];
+        R4 m4;
+        m4.x = a; m4.y = b; m4.z = c; m4.w = a * a + b * b + c * c;
+        sM[v] = m4;
+    }
+    for (int bq = tid; bq < VY * VZ; bq += bs) {
+        const R b = py[bq % VY], c = pz[bq / VY];
+        R4 y4;
+        y4.x = b; y4.y = c; y4.z = b * b + c * c; y4.w = R(0);
+        sYZ[bq] = y4;
+    }
+    __syncthreads();
+    // 4-vector loads need 4 | 2Qx and 2Qx | 128 (2Qx a power of two up to 128):
+    // then 4 consecutive velocities share (jy, kz) and a lane's p_x never change
+    const bool vec4 = (QX2 & 3) == 0 && (QX2 & (QX2 - 1)) == 0 && QX2 <= 128;
+    for (int node = blockIdx.x * nw + warp; node < g.nnodes; node += gridDim.x * nw) {
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const InstDev& I = g.inst[ii];
+        const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+        if (vec4) {
+            const R4* f4 = reinterpret_cast<const R4*>(f);
+            const int x0 = (4 * lane) % QX2;
+            const R pxa = sM[x0].x, pxb = sM[x0 + 1].x, pxc = sM[x0 + 2].x, pxd = sM[x0 + 3].x;
+#pragma unroll 4
+            for (int q = lane; q < (V >> 2); q += 32) {
+                const R4 x = f4[q];
+                const R4 yz = sYZ[(q << 2) / QX2];
+                const R s = (x.x + x.y) + (x.z + x.w);
+                a0 += s;
+                a1 += pxa * x.x + pxb * x.y + pxc * x.z + pxd * x.w;
+                a2 += yz.x * s;
+                a3 += yz.y * s;
+                a4 += pxa * pxa * x.x + pxb * pxb * x.y + pxc * pxc * x.z + pxd * pxd * x.w + yz.z * s;
+            }
+        } else {
+            for (int v = lane; v < V; v += 32) {
+                const R val = f[v];
+                const R4 mw = sM[v];
+                a0 += val;
+                a1 += mw.x * val;
+                a2 += mw.y * val;
+                a3 += mw.z * val;
+                a4 += mw.w * val;
+            }
+        }
+        a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
+        if (lane == 0) {
+            R* o = sums + (size_t)node * 8;
+            o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = a4;
+        }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __restrict__ sums) {
+    extern __shared__ __align__(16) double csm[];
+    const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz;
+    const int nrec = 5 * Nx + 1;
+    const int nT = g.Qx * (Nx + 1) + g.VY * (Ny + 1) + g.VZ * (Nz + 1);
+    const int ncoef = 2 * (Nx + 1) + (Ny + 1) + (Nz + 1);
+    const int QX2 = g.QX2, VY = g.VY, VZ = g.VZ;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = bs >> 5;
+    const bool df = g.use_df != 0;
+    double* sRec = csm;
+    double* sT = sRec + nrec;
+    double* sW = sT + nT;                                // per warp: [32][ncoef] coefficients + [32] state
+    const int per_warp = 32 * ncoef + 32 * 2 + 32 * (int)(sizeof(NodeDF) / 8);
+    double* sG = sW + warp * per_warp;
+    double* sNT = sG + 32 * ncoef;                       // [32][2]: n, 1/tau
+    NodeDF* sIn = reinterpret_cast<NodeDF*>(sNT + 64);   // [32]
+    float2* sRecF = reinterpret_cast<float2*>(sRec);
+    float2* sTF = reinterpret_cast<float2*>(sT);
+    float2* sGF = reinterpret_cast<float2*>(sG);
+    if (df) {
+        for (int i = tid; i < nrec; i += bs) sRecF[i] = g.recf[i];
+        for (int i = tid; i < nT; i += bs) sTF[i] = g.Tf[i];
+    } else {
+        for (int i = tid; i < nrec; i += bs) sRec[i] = g.rec[i];
+        for (int i = tid; i < nT; i += bs) sT[i] = g.Td[i];
+    }
+    __syncthreads();
+    const double* sTx = sT;
+    const double* sTy = sTx + g.Qx * (Nx + 1);
+    const double* sTz = sTy + VY * (Ny + 1);
+    const float2* sTxF = sTF;
+    const float2* sTyF = sTxF + g.Qx * (Nx + 1);
+    const float2* sTzF = sTyF + VY * (Ny + 1);
+    R* coef = static_cast<R*>(g.coef);
+    const int nf = QX2 + VY + VZ;
+    const int nbatches = (g.nnodes + 31) / 32;
+    for (int bt = blockIdx.x * nw + warp; bt < nbatches; bt += gridDim.x * nw) {
+        const int base = bt * 32;
+        const int nb = min(32, g.nnodes - base);
+        // 1. lane = node: n, u, T, 1/tau; the recurrences' FP64 inputs
+        bool active = false;
+        if (lane < nb) {
+            const int node = base + lane;
+            const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+            const double inv_Kn = g.inst[ii].inv_Kn;
+            const R* sm = sums + (size_t)node * 8;
+            active = inv_Kn != 0.0;
+            double ux, uy, uz, T, n;
+            if (df) {
+                const float nf32 = (float)sm[0];
+                const float fx = (float)sm[1] / nf32, fy = (float)sm[2] / nf32, fz = (float)sm[3] / nf32;
+                const float fT = ((float)sm[4] - nf32 * (fx * fx + fy * fy + fz * fz)) / (g.D * nf32);
+                n = nf32; ux = fx; uy = fy; uz = fz; T = fT;
+            } else {
+                n = (double)sm[0];
+                ux = (double)sm[1] / n; uy = (double)sm[2] / n; uz = (double)sm[3] / n;
+                T = ((double)sm[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
+            }
+            sNT[2 * lane] = n;
+            sNT[2 * lane + 1] = n * inv_Kn;
+            if (active) {
+                if (df) {
+                    node_inputs_df(n, ux, uy, uz, T, sIn[lane]);
+                    for (int role = 0; role < 4; ++role)
+                        node_coefficients_df(g, role, sIn[lane], sRecF, sGF + lane * ncoef);
+                } else {
+                    for (int role = 0; role < 4; ++role)
+                        node_coefficients(g, role, ux, uy, uz, T, sRec, sG + lane * ncoef);
+                }
+            }
+        }
+        __syncwarp();
+        // 2. factor lines: lanes over (node, output), one loop per output kind
+        //    so that the lanes of a warp follow the same path
+        for (int t = lane; t < nb * QX2; t += 32) {          // n g_x
+            const int k = t / QX2, o = t - k * QX2;
+            R* line = coef + (size_t)(base + k) * g.ncp;
+            if (sNT[2 * k + 1] == 0.0) { line[o] = R(0); continue; }
+            const int kk = o % g.Qx, sg = o / g.Qx;
+            if (df) {
+                const float2* Gs = sGF + k * ncoef + sg * (Nx + 1);
+                const float2* Tr = sTxF + kk * (Nx + 1);
+                float2 acc = df_mul(Tr[0], Gs[0]);
+                for (int l = 1; l <= Nx; ++l) acc = df_add(acc, df_mul(Tr[l], Gs[l]));
+                acc = df_mul(acc, sIn[k].n);
+                line[o] = (R)(acc.x + acc.y);
+            } else {
+                const double* Gs = sG + k * ncoef + sg * (Nx + 1);
+                const double* Tr = sTx + kk * (Nx + 1);
+                double acc = 0.0;
+                for (int l = 0; l <= Nx; ++l) acc += Tr[l] * Gs[l];
+                line[o] = (R)(acc * sNT[2 * k]);
+            }
+        }
+        for (int t = lane; t < nb * VY; t += 32) {           // g_y
+            const int k = t / VY, j = t - k * VY;
+            R* line = coef + (size_t)(base + k) * g.ncp + QX2;
+            if (sNT[2 * k + 1] == 0.0) { line[j] = R(0); continue; }
+            if (!g.Qy) { line[j] = R(1); continue; }
+            if (df) {
+                const float2* Gy = sGF + k * ncoef + 2 * (Nx + 1);
+                const float2* Tr = sTyF + j * (Ny + 1);
+                float2 acc = df_mul(Tr[0], Gy[0]);
+                for (int l = 1; l <= Ny; ++l) acc = df_add(acc, df_mul(Tr[l], Gy[l]));
+                line[j] = (R)(acc.x + acc.y);
+            } else {
+                const double* Gy = sG + k * ncoef + 2 * (Nx + 1);
+                const double* Tr = sTy + j * (Ny + 1);
+                double acc = 0.0;
+                for (int l = 0; l <= Ny; ++l) acc += Tr[l] * Gy[l];
+                line[j] = (R)acc;
+            }
+        }
+        for (int t = lane; t < nb * VZ; t += 32) {           // g_z
+            const int k = t / VZ, j = t - k * VZ;
+            R* line = coef + (size_t)(base + k) * g.ncp + QX2 + VY;
+            if (sNT[2 * k + 1] == 0.0) { line[j] = R(0); continue; }
+            if (!g.Qz) { line[j] = R(1); continue; }
+            if (df) {
+                const float2* Gz = sGF + k * ncoef + 2 * (Nx + 1) + (Ny + 1);
+                const float2* Tr = sTzF + j * (Nz + 1);
+                float2 acc = df_mul(Tr[0], Gz[0]);
+                for (int l = 1; l <= Nz; ++l) acc = df_add(acc, df_mul(Tr[l], Gz[l]));
+                line[j] = (R)(acc.x + acc.y);
+            } else {
+                const double* Gz = sG + k * ncoef + 2 * (Nx + 1) + (Ny + 1);
+                const double* Tr = sTz + j * (Nz + 1);
+                double acc = 0.0;
+                for (int l = 0; l <= Nz; ++l) acc += Tr[l] * Gz[l];
+                line[j] = (R)acc;
+            }
+        }
+        if (lane < nb) coef[(size_t)(base + lane) * g.ncp + nf] = (R)sNT[2 * lane + 1];   // 1/tau
+        __syncwarp();
+    }
+}
+
+// FP32 groups whose equilibrium orders are all below NM (double-float path, orders up to 15):
+// one thread per node, coefficients in registers.  The FP64 prelude (erf,
+// exp, sqrt) runs once per node on full warps; each role's recurrence is
+// followed at once by its dot products with the quadrature tables (broadcast
+// reads from shared memory); a warp's 32 factor lines are assembled in shared
+// memory and written out contiguously.
+template <int NM>
+__device__ __forceinline__ void half_range_G_df(int r, const NodeDF& in, const float2* recf, int Nx, float2 (&G)[NM]) {
+    const float2* ra = recf;
+    const float2* rb = recf + Nx;
+    const float2* rc = recf + 2 * Nx;
+    const float2* h0 = recf + 3 * Nx;
+    const float2* inv_ra = recf + 4 * Nx + 1;
+    const float sg = r ? -1.0f : 1.0f;
+    const float2 us = make_float2(sg * in.ux.x, sg * in.ux.y);
+    const float2 half = df_add(make_float2(0.5f, 0.0f), make_float2(0.5f * sg * in.erf_z.x, 0.5f * sg * in.erf_z.y));
+    G[0] = df_mul(h0[0], half);
+    const float2 m_om0 = make_float2(-3.989422917e-01f, 1.133517014e-08f);   // -1/sqrt(2 pi)
+    float2 S = make_float2(0.0f, 0.0f), gm1 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int l = 0; l < NM - 1; ++l) {
+        if (l < Nx) {
+            float2 ig = df_mul(df_mul(m_om0, h0[l]), S);
+            if (l) ig = df_add(ig, df_mul(gm1, inv_ra[l - 1]));
+            const float2 pg = df_add(df_mul(us, G[l]), df_mul(in.T, df_add(df_mul(in.g0, h0[l]), ig)));
+            G[l + 1] = df_add(df_add(df_mul(ra[l], pg), df_mul(rb[l], G[l])), df_mul(rc[l], gm1));
+            S = df_add(S, df_mul(h0[l], G[l]));
+            gm1 = G[l];
+        }
+    }
+}
+
+template <int NM>
+__device__ __forceinline__ void full_range_G_df(float2 u, float2 Tm1, int N, float2 (&G)[NM]) {
+    G[0] = make_float2(1.0f, 0.0f);
+    G[1] = u;
+#pragma unroll
+    for (int l = 1; l < NM - 1; ++l)
+        if (l < N) G[l + 1] = df_add(df_mul(u, G[l]), df_mul(df_mul(make_float2((float)l, 0.0f), Tm1), G[l - 1]));
+}
+
+template <int NM>
+__device__ __forceinline__ float2 dot_df(const float2* Trow, const float2 (&G)[NM], int N) {
+    float2 acc = df_mul(Trow[0], G[0]);
+#pragma unroll
+    for (int l = 1; l < NM; ++l)
+        if (l <= N) acc = df_add(acc, df_mul(Trow[l], G[l]));
+    return acc;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const float* __restrict__ sums) {
+    extern __shared__ __align__(16) float2 cdf[];
+    const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz, Qx = g.Qx, QX2 = g.QX2, VY = g.VY, VZ = g.VZ, ncp = g.ncp;
+    const int nrec = 5 * Nx + 1;
+    const int nT = Qx * (Nx + 1) + VY * (Ny + 1) + VZ * (Nz + 1);
+    float2* sRec = cdf;
+    float2* sT = sRec + nrec;
+    float* sLine = reinterpret_cast<float*>(cdf + ((nrec + nT + 1) & ~1)) + (threadIdx.x >> 5) * 32 * ncp;   // [32][ncp] per warp
+    for (int i = threadIdx.x; i < nrec; i += blockDim.x) sRec[i] = g.recf[i];
+    for (int i = threadIdx.x; i < nT; i += blockDim.x) sT[i] = g.Tf[i];
+    __syncthreads();
+    const float2* sTx = sT;
+    const float2* sTy = sTx + Qx * (Nx + 1);
+    const float2* sTz = sTy + VY * (Ny + 1);
+    const int lane = threadIdx.x & 31;
+    const int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    const int node = base + lane;
+    float* line = sLine + lane * ncp;
+    if (node < g.nnodes) {
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const double inv_Kn = g.inst[ii].inv_Kn;
+        const float* sm = sums + (size_t)node * 8;
+        const float n = sm[0];
+        const float ux = sm[1] / n, uy = sm[2] / n, uz = sm[3] / n;
+        const float T = (sm[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
+        const double itau = (double)n * inv_Kn;
+        for (int o = QX2 + VY + VZ; o < ncp; ++o) line[o] = 0.0f;
+        line[QX2 + VY + VZ] = (float)itau;
+        if (itau == 0.0) {
+            for (int o = 0; o < QX2 + VY + VZ; ++o) line[o] = 0.0f;
+        } else {
+            NodeDF in;
+            node_inputs_df(n, ux, uy, uz, T, in);
+            float2 G[NM];
+#pragma unroll 1
+            for (int r = 0; r < 2; ++r) {                    // n g_x, p_x > 0 then p_x < 0
+                half_range_G_df<NM>(r, in, sRec, Nx, G);
+                for (int kk = 0; kk < Qx; ++kk) {
+                    const float2 v = df_mul(dot_df<NM>(sTx + kk * (Nx + 1), G, Nx), in.n);
+                    line[r * Qx + kk] = v.x + v.y;
+                }
+            }
+            if (g.Qy) {
+                full_range_G_df<NM>(in.uy, in.Tm1, Ny, G);
+                for (int j = 0; j < VY; ++j) {
+                    const float2 v = dot_df<NM>(sTy + j * (Ny + 1), G, Ny);
+                    line[QX2 + j] = v.x + v.y;
+                }
+            } else {
+                line[QX2] = 1.0f;
+            }
+            if (g.Qz) {
+                full_range_G_df<NM>(in.uz, in.Tm1, Nz, G);
+                for (int j = 0; j < VZ; ++j) {
+                    const float2 v = dot_df<NM>(sTz + j * (Nz + 1), G, Nz);
+                    line[QX2 + VY + j] = v.x + v.y;
+                }
+            } else {
+                line[QX2 + VY] = 1.0f;
+            }
+        }
+    }
+    __syncwarp();
+    // the warp's lines are contiguous in the factor-line buffer
+    const int nb = min(32, g.nnodes - base);
+    if (nb > 0) {
+        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(g.coef) + (size_t)base * ncp);
+        const float4* src = reinterpret_cast<const float4*>(sLine);
+        for (int i = lane; i < nb * ncp / 4; i += 32) dst[i] = src[i];
+    }
+}
+
+
+}  // namespace
+
+cudaError_t prepare_node() {
+    cudaError_t e = cudaFuncSetAttribute(coef_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_df_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_df_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(coef_df_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sums_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sums_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+}
+
+// Node pass of a stage: the quadrature sums of every node, then the factor
+// lines.  The sums live in the first 8 R of each node's factor line slot of
+// an auxiliary buffer (g.sums).
+void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t st) {
+    const size_t es = precision == HLB_FP64_ ? 8 : 4;
+    const size_t smem_a = 4 * (g.V + g.VY * g.VZ) * es;
+    const int blocks_a = (g.nnodes + 7) / 8 < 152 * 16 ? (g.nnodes + 7) / 8 : 152 * 16;
+    const int nrec = 5 * g.Nx + 1;
+    const int nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
+    const int ncoef = 2 * (g.Nx + 1) + (g.Ny + 1) + (g.Nz + 1);
+    const int block_b = 32;
+    const size_t per_warp = 8 * (32 * ncoef + 64) + 32 * sizeof(NodeDF);
+    const size_t smem_b = 8 * (nrec + nT) + (block_b / 32) * per_warp;
+    const int batches = (g.nnodes + 31) / 32;
+    const int blocks_b = batches;
+    if (precision == HLB_FP64_) {
+        sums_kernel<double><<<blocks_a, 256, smem_a, st>>>(g, (const double*)fs, (double*)g.sums);
+        coef_kernel<double><<<blocks_b, block_b, smem_b, st>>>(g, (const double*)g.sums);
+    } else {
+        sums_kernel<float><<<blocks_a, 256, smem_a, st>>>(g, (const float*)fs, (float*)g.sums);
+        const int nmax = max(g.Nx, max(g.Ny, g.Nz));
+        if (g.use_df && nmax < 16) {
+            const int nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
+            const size_t smem_c = 8 * ((size_t)nrec + nT + 1) + 4 * 32 * (size_t)g.ncp * 4;
+            const int blocks_c = (g.nnodes + 127) / 128;
+            if (nmax < 8) coef_df_kernel<8><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
+            else if (nmax < 12) coef_df_kernel<12><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
+            else coef_df_kernel<16><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
+        } else {
+            coef_kernel<float><<<blocks_b, block_b, smem_b, st>>>(g, (const float*)g.sums);
+        }
+    }
+}
+
+}  // namespace hlb

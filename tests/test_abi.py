@@ -115,7 +115,7 @@ def test_tensor_core_force_variant_compiles(tmp_path):
     from paper_1708_03249_gb300 import build as B
     if shutil.which(B.nvcc()) is None and not os.path.exists(B.nvcc()):
         pytest.skip("nvcc not available")
-    cmd = [B.nvcc(), "-c", os.path.join(B.CSRC, "hlb_march.cu"), "-o", str(tmp_path / "m.o"),
+    cmd = [B.nvcc(), "-c", os.path.join(B.CSRC, "hlb_pair.cu"), "-o", str(tmp_path / "m.o"),
            "-DHLB_PAIR_MMA=1"] + B._flags()
     res = subprocess.run(cmd, capture_output=True, text=True)
     assert res.returncode == 0, res.stderr[-2000:]

@@ -211,6 +211,17 @@ def test_fp32_2d_q8_16x8(adv):
     _check_fp32(got, mom, refs)
 
 
+@pytest.mark.parametrize("Qx,Qy,nx", [(16, 0, 31), (4, 0, 31), (8, 8, 55), (4, 4, 13)])
+def test_fp32_1d_shapes_ragged(Qx, Qy, nx):
+    # 1D FP32: the line kernel (two cells per iteration; whole-warp slabs:
+    # 32 x 1, 16 x 8, 8 x 4) and the scalar kernel (8 x 1); odd lengths end a
+    # segment on a single cell
+    cfg = W.make(Qx=Qx, Qy=Qy, nx=nx, advection=W.WENO5, precision=W.FP32, T_left=0.7, T_right=1.3,
+                 Kn=0.2, **(W.gravity(0.4, 30.0) if Qy else {"ax": -0.4}))
+    got, mom, N, refs = run_pair(cfg, 10, init=(1.0, 0.05, 0.0, 1.0))
+    _check_fp32(got, mom, refs)
+
+
 def test_fp32_batched_mixed_instances():
     insts = W.batched_instances(6)
     insts = [W.scaled(c, nx=min(c["nx"], 40)) for c in insts]

@@ -21,6 +21,9 @@ CASES = {
                            T_left=1.0, T_right=1.5, ax=-0.2, ay=0.1, Kn=0.3),
     # 1D FP64: the scalar marching kernel
     "scalar_fp64_1d": W.scaled(W.CHANNEL_1D_FP64, nx=40),
+    # 1D FP32: the line kernel (two cells per iteration)
+    "line_fp32_1d": W.make(Qx=8, Qy=8, nx=60, advection=W.WENO5, precision=W.FP32, T_left=1.0, T_right=1.4,
+                           Kn=0.3, **W.gravity(0.3, 20.0)),
 }
 
 
