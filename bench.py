@@ -122,23 +122,50 @@ class ClockSampler:
 # ------------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ------------------------------------------------------------------------------
-def oracle_sample(steps: int = 1, nx: int = 32, ny: int = 32):
-    """Time the FP64 oracle on an nx x ny window of the same workload (same
-    velocity set, physics and dt), ``steps`` RK-3 steps; returns (nv/s, secs, desc)."""
-    import numpy as np
-    from oracle.solver import Solver, config_from
+def window_config(nx: int = 32, ny: int = 32) -> dict:
+    """An nx x ny channel with the workload's velocity set, physics and cell
+    size (so the same dt)."""
     cfg = dict(W.LARGE_2D)
     full_dx = cfg["Lx"] / cfg["nx"]
     cfg.update(nx=nx, ny=ny, Lx=nx * full_dx, Ly=ny * full_dx)
+    return cfg
+
+
+def oracle_sample(steps: int = 1, nx: int = 32, ny: int = 32, keep: bool = False):
+    """Time the FP64 oracle on an nx x ny window of the same workload (same
+    velocity set, physics and dt), ``steps`` RK-3 steps; returns (nv/s, secs,
+    desc, cores) and, with keep, also (initial state, final moments)."""
+    from oracle.solver import Solver, config_from
+    cfg = window_config(nx, ny)
     s = Solver(config_from(cfg))
     s.init_equilibrium(1.0, 0.05, -0.02, 1.2)
     s.f *= W.perturbation(s.f.shape, seed=3, amplitude=0.02)
+    f0 = s.f.copy() if keep else None
     t0, c0 = time.perf_counter(), time.process_time()
     s.step(steps)
     dt, cpu = time.perf_counter() - t0, time.process_time() - c0
     nv = nx * ny * s.vs.V * steps
     desc = f"{nx}x{ny} nodes of the workload's velocity set x {steps} RK-3 step(s), FP64 numpy oracle"
-    return nv / dt, dt, desc, max(1, round(cpu / dt))
+    out = (nv / dt, dt, desc, max(1, round(cpu / dt)))
+    if keep:
+        n, u, T, q = s.moments()
+        out = out + (f0, (n.reshape(-1), u.reshape(-1, 3), T.reshape(-1), q.reshape(-1)))
+    return out
+
+
+def moment_errors(mom, ref) -> dict:
+    """L-infinity error of each moment against the FP64 oracle, relative to
+    max(max |M_ref|, s_M) with s_n = max n, s_u = sqrt(max T), s_T = max T,
+    s_q = max n (max T)^(3/2)."""
+    import numpy as np
+    n, u, T, q = (np.asarray(a, dtype=np.float64) for a in mom)
+    rn, ru, rT, rq = (np.asarray(a, dtype=np.float64) for a in ref)
+    u, ru = u.reshape(-1, 3), ru.reshape(-1, 3)
+    sT = np.abs(rT).max()
+    return {"n": float(np.abs(n - rn).max() / np.abs(rn).max()),
+            "u": float(np.abs(u - ru).max() / max(np.abs(ru).max(), math.sqrt(sT))),
+            "T": float(np.abs(T - rT).max() / sT),
+            "q": float(np.abs(q - rq).max() / max(np.abs(rq).max(), np.abs(rn).max() * sT ** 1.5))}
 
 
 def run_reference(args):
@@ -310,7 +337,13 @@ def run_gpu(args):
             prof = json.load(fh)
         if prof.get("kernel_hash") == kernel_source_hash():
             traffic = prof.get("dram_bytes_per_launch")
-    cpu_rate, cpu_secs, cpu_desc, cpu_cores = oracle_sample(steps=3)
+    # the same window on the GPU from the oracle's own initial state: the L-inf
+    # moment errors of the timed kernels against the FP64 oracle
+    cpu_rate, cpu_secs, cpu_desc, cpu_cores, f0_win, mom_ref = oracle_sample(steps=3, keep=True)
+    with hlb.Handle(window_config(), stream=stream.cuda_stream) as hw:
+        hw.set_state(f0_win.reshape(-1).astype(np.float32))
+        hw.step(3)
+        errs = moment_errors(hw.moments(), mom_ref)
     line = {
         "metric": METRIC, "value": value, "unit": "node-velocity updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -325,6 +358,9 @@ def run_gpu(args):
                                 stage_avg_ms, kt, flop_nv),
         "cpu_baseline": {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": cpu_cores,
                          "kind": "oracle", "sample": cpu_desc},
+        "accuracy": {"moment_linf_rel_err": errs, "bound": 1e-5, "within_bound": max(errs.values()) <= 1e-5,
+                     "case": "the cpu_baseline window (32x32 nodes, 3 RK-3 steps) from the oracle's initial "
+                             "state, FP32 kernels vs the FP64 oracle"},
         "e2e": {"value": e2e_value, "unit": "node-velocity updates/s",
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": 6 * 8 * nodes},
         "gpu_launches": launches,

@@ -280,3 +280,30 @@ def test_fp32_full_size_large_2d_sampled_nodes():
         g = got[y, x].astype(np.float64)
         err = np.abs(g - ref).max() / np.abs(ref).max()
         assert err < 2e-6, (x, y, err)
+
+
+def test_fp64_channel_full_length_barometric():
+    # The FP64 channel at its full length (64 cells, 10^4 RK-3 steps, CUDA-graph
+    # replay) from n = 1, u = 0, T = 1, against the oracle run alike; the
+    # result is the near-steady barometric state of Sec. V, log n linear in x
+    # with slope -g/T away from the walls.
+    from oracle.solver import Solver, config_from
+    from paper_1708_03249_gb300 import hlb
+    cfg = W.CHANNEL_1D_FP64
+    steps = W.CHANNEL_1D_FP64_STEPS
+    with hlb.Handle(cfg, stream=_stream()) as h:
+        h.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+        f0 = h.get_state().astype(np.float64)
+        h.step(steps)
+        got = h.get_state().astype(np.float64)
+        n, u, T, q = h.moments()
+    s = Solver(config_from(cfg))
+    s.f = f0.reshape(s.f.shape).copy()
+    s.step(steps)
+    ref = s.f.reshape(-1)
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+    g = -cfg["ax"]
+    x = (np.arange(cfg["nx"]) + 0.5) / cfg["nx"]
+    inner = slice(8, cfg["nx"] - 8)
+    slope = np.polyfit(x[inner], np.log(n[inner]), 1)[0]
+    assert slope == pytest.approx(-g / T[inner].mean(), rel=2e-3)
