@@ -435,14 +435,63 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------
+# the other configurations: one handle, graph replay, CUDA-event timing
+# ------------------------------------------------------------------------------
+OTHER_WORKLOADS = {
+    "fp64_channel": ("1D FP64 channel, 64 cells, Qx=4 x Qy=4, upwind2, Kn=0.1, g=0.1 normal",
+                     lambda: W.CHANNEL_1D_FP64),
+    "stretched_channel": ("1D FP32 channel, 512 cells tanh A=0.9, Qx=8 x Qy=8, WENO5, Kn=0.1, g=0.5 at 30 deg",
+                          lambda: W.channel_1d_stretched(0.1)),
+    "box2d": ("2D FP32 box 256x256, Qx=16 x Qy=16, WENO5, Kn=0.05, g=0.2 at 45 deg", lambda: W.BOX_2D),
+}
+
+
+def run_other(args):
+    import numpy as np
+    import torch
+
+    from paper_1708_03249_gb300 import build as hbuild
+    from paper_1708_03249_gb300 import hlb
+
+    torch.cuda.set_device(0)
+    if not os.path.exists(hlb.LIB_PATH):
+        hbuild.build()
+    desc, make_cfg = OTHER_WORKLOADS[args.workload]
+    cfg = make_cfg()
+    stream = torch.cuda.Stream()
+    with hlb.Handle(cfg, stream=stream.cuda_stream) as h:
+        h.init_equilibrium()
+        h.set_options(use_graphs=True, time_kernels=False)
+        h.step(max(args.warmup, 30))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(args.steps, 30)
+        e0.record(stream)
+        h.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        n, u, T, q = h.moments()
+        nv = h.values
+    line = {"metric": METRIC, "value": nv * steps / (ms * 1e-3), "unit": "node-velocity updates/s", "n_gpus": 1,
+            "steps": steps, "warmup": max(args.warmup, 30), "ms_per_step": ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if cfg["precision"] == W.FP64 else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "values_per_copy": nv,
+                       "moments_finite": bool(np.isfinite(n).all() and np.isfinite(T).all())}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="large2d", choices=["large2d", "batched"],
-                    help="large2d: the JSON line of record; batched: the 4096-channel batch vs per-instance FP64")
+    ap.add_argument("--workload", default="large2d", choices=["large2d", "batched"] + sorted(OTHER_WORKLOADS),
+                    help="large2d: the JSON line of record; batched: the 4096-channel batch vs per-instance "
+                         "FP64; the others time one handle of that configuration")
     ap.add_argument("--ninst", type=int, default=4096)
     ap.add_argument("--nx", type=int, default=0, help="profiling: the large 2D workload on a smaller grid")
     ap.add_argument("--ny", type=int, default=0)
@@ -452,6 +501,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload in OTHER_WORKLOADS:
+        run_other(args)
     else:
         run_gpu(args)
 

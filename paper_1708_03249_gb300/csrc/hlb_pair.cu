@@ -85,7 +85,7 @@ __device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&a)[4], u
 }
 
 template <int ADV, int QX2, int VY>
-__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? HLB_PAIR_MIN_BLOCKS : 1)))
+__global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? HLB_PAIR_MIN_BLOCKS : 2)))
 march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
                   const float* __restrict__ fn, float* __restrict__ fo, int stage) {
     constexpr int S = QX2 * VY;
