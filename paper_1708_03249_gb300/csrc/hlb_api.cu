@@ -343,7 +343,7 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     {
         const int ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
         if (cudaMalloc(&G.d_coef.p, std::max<size_t>((size_t)G.nnodes * ncp * G.esize, 16)) != cudaSuccess ||
-            cudaMalloc(&G.d_sums.p, std::max<size_t>((size_t)G.nnodes * 8 * G.esize, 16)) != cudaSuccess) {
+            cudaMalloc(&G.d_sums.p, std::max<size_t>((size_t)G.nnodes * 16 * G.esize, 16)) != cudaSuccess) {
             cudaGetLastError();
             return fail(HLB_ENOMEM, "cudaMalloc of the equilibrium factor lines failed");
         }

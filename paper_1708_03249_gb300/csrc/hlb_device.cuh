@@ -194,6 +194,36 @@ __device__ __forceinline__ int find_slot(const int* start, int n, int key) {
     return lo;
 }
 
+// Compensated summation (Kahan-Babuska / Neumaier): the running sum s and an
+// error term c with s + c equal to the sum of the terms to about twice the
+// working precision.  The FP32 form is the error-free TwoSum of Knuth; the FP64
+// form is a plain sum (c stays 0).
+__device__ __forceinline__ void csum_add(float& s, float& c, float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+__device__ __forceinline__ void csum_add(double& s, double& c, double x) {
+    (void)c;
+    s += x;
+}
+
+// Butterfly reduction of (s, c) over the warp; every lane ends with the sum.
+template <typename R>
+__device__ __forceinline__ void csum_warp(R& s, R& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const R s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        csum_add(s, c, s2);
+        c += c2;
+    }
+}
+
+// Slots of a node's moment sums: n, j_x, j_y, j_z, E at [0..4] and their
+// compensation terms at [8..12] (zero for FP64 states).
+constexpr int kSumStride = 16;
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -70,7 +70,8 @@ struct GroupDev {
     int V, QX2, VY, VZ, Qx, Nx, Ny, Nz, Qy, Qz, D;
     int ncp;                 // stride of a node's equilibrium-factor line
     void* coef;              // R: [node][ncp] = g_x * n (QX2), g_y (VY), g_z (VZ), 1/tau
-    void* sums;              // R: [node][8] = n, j_x, j_y, j_z, E of the stage input
+    void* sums;              // R: [node][16] = n, j_x, j_y, j_z, E of the stage input at [0..4],
+                             //    their compensation terms at [8..12]
     const void* inv_dx;      // R: 1/dx, concatenated per instance (same offsets as dx)
     const void* wscale;      // R: [V] 1/(w_x w_y w_z) per velocity (WENO smoothness scale)
     int ninst, nnodes, nrows;

@@ -381,8 +381,8 @@ __global__ void broadcast_kernel(R* __restrict__ f, const R* __restrict__ g, lon
 //   u = j/n,  T = (E - n|u|^2)/(D n),
 //   q_x = (1/2) sum (p_x - u_x)|p - u|^2 f
 //       = (1/2) [Q - 2 (u_x P_xx + u_y P_xy + u_z P_xz) - u_x E + 2 n u_x |u|^2].
-// Lanes and the warp tree accumulate in the state's precision; the per-node
-// combination is FP64.  With
+// Lanes and the warp tree accumulate in the state's precision, compensated for
+// FP32 states (sum and error term); the per-node combination is FP64.  With
 // 4 | 2Q_x and 2Q_x | 128 the lanes read 4-vectors whose p_x are fixed per
 // lane (as in sums_kernel); otherwise a shared table of (p_x, p_y, p_z) per
 // velocity (up to kMomentTableMax velocities) or per-value index arithmetic.
@@ -424,16 +424,18 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
     const int lane = threadIdx.x & 31;
     for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < g.nnodes; base += warps * 32) {
         const int nb = min(32, g.nnodes - base);
-        R mine[9];
+        R mine[9], mine_c[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) mine[k] = R(0);
+        for (int k = 0; k < 9; ++k) mine[k] = mine_c[k] = R(0);
         for (int kn = 0; kn < nb; ++kn) {
             const int node = base + kn;
             const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
             const InstDev& I = g.inst[ii];
             const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
             // n, j_x, j_y, j_z, P_xx, E - P_xx, P_xy, P_xz, Q
+            // compensated per-lane sums (FP32 states)
             R a[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+            R c[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
             if (kTable && vec4) {
                 const R4* f4 = reinterpret_cast<const R4*>(f);
                 const int x0 = (4 * lane) % QX2;
@@ -450,32 +452,36 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
                     const R jx = px[0] * x.x + px[1] * x.y + px[2] * x.z + px[3] * x.w;
                     const R pxx = px2[0] * x.x + px2[1] * x.y + px2[2] * x.z + px2[3] * x.w;
                     const R pxxx = px3[0] * x.x + px3[1] * x.y + px3[2] * x.z + px3[3] * x.w;
-                    a[0] += sm; a[1] += jx; a[2] += yz.x * sm; a[3] += yz.y * sm;
-                    a[4] += pxx; a[5] += yz.z * sm; a[6] += yz.x * jx; a[7] += yz.y * jx;
-                    a[8] += pxxx + yz.z * jx;
+                    csum_add(a[0], c[0], sm); csum_add(a[1], c[1], jx);
+                    csum_add(a[2], c[2], yz.x * sm); csum_add(a[3], c[3], yz.y * sm);
+                    csum_add(a[4], c[4], pxx); csum_add(a[5], c[5], yz.z * sm);
+                    csum_add(a[6], c[6], yz.x * jx); csum_add(a[7], c[7], yz.y * jx);
+                    csum_add(a[8], c[8], pxxx + yz.z * jx);
                 }
             } else {
                 for (int v = lane; v < V; v += 32) {
                     const R val = f[v];
                     const R4 p = kTable ? sP[v] : velocity_of<R, R4>(P, v, QX2, VY);
                     const R jx = p.x * val, yz2 = p.y * p.y + p.z * p.z;
-                    a[0] += val; a[1] += jx; a[2] += p.y * val; a[3] += p.z * val;
-                    a[4] += p.x * jx; a[5] += yz2 * val; a[6] += p.y * jx; a[7] += p.z * jx;
-                    a[8] += (p.x * p.x + yz2) * jx;
+                    csum_add(a[0], c[0], val); csum_add(a[1], c[1], jx);
+                    csum_add(a[2], c[2], p.y * val); csum_add(a[3], c[3], p.z * val);
+                    csum_add(a[4], c[4], p.x * jx); csum_add(a[5], c[5], yz2 * val);
+                    csum_add(a[6], c[6], p.y * jx); csum_add(a[7], c[7], p.z * jx);
+                    csum_add(a[8], c[8], (p.x * p.x + yz2) * jx);
                 }
             }
             // warp sums in the state's precision (FP64 adds run at 1/64 of FP32 here)
     #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                const R sk = warp_sum(a[k]);
-                if (lane == kn) mine[k] = sk;
+                csum_warp(a[k], c[k]);
+                if (lane == kn) { mine[k] = a[k]; mine_c[k] = c[k]; }
             }
         }
         if (lane < nb) {
             const int node = base + lane;
             double d[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) d[k] = (double)mine[k];
+            for (int k = 0; k < 9; ++k) d[k] = (double)mine[k] + (double)mine_c[k];
             const double n = d[0];
             const double ux = d[1] / n, uy = d[2] / n, uz = d[3] / n;
             const double u2 = ux * ux + uy * uy + uz * uz;

@@ -53,45 +53,73 @@ __global__ void __launch_bounds__(256) sums_kernel(const GroupDev g, const R* __
         sYZ[bq] = y4;
     }
     __syncthreads();
-    // 4-vector loads need 4 | 2Qx and 2Qx | 128 (2Qx a power of two up to 128):
-    // then 4 consecutive velocities share (jy, kz) and a lane's p_x never change
-    const bool vec4 = (QX2 & 3) == 0 && (QX2 & (QX2 - 1)) == 0 && QX2 <= 128;
+    // 4-vector loads with eight lanes per node, four nodes per warp: they need
+    // 4 | 2Qx and 2Qx | 32 (2Qx a power of two up to 32), so that the four
+    // velocities of a load share (jy, kz) and a lane's p_x never change.  The
+    // compensated tree then has three levels, and each shuffle serves four
+    // nodes.  Other sets: one warp per node, a table of all velocities.
+    const bool vec4 = (QX2 & 3) == 0 && (QX2 & (QX2 - 1)) == 0 && QX2 <= 32 && V >= 32;
+    auto store = [&](int node, R a0, R a1, R a2, R a3, R a4, R c0, R c1, R c2, R c3, R c4) {
+        R* o = sums + (size_t)node * kSumStride;
+        o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = a4;
+        o[8] = c0; o[9] = c1; o[10] = c2; o[11] = c3; o[12] = c4;
+    };
+    if (vec4) {
+        const int sl = lane & 7;
+        const int x0 = (4 * sl) % QX2;
+        const int lg = __ffs(QX2) - 1;                   // 2Qx = 2^lg
+        const R pxa = sM[x0].x, pxb = sM[x0 + 1].x, pxc = sM[x0 + 2].x, pxd = sM[x0 + 3].x;
+        for (int nb = (blockIdx.x * nw + warp) * 4; nb < g.nnodes; nb += gridDim.x * nw * 4) {
+            const int node = nb + (lane >> 3);
+            // compensated per-lane sums (FP32 states)
+            R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+            if (node < g.nnodes) {
+                const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+                const InstDev& I = g.inst[ii];
+                const R4* f4 = reinterpret_cast<const R4*>(fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V);
+#pragma unroll 4
+                for (int q = sl; q < (V >> 2); q += 8) {
+                    const R4 x = f4[q];
+                    const R4 yz = sYZ[(q << 2) >> lg];
+                    const R sq = (x.x + x.y) + (x.z + x.w);
+                    csum_add(a0, c0, sq);
+                    csum_add(a1, c1, pxa * x.x + pxb * x.y + pxc * x.z + pxd * x.w);
+                    csum_add(a2, c2, yz.x * sq);
+                    csum_add(a3, c3, yz.y * sq);
+                    csum_add(a4, c4, pxa * pxa * x.x + pxb * pxb * x.y + pxc * pxc * x.z + pxd * pxd * x.w + yz.z * sq);
+                }
+            }
+            // compensated tree over the eight lanes of each node
+            auto tree8 = [](R& sa, R& ca) {
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) {
+                    const R s2 = __shfl_xor_sync(0xffffffffu, sa, o), c2 = __shfl_xor_sync(0xffffffffu, ca, o);
+                    csum_add(sa, ca, s2);
+                    ca += c2;
+                }
+            };
+            tree8(a0, c0); tree8(a1, c1); tree8(a2, c2); tree8(a3, c3); tree8(a4, c4);
+            if (sl == 0 && node < g.nnodes) store(node, a0, a1, a2, a3, a4, c0, c1, c2, c3, c4);
+        }
+        return;
+    }
     for (int node = blockIdx.x * nw + warp; node < g.nnodes; node += gridDim.x * nw) {
         const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
         const InstDev& I = g.inst[ii];
         const R* f = fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V;
-        R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-        if (vec4) {
-            const R4* f4 = reinterpret_cast<const R4*>(f);
-            const int x0 = (4 * lane) % QX2;
-            const R pxa = sM[x0].x, pxb = sM[x0 + 1].x, pxc = sM[x0 + 2].x, pxd = sM[x0 + 3].x;
-#pragma unroll 4
-            for (int q = lane; q < (V >> 2); q += 32) {
-                const R4 x = f4[q];
-                const R4 yz = sYZ[(q << 2) / QX2];
-                const R s = (x.x + x.y) + (x.z + x.w);
-                a0 += s;
-                a1 += pxa * x.x + pxb * x.y + pxc * x.z + pxd * x.w;
-                a2 += yz.x * s;
-                a3 += yz.y * s;
-                a4 += pxa * pxa * x.x + pxb * pxb * x.y + pxc * pxc * x.z + pxd * pxd * x.w + yz.z * s;
-            }
-        } else {
-            for (int v = lane; v < V; v += 32) {
-                const R val = f[v];
-                const R4 mw = sM[v];
-                a0 += val;
-                a1 += mw.x * val;
-                a2 += mw.y * val;
-                a3 += mw.z * val;
-                a4 += mw.w * val;
-            }
+        // compensated per-lane sums (FP32 states), compensated warp tree
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+        for (int v = lane; v < V; v += 32) {
+            const R val = f[v];
+            const R4 mw = sM[v];
+            csum_add(a0, c0, val);
+            csum_add(a1, c1, mw.x * val);
+            csum_add(a2, c2, mw.y * val);
+            csum_add(a3, c3, mw.z * val);
+            csum_add(a4, c4, mw.w * val);
         }
-        a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
-        if (lane == 0) {
-            R* o = sums + (size_t)node * 8;
-            o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3; o[4] = a4;
-        }
+        csum_warp(a0, c0); csum_warp(a1, c1); csum_warp(a2, c2); csum_warp(a3, c3); csum_warp(a4, c4);
+        if (lane == 0) store(node, a0, a1, a2, a3, a4, c0, c1, c2, c3, c4);
     }
 }
 
@@ -142,19 +170,14 @@ __global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __r
             const int node = base + lane;
             const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
             const double inv_Kn = g.inst[ii].inv_Kn;
-            const R* sm = sums + (size_t)node * 8;
+            const R* sm = sums + (size_t)node * kSumStride;
             active = inv_Kn != 0.0;
-            double ux, uy, uz, T, n;
-            if (df) {
-                const float nf32 = (float)sm[0];
-                const float fx = (float)sm[1] / nf32, fy = (float)sm[2] / nf32, fz = (float)sm[3] / nf32;
-                const float fT = ((float)sm[4] - nf32 * (fx * fx + fy * fy + fz * fz)) / (g.D * nf32);
-                n = nf32; ux = fx; uy = fy; uz = fz; T = fT;
-            } else {
-                n = (double)sm[0];
-                ux = (double)sm[1] / n; uy = (double)sm[2] / n; uz = (double)sm[3] / n;
-                T = ((double)sm[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
-            }
+            // n, u, T in FP64 from the compensated sums (one division)
+            const double n = (double)sm[0] + (double)sm[8], in = 1.0 / n;
+            const double ux = ((double)sm[1] + (double)sm[9]) * in, uy = ((double)sm[2] + (double)sm[10]) * in,
+                         uz = ((double)sm[3] + (double)sm[11]) * in;
+            const double T = ((double)sm[4] + (double)sm[12] - n * (ux * ux + uy * uy + uz * uz)) * in *
+                             (g.D == 3 ? 1.0 / 3.0 : (g.D == 2 ? 0.5 : 1.0));
             sNT[2 * lane] = n;
             sNT[2 * lane + 1] = n * inv_Kn;
             if (active) {
@@ -306,10 +329,13 @@ __global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const fl
     if (node < g.nnodes) {
         const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
         const double inv_Kn = g.inst[ii].inv_Kn;
-        const float* sm = sums + (size_t)node * 8;
-        const float n = sm[0];
-        const float ux = sm[1] / n, uy = sm[2] / n, uz = sm[3] / n;
-        const float T = (sm[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
+        const float* sm = sums + (size_t)node * kSumStride;
+        // n, u, T in FP64 from the compensated sums (one division)
+        const double n = (double)sm[0] + (double)sm[8], in = 1.0 / n;
+        const double ux = ((double)sm[1] + (double)sm[9]) * in, uy = ((double)sm[2] + (double)sm[10]) * in,
+                     uz = ((double)sm[3] + (double)sm[11]) * in;
+        const double T = ((double)sm[4] + (double)sm[12] - n * (ux * ux + uy * uy + uz * uz)) * in *
+                         (g.D == 3 ? 1.0 / 3.0 : (g.D == 2 ? 0.5 : 1.0));
         const double itau = (double)n * inv_Kn;
         for (int o = QX2 + VY + VZ; o < ncp; ++o) line[o] = 0.0f;
         line[QX2 + VY + VZ] = (float)itau;

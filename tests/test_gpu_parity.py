@@ -307,3 +307,45 @@ def test_fp64_channel_full_length_barometric():
     inner = slice(8, cfg["nx"] - 8)
     slope = np.polyfit(x[inner], np.log(n[inner]), 1)[0]
     assert slope == pytest.approx(-g / T[inner].mean(), rel=2e-3)
+
+
+@pytest.mark.parametrize("cfg", [W.scaled(W.LARGE_2D, nx=12, ny=6, Ly=6 / 12),
+                                 W.make(Qx=16, Qy=16, nx=40, precision=W.FP32)])
+def test_fp32_moment_sums_are_compensated(cfg):
+    # Every node holds 1 in one aligned block of four velocities and 1e-8 in all
+    # others.  A plain FP32 running sum that has reached 4 drops each later
+    # 4e-8 partial (below half an ulp of 4), a relative loss of ~1e-7 in n; the
+    # compensated sums (running sum and error term, lanes and warp tree) keep
+    # them, so n agrees with the exact FP64 sum of the same values to rounding.
+    from paper_1708_03249_gb300 import hlb
+    with hlb.Handle(cfg, stream=_stream()) as h:
+        V = h.values // h.nodes
+        f = np.full((h.nodes, V), 1e-8, dtype=np.float32)
+        rng = np.random.default_rng(11)
+        blocks = rng.integers(0, V // 4, size=h.nodes)
+        for k in range(4):
+            f[np.arange(h.nodes), 4 * blocks + k] = 1.0
+        h.set_state(f.reshape(-1))
+        n, u, T, q = h.moments()
+    exact = f.astype(np.float64).sum(axis=1)
+    err = np.abs(n - exact).max() / exact.max()
+    assert err < 1e-9, err
+
+
+def test_fp32_moments_of_a_given_state():
+    # The moments of a given FP32 state against the FP64 moments of the very
+    # same values: what remains is the FP32 rounding of the velocity table and
+    # of the per-term products, well below the 1e-5 bar.
+    from oracle.solver import Solver, config_from
+    from paper_1708_03249_gb300 import hlb
+    cfg = W.scaled(W.LARGE_2D, nx=12, ny=6, Ly=6 / 12)
+    with hlb.Handle(cfg, stream=_stream()) as h:
+        h.init_equilibrium(1.0, 0.3, -0.2, 1.4)
+        f = h.get_state().astype(np.float64)
+        f = (f * W.perturbation(f.shape, seed=7, amplitude=0.3)).astype(np.float32)
+        h.set_state(f)
+        mom = h.moments()
+    s = Solver(config_from(cfg))
+    s.f = f.astype(np.float64).reshape(s.f.shape)
+    errs = moment_errors(mom, _oracle_moments([s]))
+    assert max(errs.values()) < 2e-7, errs
