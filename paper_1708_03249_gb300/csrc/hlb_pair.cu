@@ -3,6 +3,7 @@
 // march_pair_kernel below.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <type_traits>
 
@@ -195,35 +196,6 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     // Copy `lane` of pair p (22 lanes: 12 halo rows, 4 head rows, 4 f^n rows,
     // 2 factor-line runs): source, bytes and destination in B; false if the
     // lane has none for this pair.
-    auto copy_of = [&](int lane, int p, Buf& B, const float*& src, uint32_t& bytes, float*& dst) -> bool {
-        const int x0 = xa + 2 * p;
-        const int n2 = min(2, xb - x0);
-        bytes = row_bytes;
-        if (lane < 12) {                                   // halo rows of cells x0, x0+1
-            const int i = lane / 6, k = lane % 6;
-            const int yk = k < 3 ? ((W.y0 - 3 + k) % ny + ny) % ny : (W.y0 + k - 1) % ny;
-            src = fsI + yk * rs + (x0 + i) * V + slab;
-            dst = B.halo[i][k];
-            return i < n2;
-        } else if (lane < 16) {                            // head cells x0+3, x0+4
-            const int i = (lane - 12) >> 1, r = lane & 1;
-            src = fsI + roff[r] + (x0 + 3 + i) * V + slab;
-            dst = B.head[i][r];
-            return i < n2 && x0 + 3 + i < nx;
-        } else if (lane < 20) {                            // f^n of cells x0, x0+1
-            const int i = (lane - 16) >> 1, r = lane & 1;
-            src = fnI + roff[r] + (x0 + i) * V + slab;
-            dst = B.fnr[i][r];
-            return stage > 0 && i < n2;
-        } else if (lane < 22) {                            // factor lines
-            const int r = lane - 20;
-            src = cI + (size_t)(crow[r] + x0) * ncp;
-            bytes = n2 * ncp * (uint32_t)sizeof(float);
-            dst = B.coef[r];
-            return true;
-        }
-        return false;
-    };
     // The copies are spread over the warps so that no warp carries them all:
     // with four or more warps, warps 0 and 1 take the halo rows of cells x0
     // and x0+1, warp 2 the head rows and factor lines, warp 3 the f^n rows; a
@@ -246,14 +218,51 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
         if (stage > 0) bytes += 2 * n2 * row_bytes;
         mbar_expect_tx(&bars[p % kPairDepth], bytes);
     };
+    // This thread's copy, fixed for the whole segment (22 copies per pair: 12
+    // halo rows, 4 head rows, 4 f^n rows, 2 factor-line runs): the source of
+    // pair 0 and its step per pair, the destination's offset in a buffer, and
+    // the cell i of the pair it belongs to (the copy exists while i < cells of
+    // the pair).  Computed once, so the per-pair issue is an add and a copy.
+    const float* cp_src = nullptr;
+    long long cp_step = 2LL * V;
+    size_t cp_dst = 0;
+    int cp_i = 0, cp_kind = 0;                         // 0 halo, 1 head, 2 f^n, 3 factor lines
+    if (my_copy >= 0 && my_copy < 12) {
+        const int i = my_copy / 6, k = my_copy % 6;
+        const int yk = k < 3 ? ((W.y0 - 3 + k) % ny + ny) % ny : (W.y0 + k - 1) % ny;
+        cp_src = fsI + (size_t)yk * rs + (size_t)(xa + i) * V + slab;
+        cp_dst = offsetof(Buf, halo) + ((size_t)i * 6 + k) * S * sizeof(float);
+        cp_i = i; cp_kind = 0;
+    } else if (my_copy >= 12 && my_copy < 16) {
+        const int i = (my_copy - 12) >> 1, r = my_copy & 1;
+        cp_src = fsI + roff[r] + (size_t)(xa + 3 + i) * V + slab;
+        cp_dst = offsetof(Buf, head) + ((size_t)i * 2 + r) * S * sizeof(float);
+        cp_i = i; cp_kind = 1;
+    } else if (my_copy >= 16 && my_copy < 20) {
+        const int i = (my_copy - 16) >> 1, r = my_copy & 1;
+        cp_src = fnI + roff[r] + (size_t)(xa + i) * V + slab;
+        cp_dst = offsetof(Buf, fnr) + ((size_t)i * 2 + r) * S * sizeof(float);
+        cp_i = i; cp_kind = 2;
+    } else if (my_copy >= 20 && my_copy < 22) {
+        const int r = my_copy - 20;
+        cp_src = cI + (size_t)(crow[r] + xa) * ncp;
+        cp_step = 2LL * ncp;
+        cp_dst = offsetof(Buf, coef) + (size_t)r * Buf::NCPMAX * 2 * sizeof(float);
+        cp_kind = 3;
+    }
     auto issue = [&](int p) {
         if (my_copy < 0 || p >= npairs || (g.inject_stall && p == 1)) return;
-        Buf& B = buf[p % kPairDepth];
-        const float* src;
-        uint32_t bytes;
-        float* dst;
+        const int x0 = xa + 2 * p;
+        const int n2 = min(2, xb - x0);
+        bool go = cp_i < n2;
+        uint32_t bytes = row_bytes;
+        if (cp_kind == 1) go = go && x0 + 3 + cp_i < nx;
+        else if (cp_kind == 2) go = go && stage > 0;
+        else if (cp_kind == 3) bytes = n2 * ncp * (uint32_t)sizeof(float);
         fence_proxy_async_smem();
-        if (copy_of(my_copy, p, B, src, bytes, dst)) bulk_g2s(dst, src, bytes, &bars[p % kPairDepth]);
+        if (go)
+            bulk_g2s(reinterpret_cast<unsigned char*>(&buf[p % kPairDepth]) + cp_dst, cp_src + p * cp_step, bytes,
+                     &bars[p % kPairDepth]);
     };
 
     if (t == 0) {
@@ -366,6 +375,8 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     // xch[b] of pair p also means every warp is done with pair p-1, so its
     // copy buffer is refilled then.  Every wait is bounded, so no warp can be
     // left waiting for good.
+    float* fo0 = fov + roff[0] + (size_t)xa * V;       // this thread's outputs at cell x0, rows y0, y0+1
+    float* fo1 = fov + roff[1] + (size_t)xa * V;
     int pa = 0, slot = 0;
     uint32_t phase = 0;
 #pragma unroll 1
@@ -470,10 +481,11 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
                 else
                     out = __ffma2_rn(f2(1.0f / 3.0f), fo_n, __fmul2_rn(f2(2.0f / 3.0f), fsub2(fc, __fmul2_rn(dt2, L))));
             }
-            const int x = x0 + i;
-            if (valid[0]) fov[roff[0] + x * V] = out.x;
-            if (valid[1]) fov[roff[1] + x * V] = out.y;
+            if (valid[0]) fo0[(size_t)i * V] = out.x;
+            if (valid[1]) fo1[(size_t)i * V] = out.y;
         }
+        fo0 += 2 * (size_t)V;
+        fo1 += 2 * (size_t)V;
         if (++slot == kPairDepth) { slot = 0; phase ^= 1u; }
     }
     if (*sAbort && t == 0) {
