@@ -295,27 +295,47 @@ def run_gpu(args):
     finite = bool(np.isfinite(n).all() and np.isfinite(T).all())
     value = job_rate(nodes * V * args.steps, world, ms * 1e-3)
 
-    # end to end through the C ABI with host buffers: H2D of the state from
-    # pinned memory, one RK-3 step, D2H of the moments, every iteration
+    # end to end through the C ABI with host buffers, every step: the state
+    # uploaded from pinned memory, one RK-3 step, the moments read back into
+    # pinned arrays.  Overlapped form (the e2e value): the upload of step k+1's
+    # state is staged (hlb_prefetch_state, its own copy stream) while step k
+    # runs, then committed; the first upload is inside the timed region.
+    # Serial form (context): hlb_set_state, step, hlb_moments.
     pinned = torch.empty(values, dtype=torch.float32, pin_memory=True)
     h.get_state(pinned.numpy())
     h.set_options(use_graphs=True, time_kernels=False)
-    e2e_iters = max(2, min(args.steps, 5))
+    e2e_iters = max(2, min(args.steps, 10))
     # page-locked result arrays, like the input: the moments land by DMA
     moms = [torch.empty(k * nodes, dtype=torch.float64, pin_memory=True).numpy() for k in (1, 3, 1, 1)]
     import ctypes
     ptrs = [m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for m in moms]
     lib = hlb.lib()
-    for it in range(1 + e2e_iters):
-        if it == 1:
-            barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-        hlb._check(lib.hlb_set_state(h._h, pinned.data_ptr(), state_bytes))
-        h.step(1)
-        hlb._check(lib.hlb_moments(h._h, *ptrs))
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-    e2e_value = job_rate(nodes * V * e2e_iters, world, e2e_s)
+
+    def e2e_overlapped(iters):
+        h.prefetch_state(pinned.data_ptr(), state_bytes)
+        for it in range(iters):
+            h.commit_state()
+            if it + 1 < iters:
+                h.prefetch_state(pinned.data_ptr(), state_bytes)
+            h.step(1)
+            hlb._check(lib.hlb_moments(h._h, *ptrs))
+
+    def e2e_serial(iters):
+        for it in range(iters):
+            hlb._check(lib.hlb_set_state(h._h, pinned.data_ptr(), state_bytes))
+            h.step(1)
+            hlb._check(lib.hlb_moments(h._h, *ptrs))
+
+    def timed(fn):
+        fn(1)                                    # untimed: staging buffer, graph
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn(e2e_iters)
+        return max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+
+    e2e_value = job_rate(nodes * V * e2e_iters, world, timed(e2e_overlapped))
+    e2e_serial_value = job_rate(nodes * V * e2e_iters, world, timed(e2e_serial))
     h.close()
 
     if rank != 0:
@@ -362,7 +382,12 @@ def run_gpu(args):
                      "case": "the cpu_baseline window (32x32 nodes, 3 RK-3 steps) from the oracle's initial "
                              "state, FP32 kernels vs the FP64 oracle"},
         "e2e": {"value": e2e_value, "unit": "node-velocity updates/s",
-                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": 6 * 8 * nodes},
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": 6 * 8 * nodes,
+                "steps": e2e_iters,
+                "form": "per step: the state from pinned memory (staged by hlb_prefetch_state on a copy "
+                        "stream during the previous step, then hlb_commit_state), one RK-3 step, "
+                        "hlb_moments into pinned arrays; the first upload inside the timed region",
+                "serial": e2e_serial_value},
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -177,6 +177,24 @@ hlb_status hlb_set_state(hlb_handle* h, const void* host_f, size_t bytes);
 hlb_status hlb_get_state_dev(hlb_handle* h, void* f_dev, size_t bytes);
 hlb_status hlb_set_state_dev(hlb_handle* h, const void* f_dev, size_t bytes);
 
+/* Staged state input, so that the upload of the next state overlaps the
+ * steps still running (no counterpart in the paper: host I/O only).
+ * hlb_prefetch_state enqueues a host-to-device copy of host_f (exactly
+ * hlb_sizes(...bytes) bytes, layout as hlb_set_state) into a staging buffer
+ * that the handle allocates on first use, on a copy stream of the handle's
+ * own, after the work already enqueued on the handle's stream that reads the
+ * staging buffer; it returns at once.  The copy overlaps compute only from
+ * page-locked host memory.  host_f must stay valid and unchanged until the
+ * copy has run, i.e. until the hlb_commit_state that consumes it has been
+ * followed by a synchronisation of the handle's stream (hlb_moments, or the
+ * caller's own).  A second prefetch before a commit replaces the first.
+ * hlb_commit_state makes the handle's stream wait for that copy, then enqueues
+ * a device-to-device copy of the staging buffer into the current state.
+ * Errors: HLB_EINVAL (size, NULL, commit with nothing staged), HLB_ENOMEM,
+ * HLB_ECUDA. */
+hlb_status hlb_prefetch_state(hlb_handle* h, const void* host_f, size_t bytes);
+hlb_status hlb_commit_state(hlb_handle* h);
+
 /* Diagnostics of the current state: the particle number per instance
  * N = int n dx dy (Eq. "eq:Ndef"; ninst values) and the last step's
  * residual max|f^{n+1} - f^n| / (dt max|f^{n+1}|) per instance (0 before the

@@ -94,6 +94,12 @@ struct hlb_handle {
     long long launches = 0;                  // kernels enqueued by hlb_step (graph replays included)
     bool have_residual = false;
     size_t esize = 4;
+    // staged state (hlb_prefetch_state / hlb_commit_state): a device buffer in
+    // the caller's layout, filled on a copy stream of its own
+    void* stage_buf = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t stage_free = nullptr, stage_filled = nullptr;
+    bool staged = false;
 };
 
 namespace {
@@ -599,6 +605,10 @@ void hlb_destroy(hlb_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     collect_timer(h);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->copy_stream) { cudaStreamSynchronize(h->copy_stream); cudaStreamDestroy(h->copy_stream); }
+    if (h->stage_free) cudaEventDestroy(h->stage_free);
+    if (h->stage_filled) cudaEventDestroy(h->stage_filled);
+    if (h->stage_buf) cudaFree(h->stage_buf);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -847,6 +857,40 @@ hlb_status hlb_get_state_dev(hlb_handle* h, void* f_dev, size_t bytes) {
 }
 hlb_status hlb_set_state_dev(hlb_handle* h, const void* f_dev, size_t bytes) {
     return state_copy(h, const_cast<void*>(f_dev), bytes, false, cudaMemcpyDeviceToDevice, false);
+}
+
+hlb_status hlb_prefetch_state(hlb_handle* h, const void* host_f, size_t bytes) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (!host_f) return fail(HLB_EINVAL, "buffer is NULL");
+    const size_t total = (size_t)(h->total_values * (long long)h->esize);
+    if (bytes != total) return fail(HLB_EINVAL, "state buffer must be exactly " + std::to_string(total) + " bytes");
+    if (!h->copy_stream) {
+        HLB_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        HLB_CUDA(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
+        HLB_CUDA(cudaEventCreateWithFlags(&h->stage_filled, cudaEventDisableTiming));
+    }
+    if (!h->stage_buf && cudaMalloc(&h->stage_buf, total) != cudaSuccess) {
+        h->stage_buf = nullptr;
+        return fail(HLB_ENOMEM, "cudaMalloc of the staging buffer failed");
+    }
+    // the staging buffer is free once the work already on the handle's
+    // stream (an earlier commit's copy out of it) has run
+    HLB_CUDA(cudaEventRecord(h->stage_free, h->stream));
+    HLB_CUDA(cudaStreamWaitEvent(h->copy_stream, h->stage_free, 0));
+    HLB_CUDA(cudaMemcpyAsync(h->stage_buf, host_f, total, cudaMemcpyHostToDevice, h->copy_stream));
+    HLB_CUDA(cudaEventRecord(h->stage_filled, h->copy_stream));
+    h->staged = true;
+    return HLB_OK;
+}
+
+hlb_status hlb_commit_state(hlb_handle* h) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (!h->staged) return fail(HLB_EINVAL, "no state staged: call hlb_prefetch_state first");
+    HLB_CUDA(cudaStreamWaitEvent(h->stream, h->stage_filled, 0));
+    const hlb_status s = state_copy(h, h->stage_buf, (size_t)(h->total_values * (long long)h->esize), false,
+                                    cudaMemcpyDeviceToDevice, false);
+    if (s == HLB_OK) h->staged = false;
+    return s;
 }
 
 hlb_status hlb_diag(hlb_handle* h, double* total_N, double* residual) {

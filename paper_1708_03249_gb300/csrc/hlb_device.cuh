@@ -209,11 +209,12 @@ __device__ __forceinline__ void csum_add(double& s, double& c, double x) {
     s += x;
 }
 
-// Butterfly reduction of (s, c) over the warp; every lane ends with the sum.
-template <typename R>
+// Butterfly reduction of (s, c) over groups of 2 O consecutive lanes (O = 16:
+// the whole warp); every lane of a group ends with the group's sum.
+template <typename R, int O = 16>
 __device__ __forceinline__ void csum_warp(R& s, R& c) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = O; o > 0; o >>= 1) {
         const R s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
         csum_add(s, c, s2);
         c += c2;

@@ -422,12 +422,57 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
     // outputs are written coalesced.
     const int warps = (blockDim.x >> 5) * gridDim.x;
     const int lane = threadIdx.x & 31;
+    // 4-vector path with 2Q_x <= 32: eight lanes per node, four nodes of the
+    // batch at a time; each lane's p_x stay fixed (its 4-vectors are 8 apart).
+    const bool quad = kTable && vec4 && QX2 <= 32;
     for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < g.nnodes; base += warps * 32) {
         const int nb = min(32, g.nnodes - base);
         R mine[9], mine_c[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) mine[k] = mine_c[k] = R(0);
-        for (int kn = 0; kn < nb; ++kn) {
+        if (quad) {
+            const int sl = lane & 7, lg = __ffs(QX2) - 1;
+            const int x0 = (4 * sl) & (QX2 - 1);
+            R px[4], px2[4], px3[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                px[e] = P[x0 + e]; px2[e] = px[e] * px[e]; px3[e] = px2[e] * px[e];
+            }
+            for (int b = 0; 4 * b < nb; ++b) {
+                const int node = base + 4 * b + (lane >> 3);
+                // n, j_x, j_y, j_z, P_xx, E - P_xx, P_xy, P_xz, Q (compensated for FP32)
+                R a[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+                R c[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+                if (node < base + nb) {
+                    const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+                    const InstDev& I = g.inst[ii];
+                    const R4* f4 = reinterpret_cast<const R4*>(fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V);
+#pragma unroll 4
+                    for (int k = sl; k < (V >> 2); k += 8) {
+                        const R4 x = f4[k];
+                        const R4 yz = sYZ[k >> (lg - 2)];
+                        const R sm = (x.x + x.y) + (x.z + x.w);
+                        const R jx = px[0] * x.x + px[1] * x.y + px[2] * x.z + px[3] * x.w;
+                        const R pxx = px2[0] * x.x + px2[1] * x.y + px2[2] * x.z + px2[3] * x.w;
+                        const R pxxx = px3[0] * x.x + px3[1] * x.y + px3[2] * x.z + px3[3] * x.w;
+                        csum_add(a[0], c[0], sm); csum_add(a[1], c[1], jx);
+                        csum_add(a[2], c[2], yz.x * sm); csum_add(a[3], c[3], yz.y * sm);
+                        csum_add(a[4], c[4], pxx); csum_add(a[5], c[5], yz.z * sm);
+                        csum_add(a[6], c[6], yz.x * jx); csum_add(a[7], c[7], yz.y * jx);
+                        csum_add(a[8], c[8], pxxx + yz.z * jx);
+                    }
+                }
+                // eight-lane trees; lane L keeps node L's sums (lane 8 (L & 3) of sub-batch L >> 2)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    csum_warp<R, 4>(a[k], c[k]);
+                    const R s2 = __shfl_sync(0xffffffffu, a[k], 8 * (lane & 3));
+                    const R c2 = __shfl_sync(0xffffffffu, c[k], 8 * (lane & 3));
+                    if ((lane >> 2) == b) { mine[k] = s2; mine_c[k] = c2; }
+                }
+            }
+        }
+        for (int kn = 0; kn < (quad ? 0 : nb); ++kn) {
             const int node = base + kn;
             const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
             const InstDev& I = g.inst[ii];

@@ -64,6 +64,8 @@ SIGNATURES = {
     "hlb_set_state": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_get_state_dev": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_set_state_dev": (C.c_int, [_P, _P, C.c_size_t]),
+    "hlb_prefetch_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "hlb_commit_state": (C.c_int, [_P]),
     "hlb_diag": (C.c_int, [_P, _D, _D]),
     "hlb_tables": (C.c_int, [_P, C.c_int] + [_D] * 10),
     "hlb_equilibrium_x": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_double, _D]),
@@ -203,6 +205,13 @@ class Handle:
 
     def set_state_dev(self, ptr: int, nbytes: int):
         _check(lib().hlb_set_state_dev(self._h, ptr, nbytes))
+
+    def prefetch_state(self, ptr: int, nbytes: int):
+        """hlb_prefetch_state: stage the host buffer at ptr (keep it alive and unchanged until the commit has run)."""
+        _check(lib().hlb_prefetch_state(self._h, ptr, nbytes))
+
+    def commit_state(self):
+        _check(lib().hlb_commit_state(self._h))
 
     def diag(self):
         k = len(self.cfgs)

@@ -1,0 +1,61 @@
+"""hlb_prefetch_state / hlb_commit_state: a staged upload of the next state.
+
+A state staged from page-locked memory while steps run on the current one,
+then committed, must be exactly the state that hlb_set_state would have set
+(byte for byte), and the steps that follow must give the same bits as after
+hlb_set_state.  Several instances of two velocity sets exercise the
+per-instance copies out of the staging buffer.  A commit with nothing staged
+and a buffer of the wrong size are rejected.
+"""
+import numpy as np
+import pytest
+
+from paper_1708_03249_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _cfgs():
+    return [W.make(Qx=4, Qy=4, nx=24, Kn=0.3, ax=-0.2, precision=W.FP32),
+            W.make(Qx=8, Qy=8, nx=16, Kn=1.0, T_right=1.5, precision=W.FP32),
+            W.make(Qx=4, Qy=4, nx=40, Kn=0.1, precision=W.FP32)]
+
+
+def test_committed_state_equals_set_state_and_steps_agree():
+    from paper_1708_03249_gb300 import hlb
+    with hlb.Handle(_cfgs()) as a, hlb.Handle(_cfgs()) as b:
+        a.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+        f1 = a.get_state().astype(np.float64) * W.perturbation(a.values, seed=11, amplitude=0.05)
+        pinned = torch.empty(a.values, dtype=torch.float32, pin_memory=True)
+        pinned.numpy()[:] = f1.astype(np.float32)
+        a.step(3)                                   # running on the old state
+        a.prefetch_state(pinned.data_ptr(), a.state_bytes)
+        a.step(2)                                   # overlaps the staged copy
+        a.commit_state()
+        got = a.get_state()
+        np.testing.assert_array_equal(got, pinned.numpy())
+        b.set_state(pinned.numpy())
+        a.step(4)
+        b.step(4)
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
+        with pytest.raises(hlb.HlbError) as e:     # the staged state was consumed
+            a.commit_state()
+        assert e.value.status == hlb.HLB_EINVAL
+
+
+def test_second_prefetch_replaces_the_first_and_bad_size_is_rejected():
+    from paper_1708_03249_gb300 import hlb
+    with hlb.Handle(_cfgs()) as h:
+        h.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+        base = h.get_state()
+        first = torch.from_numpy(base * np.float32(0.5)).pin_memory()
+        second = torch.from_numpy(base * np.float32(2.0)).pin_memory()
+        h.prefetch_state(first.data_ptr(), h.state_bytes)
+        h.prefetch_state(second.data_ptr(), h.state_bytes)
+        h.commit_state()
+        np.testing.assert_array_equal(h.get_state(), second.numpy())
+        with pytest.raises(hlb.HlbError) as e:
+            h.prefetch_state(first.data_ptr(), h.state_bytes - 4)
+        assert e.value.status == hlb.HLB_EINVAL
