@@ -107,6 +107,102 @@ __device__ __forceinline__ R upwind2_face(R b, R c) { return R(1.5) * c - R(0.5)
 template <int QX2, int VY>
 __host__ __device__ constexpr int pair_kdup_pairs() { return QX2 * (QX2 + 2) + VY * (VY + 2); }
 
+// ---------------------------------------------------------------------------
+// The force term a_x K_x f + a_y K_y f of one exchange tile on the tensor cores
+// (warp-level mma.sync, three TF32 products, FP32 accumulation).  The tile is
+// sF[VY][QX2 + 1] of float4 (four cells or cell/row combinations c per
+// velocity).  The two contractions are written as F^T K^T:
+//   X rows (j_y, c), 4 VY of them, columns i_x:  (a_x K_x f)^T,
+//   Y rows (i_x, c), 4 QX2 of them, columns j_y: (a_y K_y f)^T.
+// Warp w computes one 16 x 8 tile of each (exactly S/32 tiles per product
+// when 8 | QX2 and 8 | VY) and stores it into sKx / sKy in the layout of sF.
+// The B fragments (a K)^T stay in registers, split into TF32 hi and lo parts.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    // D += A B, m16n8k8, A row-major 16 x 8, B column-major 8 x 8
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// x = hi + lo with hi a TF32 value (round to nearest); lo keeps the rest
+// (its own low bits are dropped by the tensor core).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+// D += A B in three TF32 products (A_lo B_hi + A_hi B_lo + A_hi B_hi), close
+// to an FP32 product; a[k] are FP32 values, b{0,1}{h,l} split fragments.
+__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&a)[4], uint32_t b0h, uint32_t b0l,
+                                           uint32_t b1h, uint32_t b1l) {
+    uint32_t ah[4], al[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) split_tf32(a[k], ah[k], al[k]);
+    mma_tf32(d, al[0], al[1], al[2], al[3], b0h, b1h);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0l, b1l);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0h, b1h);
+}
+
+template <int QX2, int VY>
+struct ForceMMA {
+    static constexpr int XS = QX2 / 8, YS = VY / 8, SP = QX2 + 1;   // k-steps; padded tile row
+    static constexpr int XA = XS > 0 ? XS : 1, YA = YS > 0 ? YS : 1;
+    uint32_t bxh[XA][2], bxl[XA][2], byh[YA][2], byl[YA][2];
+    int mX, nX, mY, nY, gq, tq;
+
+    // K: K_x (QX2 x QX2) then K_y (VY x VY), row-major; ax, ay the acceleration
+    __device__ __forceinline__ void load(const float* K, float axf, float ayf, int warp, int lane) {
+        mX = warp / XS; nX = warp % XS; mY = warp / YS; nY = warp % YS;
+        gq = lane >> 2; tq = lane & 3;
+#pragma unroll
+        for (int ks = 0; ks < XS; ++ks)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)      // B[k][n] = a_x K_x[8 nX + n][8 ks + k]
+                split_tf32(axf * K[(8 * nX + gq) * QX2 + 8 * ks + tq + 4 * h], bxh[ks][h], bxl[ks][h]);
+#pragma unroll
+        for (int ks = 0; ks < YS; ++ks)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)      // B[k][n] = a_y K_y[8 nY + n][8 ks + k]
+                split_tf32(ayf * K[QX2 * QX2 + (8 * nY + gq) * VY + 8 * ks + tq + 4 * h], byh[ks][h], byl[ks][h]);
+    }
+
+    __device__ __forceinline__ void run(const float4* fr, float4* sKx, float4* sKy) const {
+        const float* ff = reinterpret_cast<const float*>(fr);
+        float* kxo = reinterpret_cast<float*>(sKx);
+        float* kyo = reinterpret_cast<float*>(sKy);
+        const int R0 = 16 * mX + gq, jy0 = R0 >> 2, rx = R0 & 3;       // X rows: (j_y, c)
+        float dx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < XS; ++ks) {
+            const int i0 = 8 * ks + tq;
+            const float a[4] = {ff[(jy0 * SP + i0) * 4 + rx], ff[((jy0 + 2) * SP + i0) * 4 + rx],
+                                ff[(jy0 * SP + i0 + 4) * 4 + rx], ff[((jy0 + 2) * SP + i0 + 4) * 4 + rx]};
+            mma_3xtf32(dx, a, bxh[ks][0], bxl[ks][0], bxh[ks][1], bxl[ks][1]);
+        }
+        const int ixo = 8 * nX + 2 * tq;
+        kxo[(jy0 * SP + ixo) * 4 + rx] = dx[0];
+        kxo[(jy0 * SP + ixo + 1) * 4 + rx] = dx[1];
+        kxo[((jy0 + 2) * SP + ixo) * 4 + rx] = dx[2];
+        kxo[((jy0 + 2) * SP + ixo + 1) * 4 + rx] = dx[3];
+        const int Q0 = 16 * mY + gq, ix0 = Q0 >> 2, ry = Q0 & 3;       // Y rows: (i_x, c)
+        float dy[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < YS; ++ks) {
+            const int j0 = 8 * ks + tq;
+            const float a[4] = {ff[(j0 * SP + ix0) * 4 + ry], ff[(j0 * SP + ix0 + 2) * 4 + ry],
+                                ff[((j0 + 4) * SP + ix0) * 4 + ry], ff[((j0 + 4) * SP + ix0 + 2) * 4 + ry]};
+            mma_3xtf32(dy, a, byh[ks][0], byl[ks][0], byh[ks][1], byl[ks][1]);
+        }
+        const int jyo = 8 * nY + 2 * tq;
+        kyo[(jyo * SP + ix0) * 4 + ry] = dy[0];
+        kyo[((jyo + 1) * SP + ix0) * 4 + ry] = dy[1];
+        kyo[(jyo * SP + ix0 + 2) * 4 + ry] = dy[2];
+        kyo[((jyo + 1) * SP + ix0 + 2) * 4 + ry] = dy[3];
+    }
+};
+
 // 1/x on the special-function unit (x >= 1e-30 here; beyond 1e38 it flushes to 0).
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;

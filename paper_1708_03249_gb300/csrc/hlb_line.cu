@@ -27,10 +27,24 @@ struct LineBuf {
 
 constexpr int kLineDepth = 2;   // iterations in flight
 
+// The force term on the tensor cores (ForceMMA: three TF32 products, FP32
+// accumulation) for slabs of at least HLB_LINE_MMA_MIN_S velocities that tile
+// into 16 x 8 x 8 blocks.  There the FMA form is bound by shared-memory
+// wavefronts (each thread reads its a K row and the fibre's four-cell words
+// for every term); the tensor-core form reads each fibre value once per tile
+// and keeps a K in registers.
+#ifndef HLB_LINE_MMA_MIN_S
+#define HLB_LINE_MMA_MIN_S 512
+#endif
+template <int QX2, int VY>
+__host__ __device__ constexpr bool line_uses_mma() {
+    return HLB_LINE_MMA_MIN_S > 0 && QX2 * VY >= HLB_LINE_MMA_MIN_S && QX2 % 8 == 0 && VY % 8 == 0;
+}
+
 template <int QX2, int VY>
 constexpr size_t line_smem_bytes() {
-    return kLineDepth * sizeof(LineBuf<QX2, VY>) + 2 * VY * (QX2 + 1) * sizeof(float4) +
-           pair_kdup_pairs<QX2, VY>() * sizeof(float2) + (kLineDepth + 2) * 8 + 16;
+    return kLineDepth * sizeof(LineBuf<QX2, VY>) + (line_uses_mma<QX2, VY>() ? 4 : 2) * VY * (QX2 + 1) * sizeof(float4) +
+           (line_uses_mma<QX2, VY>() ? 0 : pair_kdup_pairs<QX2, VY>() * sizeof(float2)) + (kLineDepth + 3) * 8 + 16;
 }
 
 template <int ADV, int QX2, int VY>
@@ -43,13 +57,18 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     constexpr int SP = QX2 + 1;              // padded sF row (float4: cells x0 .. x0+3)
     constexpr int KXR = QX2 + 2, KYR = VY + 2;
     using Buf = LineBuf<QX2, VY>;
+    constexpr bool kMMA = line_uses_mma<QX2, VY>();
     extern __shared__ __align__(128) unsigned char msm[];
     Buf* buf = reinterpret_cast<Buf*>(msm);
     float4* sF = reinterpret_cast<float4*>(msm + kLineDepth * sizeof(Buf));    // [2][VY][SP]
-    float2* sKd = reinterpret_cast<float2*>(sF + 2 * VY * SP);                   // duplicated a K rows
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sKd + pair_kdup_pairs<QX2, VY>());
+    float4* sKx = sF + 2 * VY * SP;                   // [VY][SP]: a_x K_x f, four cells (tensor-core path)
+    float4* sKy = sKx + VY * SP;                      // [VY][SP]: a_y K_y f
+    float2* sKd = reinterpret_cast<float2*>(sF + (kMMA ? 4 : 2) * VY * SP);     // FMA path: duplicated a K rows
+    unsigned long long* bars =
+        reinterpret_cast<unsigned long long*>(sKd + (kMMA ? 0 : pair_kdup_pairs<QX2, VY>()));
     unsigned long long* xch = bars + kLineDepth;                                 // [2]: sF[b] written by every warp
-    int* sAbort = reinterpret_cast<int*>(xch + 2);
+    unsigned long long* xch2 = xch + 2;                                          // sKx, sKy written by every warp
+    int* sAbort = reinterpret_cast<int*>(xch2 + 1);
 
     const Work W = works[blockIdx.x];
     const InstDev& I = g.inst[W.inst];
@@ -77,11 +96,15 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     const float sv = static_cast<const float*>(g.wscale)[v];
     const float isv = 1.0f / sv;
     const float* K = static_cast<const float*>(g.K);
-    {
+    ForceMMA<QX2, VY> mma;
+    if constexpr (kMMA) {
+        mma.load(K, (float)I.ax, (float)I.ay, t >> 5, t & 31);
+    } else {
         const float axf = (float)I.ax, ayf = (float)I.ay;
         for (int e = t; e < QX2 * QX2; e += S) sKd[(e / QX2) * KXR + e % QX2] = f2(axf * K[e]);
         for (int e = t; e < VY * VY; e += S) sKd[QX2 * KXR + (e / VY) * KYR + e % VY] = f2(ayf * K[QX2 * QX2 + e]);
     }
+    (void)mma;
     const float2 dt2 = f2((float)I.dt), isv2 = f2(isv), vxs = f2(vx * isv);
     const float* invdx = static_cast<const float*>(g.inv_dx) + I.dx_off;
     const float* fsI = fs + I.f_off;
@@ -135,6 +158,7 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
         for (int d = 0; d < kLineDepth; ++d) mbar_init(&bars[d], 1);
         mbar_init(&xch[0], S / 32);
         mbar_init(&xch[1], S / 32);
+        mbar_init(xch2, S / 32);
         *sAbort = 0;
         mbar_init_fence();
         for (int p = 0; p < kLineDepth - 1; ++p) expect(p);
@@ -237,25 +261,37 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
         issue(p + kLineDepth - 1);
         // a_x K_x f + a_y K_y f at the four cells
         const float4* fr = sF + b * VY * SP;
-        const float4* kxr = reinterpret_cast<const float4*>(sKd + ix * KXR);
-        const float4* kyr = reinterpret_cast<const float4*>(sKd + QX2 * KXR + jy * KYR);
         float2 fk01 = f2(0.0f), fk23 = f2(0.0f);
+        if constexpr (kMMA) {
+            // every warp's tiles, exchanged through xch2 (sKx, sKy are free
+            // again: every warp passed xch[b] after reading them last time)
+            mma.run(fr, sKx, sKy);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(xch2);
+            if (!mbar_wait(xch2, p & 1, g.err, g.wait_ns)) *sAbort = 1;
+            const float4 ex = sKx[jy * SP + ix], ey = sKy[jy * SP + ix];
+            fk01 = __fadd2_rn(make_float2(ex.x, ex.y), make_float2(ey.x, ey.y));
+            fk23 = __fadd2_rn(make_float2(ex.z, ex.w), make_float2(ey.z, ey.w));
+        } else {
+            const float4* kxr = reinterpret_cast<const float4*>(sKd + ix * KXR);
+            const float4* kyr = reinterpret_cast<const float4*>(sKd + QX2 * KXR + jy * KYR);
 #pragma unroll
-        for (int i = 0; i < QX2; i += 2) {
-            const float4 kk = kxr[i >> 1], fa = fr[jy * SP + i], fb = fr[jy * SP + i + 1];
-            fk01 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), fk01);
-            fk23 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), fk23);
-            fk01 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), fk01);
-            fk23 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), fk23);
-        }
-        if (VY > 1) {
-#pragma unroll
-            for (int j = 0; j < VY; j += 2) {
-                const float4 kk = kyr[j >> 1], fa = fr[j * SP + ix], fb = fr[(j + 1) * SP + ix];
+            for (int i = 0; i < QX2; i += 2) {
+                const float4 kk = kxr[i >> 1], fa = fr[jy * SP + i], fb = fr[jy * SP + i + 1];
                 fk01 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), fk01);
                 fk23 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), fk23);
                 fk01 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), fk01);
                 fk23 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), fk23);
+            }
+            if (VY > 1) {
+#pragma unroll
+                for (int j = 0; j < VY; j += 2) {
+                    const float4 kk = kyr[j >> 1], fa = fr[j * SP + ix], fb = fr[(j + 1) * SP + ix];
+                    fk01 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), fk01);
+                    fk23 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), fk23);
+                    fk01 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), fk01);
+                    fk23 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), fk23);
+                }
             }
         }
 #pragma unroll

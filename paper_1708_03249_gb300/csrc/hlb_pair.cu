@@ -56,35 +56,6 @@ constexpr size_t pair_smem_bytes() {
            (pair_uses_mma<QX2, VY>() ? 0 : pair_kdup_pairs<QX2, VY>() * sizeof(float2)) + (kPairDepth + 3) * 8 + 16;
 }
 
-// D += A B on the tensor cores, TF32 operands, FP32 accumulation
-// (m16n8k8; A row-major 16 x 8, B column-major 8 x 8).
-__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// x = hi + lo with hi a TF32 value (round to nearest); lo keeps the rest
-// (its own low bits are dropped by the tensor core).
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-    lo = __float_as_uint(x - __uint_as_float(hi));
-}
-
-// D += A B in three TF32 products (A_lo B_hi + A_hi B_lo + A_hi B_hi), close
-// to an FP32 product; a[k] are FP32 values, b{0,1}{h,l} split fragments.
-__device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&a)[4], uint32_t b0h, uint32_t b0l,
-                                           uint32_t b1h, uint32_t b1l) {
-    uint32_t ah[4], al[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) split_tf32(a[k], ah[k], al[k]);
-    mma_tf32(d, al[0], al[1], al[2], al[3], b0h, b1h);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0l, b1l);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0h, b1h);
-}
-
 template <int ADV, int QX2, int VY>
 __global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? HLB_PAIR_MIN_BLOCKS : 2)))
 march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
@@ -135,34 +106,18 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     const float isv = 1.0f / sv;
     const float* K = static_cast<const float*>(g.K);
     const int warp = t >> 5, lane = t & 31;
-    // FMA path: this thread's rows of K_x and K_y.  Tensor-core path: warp w
-    // computes one 16 x 8 tile of (a_x K_x f)^T and one of (a_y K_y f)^T, the
-    // contractions written as F^T K^T with F^T rows (j_y, cell/row) resp.
-    // (i_x, cell/row); the B fragments (a K)^T stay in registers, split hi/lo.
-
-    constexpr int XS = QX2 / 8, YS = VY / 8;        // k-steps (tensor-core path)
-    uint32_t bxh[kMMA ? XS : 1][2], bxl[kMMA ? XS : 1][2], byh[kMMA ? YS : 1][2], byl[kMMA ? YS : 1][2];
-    const int mX = warp / (QX2 / 8 > 0 ? QX2 / 8 : 1), nX = warp % (QX2 / 8 > 0 ? QX2 / 8 : 1);
-    const int mY = warp / (VY / 8 > 0 ? VY / 8 : 1), nY = warp % (VY / 8 > 0 ? VY / 8 : 1);
-    const int gq = lane >> 2, tq = lane & 3;
+    // FMA path: this thread's rows of a K, duplicated into pairs in shared
+    // memory.  Tensor-core path: the B fragments of warp w's tiles in
+    // registers (ForceMMA).
+    ForceMMA<QX2, VY> mma;
     if constexpr (kMMA) {
-        const float axf = (float)I.ax, ayf = (float)I.ay;
-#pragma unroll
-        for (int ks = 0; ks < XS; ++ks)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)      // B[k][n] = a_x K_x[8 nX + n][8 ks + k]
-                split_tf32(axf * K[(8 * nX + gq) * QX2 + 8 * ks + tq + 4 * h], bxh[ks][h], bxl[ks][h]);
-#pragma unroll
-        for (int ks = 0; ks < YS; ++ks)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)      // B[k][n] = a_y K_y[8 nY + n][8 ks + k]
-                split_tf32(ayf * K[QX2 * QX2 + (8 * nY + gq) * VY + 8 * ks + tq + 4 * h], byh[ks][h], byl[ks][h]);
+        mma.load(K, (float)I.ax, (float)I.ay, warp, lane);
     } else {
         const float axf = (float)I.ax, ayf = (float)I.ay;
         for (int e = t; e < QX2 * QX2; e += S) sKd[(e / QX2) * KXR + e % QX2] = f2(axf * K[e]);
         for (int e = t; e < VY * VY; e += S) sKd[QX2 * KXR + (e / VY) * KYR + e % VY] = f2(ayf * K[QX2 * QX2 + e]);
     }
-    (void)bxh; (void)bxl; (void)byh; (void)byl; (void)mX; (void)nX; (void)mY; (void)nY;
+    (void)mma;
     const float2 dt2 = f2((float)I.dt);
     const float2 vxs = f2(vx * isv), vys = f2(vy * isv * (float)I.inv_dy), isv2 = f2(isv), sv2 = f2(sv);
     const float* invdx = static_cast<const float*>(g.inv_dx) + I.dx_off;
@@ -329,44 +284,6 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     };
     float2 Fm = __fmul2_rn(vxs, face(xpos, w));
 
-    // a_x K_x f and a_y K_y f of one pair on the tensor cores: warp w takes
-    // the X tile (rows 16 mX.., columns 8 nX..) of (K_x-contraction)^T and the
-    // Y tile (rows 16 mY.., columns 8 nY..) of (K_y-contraction)^T and stores
-    // them in the layout of sF.
-    auto force_mma = [&](const float4* fr) {
-        const float* ff = reinterpret_cast<const float*>(fr);
-        float* kxo = reinterpret_cast<float*>(sKx);
-        float* kyo = reinterpret_cast<float*>(sKy);
-        const int R0 = 16 * mX + gq, jy0 = R0 >> 2, rx = R0 & 3;       // X rows: (j_y, cell/row)
-        float dx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int ks = 0; ks < XS; ++ks) {
-            const int i0 = 8 * ks + tq;
-            const float a[4] = {ff[(jy0 * SP + i0) * 4 + rx], ff[((jy0 + 2) * SP + i0) * 4 + rx],
-                                ff[(jy0 * SP + i0 + 4) * 4 + rx], ff[((jy0 + 2) * SP + i0 + 4) * 4 + rx]};
-            mma_3xtf32(dx, a, bxh[ks][0], bxl[ks][0], bxh[ks][1], bxl[ks][1]);
-        }
-        const int ixo = 8 * nX + 2 * tq;
-        kxo[(jy0 * SP + ixo) * 4 + rx] = dx[0];
-        kxo[(jy0 * SP + ixo + 1) * 4 + rx] = dx[1];
-        kxo[((jy0 + 2) * SP + ixo) * 4 + rx] = dx[2];
-        kxo[((jy0 + 2) * SP + ixo + 1) * 4 + rx] = dx[3];
-        const int Q0 = 16 * mY + gq, ix0 = Q0 >> 2, ry = Q0 & 3;       // Y rows: (i_x, cell/row)
-        float dy[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int ks = 0; ks < YS; ++ks) {
-            const int j0 = 8 * ks + tq;
-            const float a[4] = {ff[(j0 * SP + ix0) * 4 + ry], ff[(j0 * SP + ix0 + 2) * 4 + ry],
-                                ff[((j0 + 4) * SP + ix0) * 4 + ry], ff[((j0 + 4) * SP + ix0 + 2) * 4 + ry]};
-            mma_3xtf32(dy, a, byh[ks][0], byl[ks][0], byh[ks][1], byl[ks][1]);
-        }
-        const int jyo = 8 * nY + 2 * tq;
-        kyo[(jyo * SP + ix0) * 4 + ry] = dy[0];
-        kyo[((jyo + 1) * SP + ix0) * 4 + ry] = dy[1];
-        kyo[(jyo * SP + ix0 + 2) * 4 + ry] = dy[2];
-        kyo[((jyo + 1) * SP + ix0 + 2) * 4 + ry] = dy[3];
-    };
-
     // Per pair: wait for its copies; write the centre values to sF[b] and
     // arrive on xch[b]; evaluate the faces (the other warps catch up
     // meanwhile); wait on xch[b]; then the force term, which reads every
@@ -404,7 +321,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             if (!mbar_wait(&xch[b], (p >> 1) & 1, g.err, g.wait_ns)) *sAbort = 1;
             if (*sAbort) break;
             issue(p + kPairDepth - 1);
-            force_mma(sF + b * VY * SP);
+            mma.run(sF + b * VY * SP, sKx, sKy);
             __syncwarp();
             if (lane == 0) mbar_arrive(xch2);
         }

@@ -211,14 +211,25 @@ def test_fp32_2d_q8_16x8(adv):
     _check_fp32(got, mom, refs)
 
 
-@pytest.mark.parametrize("Qx,Qy,nx", [(16, 0, 31), (4, 0, 31), (8, 8, 55), (4, 4, 13)])
+@pytest.mark.parametrize("Qx,Qy,nx", [(16, 0, 31), (4, 0, 31), (8, 8, 55), (4, 4, 13), (16, 16, 23)])
 def test_fp32_1d_shapes_ragged(Qx, Qy, nx):
-    # 1D FP32: the line kernel (two cells per iteration; whole-warp slabs:
-    # 32 x 1, 16 x 8, 8 x 4) and the scalar kernel (8 x 1); odd lengths end a
-    # segment on a single cell
+    # 1D FP32: the line kernel (four cells per iteration; whole-warp slabs:
+    # 32 x 1, 16 x 8, 8 x 4, and 32 x 16 with the force term on the tensor
+    # cores) and the scalar kernel (8 x 1); lengths that are not a multiple of
+    # four end a segment on a partial iteration
     cfg = W.make(Qx=Qx, Qy=Qy, nx=nx, advection=W.WENO5, precision=W.FP32, T_left=0.7, T_right=1.3,
                  Kn=0.2, **(W.gravity(0.4, 30.0) if Qy else {"ax": -0.4}))
     got, mom, N, refs = run_pair(cfg, 10, init=(1.0, 0.05, 0.0, 1.0))
+    _check_fp32(got, mom, refs)
+
+
+@pytest.mark.parametrize("adv", [W.WENO5, W.UPWIND2])
+def test_fp32_1d_q16_tensor_core_force(adv):
+    # 32 x 16 slabs: a K f by three TF32 products on the tensor cores; a strong
+    # oblique force so that the force term carries the update
+    cfg = W.make(Qx=16, Qy=16, nx=42, advection=adv, precision=W.FP32, T_left=0.8, T_right=1.6,
+                 Kn=0.3, **W.gravity(0.9, 35.0))
+    got, mom, N, refs = run_pair(cfg, 8, init=(1.0, 0.1, 0.05, 1.1))
     _check_fp32(got, mom, refs)
 
 
