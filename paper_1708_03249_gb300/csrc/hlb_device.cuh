@@ -133,13 +133,22 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
     lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
+// x = hi + lo with hi the TF32 truncation of x (its low 13 mantissa bits
+// cleared: one logic operation, where the rounding conversion takes several);
+// lo = x - hi is exact and below 2^-10 |x|.
+__device__ __forceinline__ void split_tf32_rz(float x, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
 // D += A B in three TF32 products (A_lo B_hi + A_hi B_lo + A_hi B_hi), close
-// to an FP32 product; a[k] are FP32 values, b{0,1}{h,l} split fragments.
+// to an FP32 product; a[k] are FP32 values (split here by truncation, once per
+// use), b{0,1}{h,l} fragments split once by rounding.
 __device__ __forceinline__ void mma_3xtf32(float (&d)[4], const float (&a)[4], uint32_t b0h, uint32_t b0l,
                                            uint32_t b1h, uint32_t b1l) {
     uint32_t ah[4], al[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) split_tf32(a[k], ah[k], al[k]);
+    for (int k = 0; k < 4; ++k) split_tf32_rz(a[k], ah[k], al[k]);
     mma_tf32(d, al[0], al[1], al[2], al[3], b0h, b1h);
     mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0l, b1l);
     mma_tf32(d, ah[0], ah[1], ah[2], ah[3], b0h, b1h);
