@@ -100,6 +100,12 @@ struct hlb_handle {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t stage_free = nullptr, stage_filled = nullptr;
     bool staged = false;
+    // velocity-set groups after the first step on streams of their own (the
+    // groups share no data within a step): forked from and joined back into
+    // the handle's stream, also inside a captured graph
+    std::vector<cudaStream_t> group_stream;
+    std::vector<cudaEvent_t> group_done;
+    cudaEvent_t step_fork = nullptr;
 };
 
 namespace {
@@ -423,8 +429,9 @@ bool group_has_z_force(const hlb_handle* h, const Group& G) {
     return false;
 }
 
-// One RK-3 step of one group: three (wall, stage) pairs; buffer roles rotate.
-void enqueue_group_step(hlb_handle* h, Group& G) {
+// One RK-3 step of one group on stream st: three (node pass, wall, stage)
+// triples; buffer roles rotate.
+void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
     void* S = G.buf[G.cur].p;
     void* X = G.buf[(G.cur + 1) % 3].p;
     void* Y = G.buf[(G.cur + 2) % 3].p;
@@ -434,19 +441,19 @@ void enqueue_group_step(hlb_handle* h, Group& G) {
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (h->time_kernels) {
             cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
-            cudaEventRecord(e0, h->stream);
+            cudaEventRecord(e0, st_);
         }
         const bool march = G.march_ok && !group_has_z_force(h, G);
-        if (march) hlb::launch_node(G.precision, G.dev, ins[st], h->stream);
-        hlb::launch_wall(G.precision, G.adv, G.dev, ins[st], h->stream);
-        if (h->time_kernels) cudaEventRecord(e1, h->stream);
+        if (march) hlb::launch_node(G.precision, G.dev, ins[st], st_);
+        hlb::launch_wall(G.precision, G.adv, G.dev, ins[st], st_);
+        if (h->time_kernels) cudaEventRecord(e1, st_);
         if (march)
             hlb::launch_march(G.precision, G.adv, G.QX2, G.VY, G.TY, G.dev, (const hlb::Work*)G.d_works.p,
-                              G.nworks, ins[st], S, outs[st], st, h->stream);
+                              G.nworks, ins[st], S, outs[st], st, st_);
         else
-            hlb::launch_stage(G.precision, G.adv, G.dev, ins[st], S, outs[st], st, G.grid, G.block, G.smem, h->stream);
+            hlb::launch_stage(G.precision, G.adv, G.dev, ins[st], S, outs[st], st, G.grid, G.block, G.smem, st_);
         if (h->time_kernels) {
-            cudaEventRecord(e2, h->stream);
+            cudaEventRecord(e2, st_);
             h->timer.wall.push_back({e0, e1});
             h->timer.stage.push_back({e1, e2});
         }
@@ -456,7 +463,20 @@ void enqueue_group_step(hlb_handle* h, Group& G) {
 }
 
 void enqueue_step(hlb_handle* h) {
-    for (auto& G : h->groups) enqueue_group_step(h, *G);
+    const size_t ng = h->groups.size();
+    if (ng == 1 || h->time_kernels || h->group_stream.size() + 1 != ng) {
+        for (auto& G : h->groups) enqueue_group_step(h, *G, h->stream);
+        return;
+    }
+    // fork: groups 1.. wait for the work already on the handle's stream
+    cudaEventRecord(h->step_fork, h->stream);
+    for (size_t k = 1; k < ng; ++k) {
+        cudaStreamWaitEvent(h->group_stream[k - 1], h->step_fork, 0);
+        enqueue_group_step(h, *h->groups[k], h->group_stream[k - 1]);
+        cudaEventRecord(h->group_done[k - 1], h->group_stream[k - 1]);
+    }
+    enqueue_group_step(h, *h->groups[0], h->stream);
+    for (size_t k = 1; k < ng; ++k) cudaStreamWaitEvent(h->stream, h->group_done[k - 1], 0);   // join
 }
 
 // Kernels one RK-3 step launches: per stage the node pass (sums, factor
@@ -596,6 +616,17 @@ hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_h
     }
     h->total_nodes = nodes;
     h->total_values = values;
+    if (h->groups.size() > 1) {
+        HLB_CUDA(cudaEventCreateWithFlags(&h->step_fork, cudaEventDisableTiming));
+        for (size_t k = 1; k < h->groups.size(); ++k) {
+            cudaStream_t s2 = nullptr;
+            cudaEvent_t e2 = nullptr;
+            HLB_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+            h->group_stream.push_back(s2);
+            HLB_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+            h->group_done.push_back(e2);
+        }
+    }
     *out = h.release();
     return HLB_OK;
 }
@@ -609,6 +640,9 @@ void hlb_destroy(hlb_handle* h) {
     if (h->stage_free) cudaEventDestroy(h->stage_free);
     if (h->stage_filled) cudaEventDestroy(h->stage_filled);
     if (h->stage_buf) cudaFree(h->stage_buf);
+    for (cudaStream_t s2 : h->group_stream) { cudaStreamSynchronize(s2); cudaStreamDestroy(s2); }
+    for (cudaEvent_t e2 : h->group_done) cudaEventDestroy(e2);
+    if (h->step_fork) cudaEventDestroy(h->step_fork);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
