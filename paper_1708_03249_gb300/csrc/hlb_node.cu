@@ -298,13 +298,48 @@ __device__ __forceinline__ void full_range_G_df(float2 u, float2 Tm1, int N, flo
         if (l < N) G[l + 1] = df_add(df_mul(u, G[l]), df_mul(df_mul(make_float2((float)l, 0.0f), Tm1), G[l - 1]));
 }
 
+// Two dot products at once (table rows 2k and 2k+1, one per lane of the f32x2
+// registers) with the same double-float coefficients G, by the compensated
+// dot product Dot2 of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005):
+// TwoProduct of the high parts, TwoSum into the running sum, the rounding
+// errors and the products with the low parts of the table and of G summed in
+// the error term.  The result is as accurate as a double-float evaluation
+// (about twice the FP32 precision, times the condition number) at a third of
+// its instructions.  P[l] = (T_2k,l hi, T_2k+1,l hi, T_2k,l lo, T_2k+1,l lo).
 template <int NM>
-__device__ __forceinline__ float2 dot_df(const float2* Trow, const float2 (&G)[NM], int N) {
-    float2 acc = df_mul(Trow[0], G[0]);
+__device__ __forceinline__ void dot2_pair(const float4* P, const float2 (&G)[NM], int N, float2& r0, float2& r1) {
+    float2 acc = f2(0.0f), err = f2(0.0f);
 #pragma unroll
-    for (int l = 1; l < NM; ++l)
-        if (l <= N) acc = df_add(acc, df_mul(Trow[l], G[l]));
-    return acc;
+    for (int l = 0; l < NM; ++l) {
+        if (l <= N) {
+            const float4 t = P[l];
+            const float2 th = make_float2(t.x, t.y), tl = make_float2(t.z, t.w);
+            const float2 gh = f2(G[l].x), gl = f2(G[l].y);
+            const float2 q = __fmul2_rn(th, f2(-G[l].x));        // -p, p = fl(th gh)
+            const float2 e = __ffma2_rn(th, gh, q);               // th gh - p, exact
+            const float2 sum = fsub2(acc, q);                     // acc + p
+            const float2 bb = fsub2(sum, acc);
+            const float2 t2 = fsub2(fsub2(acc, fsub2(sum, bb)), __fadd2_rn(q, bb));   // (acc + p) - sum, exact
+            acc = sum;
+            err = __fadd2_rn(err, __fadd2_rn(t2, e));
+            err = __ffma2_rn(th, gl, __ffma2_rn(tl, gh, err));
+        }
+    }
+    r0 = df_add(make_float2(acc.x, 0.0f), make_float2(err.x, 0.0f));
+    r1 = df_add(make_float2(acc.y, 0.0f), make_float2(err.y, 0.0f));
+}
+
+// line[k] = (row k of a paired table . G) (times scale when given), k < nrows
+template <int NM>
+__device__ __forceinline__ void lines_dot2(float* line, const float4* P, int nrows, const float2 (&G)[NM], int N,
+                                           const float2* scale) {
+    for (int k = 0; k < nrows; k += 2) {
+        float2 v0, v1;
+        dot2_pair<NM>(P + (k >> 1) * (N + 1), G, N, v0, v1);
+        if (scale) { v0 = df_mul(v0, *scale); v1 = df_mul(v1, *scale); }
+        line[k] = v0.x + v0.y;
+        if (k + 1 < nrows) line[k + 1] = v1.x + v1.y;
+    }
 }
 
 template <int NM>
@@ -312,16 +347,36 @@ __global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const fl
     extern __shared__ __align__(16) float2 cdf[];
     const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz, Qx = g.Qx, QX2 = g.QX2, VY = g.VY, VZ = g.VZ, ncp = g.ncp;
     const int nrec = 5 * Nx + 1;
-    const int nT = Qx * (Nx + 1) + VY * (Ny + 1) + VZ * (Nz + 1);
-    float2* sRec = cdf;
-    float2* sT = sRec + nrec;
-    float* sLine = reinterpret_cast<float*>(cdf + ((nrec + nT + 1) & ~1)) + (threadIdx.x >> 5) * 32 * ncp;   // [32][ncp] per warp
+    // the tables T_x (Qx rows), T_y (VY rows), T_z (VZ rows) of Nx+1, Ny+1,
+    // Nz+1 double-float entries, re-laid as row pairs (dot2_pair); an odd last
+    // row is paired with zeros
+    const int px = (Qx + 1) >> 1, py = (VY + 1) >> 1, pz = (VZ + 1) >> 1;
+    const int nP = px * (Nx + 1) + py * (Ny + 1) + pz * (Nz + 1);
+    float4* sP = reinterpret_cast<float4*>(cdf);
+    float2* sRec = reinterpret_cast<float2*>(sP + nP);
+    float* sLine = reinterpret_cast<float*>(sP + nP + ((nrec + 1) >> 1)) + (threadIdx.x >> 5) * 32 * ncp;   // [32][ncp] per warp
     for (int i = threadIdx.x; i < nrec; i += blockDim.x) sRec[i] = g.recf[i];
-    for (int i = threadIdx.x; i < nT; i += blockDim.x) sT[i] = g.Tf[i];
+    {
+        const float2* Tx = g.Tf;
+        const float2* Ty = Tx + Qx * (Nx + 1);
+        const float2* Tz = Ty + VY * (Ny + 1);
+        auto pairs = [&](float4* dst, const float2* T, int rows, int n1) {
+            const int np = (rows + 1) >> 1;
+            for (int i = threadIdx.x; i < np * n1; i += blockDim.x) {
+                const int k = 2 * (i / n1), l = i % n1;
+                const float2 a = T[k * n1 + l];
+                const float2 b = k + 1 < rows ? T[(k + 1) * n1 + l] : make_float2(0.0f, 0.0f);
+                dst[i] = make_float4(a.x, b.x, a.y, b.y);
+            }
+        };
+        pairs(sP, Tx, Qx, Nx + 1);
+        pairs(sP + px * (Nx + 1), Ty, VY, Ny + 1);
+        pairs(sP + px * (Nx + 1) + py * (Ny + 1), Tz, VZ, Nz + 1);
+    }
     __syncthreads();
-    const float2* sTx = sT;
-    const float2* sTy = sTx + Qx * (Nx + 1);
-    const float2* sTz = sTy + VY * (Ny + 1);
+    const float4* sPx = sP;
+    const float4* sPy = sPx + px * (Nx + 1);
+    const float4* sPz = sPy + py * (Ny + 1);
     const int lane = threadIdx.x & 31;
     const int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     const int node = base + lane;
@@ -348,26 +403,17 @@ __global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const fl
 #pragma unroll 1
             for (int r = 0; r < 2; ++r) {                    // n g_x, p_x > 0 then p_x < 0
                 half_range_G_df<NM>(r, in, sRec, Nx, G);
-                for (int kk = 0; kk < Qx; ++kk) {
-                    const float2 v = df_mul(dot_df<NM>(sTx + kk * (Nx + 1), G, Nx), in.n);
-                    line[r * Qx + kk] = v.x + v.y;
-                }
+                lines_dot2<NM>(line + r * Qx, sPx, Qx, G, Nx, &in.n);
             }
             if (g.Qy) {
                 full_range_G_df<NM>(in.uy, in.Tm1, Ny, G);
-                for (int j = 0; j < VY; ++j) {
-                    const float2 v = dot_df<NM>(sTy + j * (Ny + 1), G, Ny);
-                    line[QX2 + j] = v.x + v.y;
-                }
+                lines_dot2<NM>(line + QX2, sPy, VY, G, Ny, nullptr);
             } else {
                 line[QX2] = 1.0f;
             }
             if (g.Qz) {
                 full_range_G_df<NM>(in.uz, in.Tm1, Nz, G);
-                for (int j = 0; j < VZ; ++j) {
-                    const float2 v = dot_df<NM>(sTz + j * (Nz + 1), G, Nz);
-                    line[QX2 + VY + j] = v.x + v.y;
-                }
+                lines_dot2<NM>(line + QX2 + VY, sPz, VZ, G, Nz, nullptr);
             } else {
                 line[QX2 + VY] = 1.0f;
             }
@@ -424,8 +470,8 @@ void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t 
         sums_kernel<float><<<blocks_a, 256, smem_a, st>>>(g, (const float*)fs, (float*)g.sums);
         const int nmax = max(g.Nx, max(g.Ny, g.Nz));
         if (g.use_df && nmax < 16) {
-            const int nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
-            const size_t smem_c = 8 * ((size_t)nrec + nT + 1) + 4 * 32 * (size_t)g.ncp * 4;
+            const int nP = (g.Qx + 1) / 2 * (g.Nx + 1) + (g.VY + 1) / 2 * (g.Ny + 1) + (g.VZ + 1) / 2 * (g.Nz + 1);
+            const size_t smem_c = 16 * ((size_t)nP + (nrec + 1) / 2) + 4 * 32 * (size_t)g.ncp * 4;
             const int blocks_c = (g.nnodes + 127) / 128;
             if (nmax < 8) coef_df_kernel<8><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
             else if (nmax < 12) coef_df_kernel<12><<<blocks_c, 128, smem_c, st>>>(g, (const float*)g.sums);
