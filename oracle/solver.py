@@ -20,7 +20,8 @@ Steps of one evaluation of L[f] (Eq. "eq:L_def", multi-D form Eq.
   3. moments n, u, T (Eq. "eq:fmoms"), tau = Kn/n (Eq. "eq:tau");
   4. feq = n g_x g_y g_z (App. A) with the projected equilibria;
   5. force term -sum_a a_a (K_a f) along each momentum axis (App. A;
-     a = F/m; a = -g x gives the +mg dp f of Eq. "eq:L_def");
+     a = F/m; a = -g x gives the +mg dp f of Eq. "eq:L_def"); a_a is the
+     uniform value plus an optional per-node field;
   6. L = -div - force - (f - feq)/tau;  then the RK-3 of Eq. "eq:rk3".
 """
 from __future__ import annotations
@@ -60,6 +61,14 @@ class Config:
     ay: float = 0.0
     az: float = 0.0
     Kn: float = math.inf
+    # Optional per-node acceleration fields, arrays of shape (ny, nx), added
+    # to the uniform (ax, ay, az): e.g. a force from a potential, a = -grad V / m.
+    # The paper's tests use a constant force only; its conclusion (Sec.
+    # "sec:conc") presents the force-term formalism as general, and the force
+    # term of App. A acts node by node, so a(x) enters it pointwise.
+    ax_field: object = None
+    ay_field: object = None
+    az_field: object = None
     extra: dict = field(default_factory=dict)
 
 
@@ -260,16 +269,27 @@ class Solver:
         return float((n * self.dx[None, :]).sum() * (self.dy if self.two_d else 1.0))
 
     # -- right-hand side -----------------------------------------------------
+    def acceleration(self, axis: int):
+        """a_axis at every node, shape (ny, nx, 1, 1, 1): the uniform value
+        plus the per-node field, if any."""
+        cfg = self.cfg
+        a = np.full((cfg.ny, cfg.nx), (cfg.ax, cfg.ay, cfg.az)[axis], dtype=np.float64)
+        fld = (cfg.ax_field, cfg.ay_field, cfg.az_field)[axis]
+        if fld is not None:
+            a = a + np.asarray(fld, dtype=np.float64).reshape(cfg.ny, cfg.nx)
+        return a[:, :, None, None, None]
+
     def source(self, f):
         """Local part of L[f]: -sum_a a_a (K_a f) - (f - feq)/tau (no advection)."""
         cfg, vs = self.cfg, self.vs
         S = np.zeros_like(f)
-        if cfg.ax:
-            S -= cfg.ax * np.einsum("ij,...j->...i", vs.Kx, f)
-        if cfg.ay and vs.Qy:
-            S -= cfg.ay * np.einsum("ij,...jk->...ik", vs.Ky, f)
-        if cfg.az and vs.Qz:
-            S -= cfg.az * np.einsum("ij,...jkl->...ikl", vs.Kz, f)
+        ax, ay, az = (self.acceleration(k) for k in range(3))
+        if np.any(ax):
+            S -= ax * np.einsum("ij,...j->...i", vs.Kx, f)
+        if vs.Qy and np.any(ay):
+            S -= ay * np.einsum("ij,...jk->...ik", vs.Ky, f)
+        if vs.Qz and np.any(az):
+            S -= az * np.einsum("ij,...jkl->...ikl", vs.Kz, f)
         if math.isfinite(cfg.Kn):
             n, u, T, _ = self.moments(f)
             feq = vs.equilibrium(n, u[..., 0], u[..., 1], u[..., 2], T)

@@ -126,6 +126,63 @@ def test_homogeneous_force_and_bgk_closed_form(Qx, Qy, Qz, ax, ay, az):
     np.testing.assert_allclose(T, T0, rtol=1e-12)
 
 
+@pytest.mark.parametrize("Qx,Qy,Qz", [(4, 0, 0), (4, 4, 0), (3, 4, 4)])
+def test_homogeneous_force_field_closed_form(Qx, Qy, Qz):
+    # A per-node acceleration field on top of the uniform one: without
+    # advection every node evolves on its own, so n and T stay constant and
+    # u(t) = u0 + a(node) t exactly at every node (the closed form above, node
+    # by node).  A field applied to the wrong nodes, or transposed, fails it.
+    rng = np.random.default_rng(11)
+    ny, nx = 2, 3
+    fields = {k: rng.uniform(-0.4, 0.4, (ny, nx)) for k in ("ax_field", "ay_field", "az_field")}
+    uni = (0.1, -0.05, 0.2)
+    s = Solver(Config(Qx=Qx, Qy=Qy, Qz=Qz, nx=nx, ny=ny, ax=uni[0], ay=uni[1], az=uni[2], Kn=0.3, dt=0.01,
+                      **fields))
+    s.init_equilibrium(1.2, 0.1, -0.05, 0.9)
+    s.f = s.f * (1 + 0.1 * rng.uniform(-1, 1, s.f.shape))
+    n0, u0, T0, _ = s.moments()
+    for _ in range(40):
+        f = s.f
+        f1 = f + s.dt * s.source(f)
+        f2 = 0.75 * f + 0.25 * f1 + 0.25 * s.dt * s.source(f1)
+        s.f = f / 3 + 2 / 3 * f2 + 2 / 3 * s.dt * s.source(f2)
+    t = 40 * s.dt
+    n, u, T, _ = s.moments()
+    a = np.stack([uni[0] + fields["ax_field"], uni[1] + fields["ay_field"], uni[2] + fields["az_field"]], axis=-1)
+    for k, Qk in enumerate((Qx, Qy, Qz)):
+        if k and not Qk:
+            a[..., k] = 0.0          # an absent momentum axis feels no force
+    np.testing.assert_allclose(n, n0, rtol=1e-13)
+    np.testing.assert_allclose(u, u0 + a * t, atol=1e-13)
+    np.testing.assert_allclose(T, T0, rtol=1e-12)
+
+
+def test_potential_barometric_interior_residual_is_second_order():
+    # A gas at rest in a potential V(x) between walls at T = 1: f = n(x) w_k
+    # with n = exp(-V(x)) is the exact steady state of Eq. "eq:boltz_force"
+    # with a = -V'(x) (the isothermal profile of Eq. "eq:iso_n" for a general
+    # potential).  Away from the walls the discrete L[f] is the upwind2
+    # truncation error, O(dx^2); a field with the wrong sign (O(1)) or one
+    # evaluated a node off (O(dx)) leaves ten times more at nx = 64.
+    g, c = 0.4, 0.15
+    V = lambda x: g * x + c * np.sin(2 * np.pi * x)
+    dV = lambda x: g + 2 * np.pi * c * np.cos(2 * np.pi * x)
+    res = []
+    for nx in (32, 64, 128):
+        xc = grid_x(nx, 1.0, 0.0)[1]
+        s = Solver(Config(Qx=4, Qy=4, nx=nx, advection="upwind2", Kn=0.3, ax_field=-dV(xc)[None, :]))
+        n = np.exp(-V(s.xc))
+        s.f = n[None, :, None, None, None] * s.vs.equilibrium(np.float64(1.0), 0.0, 0.0, 0.0, np.float64(1.0))[None, None]
+        res.append(np.abs(s.rhs(s.f)[:, 5:-5]).max())
+    assert res[0] / res[1] > 3.5 and res[1] / res[2] > 3.5
+    xc = grid_x(64, 1.0, 0.0)[1]
+    for wrong in (+dV(xc), -np.roll(dV(xc), 1)):   # planted: sign flipped; field one node off
+        s = Solver(Config(Qx=4, Qy=4, nx=64, advection="upwind2", Kn=0.3, ax_field=wrong[None, :]))
+        n = np.exp(-V(s.xc))
+        s.f = n[None, :, None, None, None] * s.vs.equilibrium(np.float64(1.0), 0.0, 0.0, 0.0, np.float64(1.0))[None, None]
+        assert np.abs(s.rhs(s.f)[:, 5:-5]).max() > 10 * res[1]
+
+
 @pytest.mark.parametrize("Qx,Qy,adv", [(4, 0, "weno5"), (4, 4, "upwind2"), (6, 4, "weno5")])
 def test_free_molecular_closed_form(Qx, Qy, adv):
     # g = 0, Kn = inf, walls at T_L != T_R (Sec. V.D at g = 0): f is n_L g_L for
