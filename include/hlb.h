@@ -112,6 +112,19 @@ hlb_status hlb_set_walls(hlb_handle* h, int inst, double T_left, double T_right)
 hlb_status hlb_set_force(hlb_handle* h, int inst, double ax, double ay, double az);
 hlb_status hlb_set_Kn(hlb_handle* h, int inst, double Kn);
 
+/* Per-node acceleration field of instance `inst` (0 <= inst < ninst), added
+ * to its uniform acceleration: at node (y, x) the force term of App. A acts
+ * with a = (ax_u + ax[y nx + x], ay_u + ay[...], az_u + az[...]), e.g. the
+ * force -grad V / m of a potential V(x, y) (the conclusion, Sec. "sec:conc",
+ * presents the force-term formalism for general forces; the paper's tests use
+ * a constant one).  ax, ay, az: host arrays of nx * ny finite values in node
+ * order (y-major), copied before the call returns; NULL is a zero component;
+ * all three NULL removes the field.  With a field the step adds one launch per
+ * RK stage for the instance's velocity-set group.
+ * Errors: HLB_EINVAL (instance, non-finite value), HLB_EUNSUPPORTED (velocity
+ * set too large for the field kernel), HLB_ENOMEM, HLB_ECUDA. */
+hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const double* ay, const double* az);
+
 /* State = n g_x(ux,T) g_y(uy,T) g_z(0,T) at every node of every instance
  * (App. A equilibrium), computed on the host in FP64 and broadcast on the
  * device.  Enqueued on the handle's stream.  Errors: HLB_EINVAL (n, T <= 0). */

@@ -66,6 +66,11 @@ struct Group {
     // marching stage kernel (node + march) or the generic per-node kernel
     int TY = 1, SX = 0, nworks = 0;
     bool march_ok = false;
+    // per-node acceleration field (hlb_set_force_field): [nnodes][3] doubles,
+    // allocated on first use; one flag per member instance
+    DevBuf d_afield;
+    std::vector<char> field_on;
+    bool has_field = false;
 };
 
 struct KernelTimer {
@@ -106,6 +111,7 @@ struct hlb_handle {
     std::vector<cudaStream_t> group_stream;
     std::vector<cudaEvent_t> group_done;
     cudaEvent_t step_fork = nullptr;
+    bool once_field_prepared = false;
 };
 
 namespace {
@@ -452,6 +458,8 @@ void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
                               G.nworks, ins[st], S, outs[st], st, st_);
         else
             hlb::launch_stage(G.precision, G.adv, G.dev, ins[st], S, outs[st], st, G.grid, G.block, G.smem, st_);
+        if (G.has_field)
+            hlb::launch_force_field(G.precision, G.dev, (const double*)G.d_afield.p, ins[st], outs[st], st, st_);
         if (h->time_kernels) {
             cudaEventRecord(e2, st_);
             h->timer.wall.push_back({e0, e1});
@@ -483,7 +491,7 @@ void enqueue_step(hlb_handle* h) {
 // lines) when the marching kernel runs, the wall kernel and the stage kernel.
 long long kernels_per_step(hlb_handle* h) {
     long long n = 0;
-    for (auto& G : h->groups) n += 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2);
+    for (auto& G : h->groups) n += 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2) + (G->has_field ? 3 : 0);
     return n;
 }
 
@@ -681,6 +689,49 @@ hlb_status hlb_set_force(hlb_handle* h, int inst, double ax, double ay, double a
         if (s != HLB_OK) return s;
         fill_dev(*G);
     }
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    return HLB_OK;
+}
+
+hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const double* ay, const double* az) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (inst < 0 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    const hlb_config& c = h->cfg[inst];
+    const size_t nodes = (size_t)c.nx * c.ny;
+    const double* comp[3] = {ax, ay, az};
+    for (const double* a : comp)
+        if (a)
+            for (size_t k = 0; k < nodes; ++k)
+                if (!std::isfinite(a[k])) return fail(HLB_EINVAL, "acceleration field must be finite");
+    int l;
+    Group* G = group_of(h, inst, &l);
+    const bool on = ax || ay || az;
+    if (on && hlb::force_field_smem_bytes(G->dev, G->precision) > 160 * 1024)
+        return fail(HLB_EUNSUPPORTED, "velocity set too large for the force-field kernel's shared memory");
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    for (cudaStream_t s2 : h->group_stream) HLB_CUDA(cudaStreamSynchronize(s2));
+    if (on && !G->d_afield.p) {
+        if (cudaMalloc(&G->d_afield.p, (size_t)G->nnodes * 3 * sizeof(double)) != cudaSuccess) {
+            G->d_afield.p = nullptr;
+            return fail(HLB_ENOMEM, "cudaMalloc of the acceleration field failed");
+        }
+        HLB_CUDA(cudaMemset(G->d_afield.p, 0, (size_t)G->nnodes * 3 * sizeof(double)));
+        if (!h->once_field_prepared) {
+            HLB_CUDA(hlb::prepare_force_field());
+            h->once_field_prepared = true;
+        }
+    }
+    if (G->field_on.size() != G->members.size()) G->field_on.assign(G->members.size(), 0);
+    if (G->d_afield.p) {
+        std::vector<double> a(nodes * 3, 0.0);
+        for (int k = 0; k < 3; ++k)
+            if (comp[k])
+                for (size_t j = 0; j < nodes; ++j) a[3 * j + k] = comp[k][j];
+        HLB_CUDA(cudaMemcpy((double*)G->d_afield.p + 3 * (size_t)G->node_start[l], a.data(), a.size() * sizeof(double),
+                            cudaMemcpyHostToDevice));
+    }
+    G->field_on[l] = on;
+    G->has_field = std::any_of(G->field_on.begin(), G->field_on.end(), [](char f) { return f != 0; });
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     return HLB_OK;
 }

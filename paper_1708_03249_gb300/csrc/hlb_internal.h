@@ -129,4 +129,9 @@ void launch_moments(int precision, const GroupDev& g, const void* fs, double* n,
                     double* q, int node_base, cudaStream_t st);
 void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out,
                      cudaStream_t st);
+// Per-node acceleration field: fo += c_stage dt (-a(node) . K f) (hlb_kernels.cu).
+size_t force_field_smem_bytes(const GroupDev& g, int precision);
+cudaError_t prepare_force_field();
+void launch_force_field(int precision, const GroupDev& g, const double* afield, const void* fs, void* fo, int stage,
+                        cudaStream_t st);
 }  // namespace hlb

@@ -644,6 +644,74 @@ void launch_moments(int precision, const GroupDev& g, const void* fs, double* n,
     }
 }
 
+// ---------------------------------------------------------------------------
+// The force term of a per-node acceleration field (App. A, with a = a(node)):
+//   fo += c_s dt (-(a_x K_x f + a_y K_y f + a_z K_z f))   at every node,
+// f the stage input and c_s the weight of dt L in stage s of Eq. "eq:rk3"
+// (1, 1/4, 2/3).  The stage kernel has already written fo with the uniform
+// part of the force, so the two add up to the force of a_uniform + a(node).
+// One CTA takes nodes in turn: the node's values are staged in shared memory,
+// each thread forms the three contractions for its velocities.
+template <typename R>
+__global__ void __launch_bounds__(256) force_field_kernel(const GroupDev g, const double* __restrict__ afield,
+                                                          const R* __restrict__ fs, R* __restrict__ fo, int stage) {
+    extern __shared__ __align__(16) unsigned char ffsm[];
+    const int V = g.V, QX2 = g.QX2, VY = g.VY, VZ = g.VZ;
+    R* sK = reinterpret_cast<R*>(ffsm);                      // Kx [QX2^2], Ky [VY^2], Kz [VZ^2]
+    const int nK = QX2 * QX2 + VY * VY + VZ * VZ;
+    R* sf = sK + ((nK + 1) & ~1);                           // [V]: the node's values
+    const R* K = static_cast<const R*>(g.K);
+    for (int i = threadIdx.x; i < nK; i += blockDim.x) sK[i] = K[i];
+    const R* Kx = sK;
+    const R* Ky = Kx + QX2 * QX2;
+    const R* Kz = Ky + VY * VY;
+    const R cs = stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0));
+    for (int node = blockIdx.x; node < g.nnodes; node += gridDim.x) {
+        const double* a = afield + 3 * (size_t)node;
+        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+        const InstDev& I = g.inst[ii];
+        const size_t off = (size_t)I.f_off + (size_t)(node - I.node_off) * V;
+        __syncthreads();                                     // sf of the previous node is consumed
+        for (int v = threadIdx.x; v < V; v += blockDim.x) sf[v] = fs[off + v];
+        __syncthreads();
+        const R ax = (R)a[0], ay = (R)a[1], az = (R)a[2];
+        const R w = cs * (R)I.dt;
+        for (int v = threadIdx.x; v < V; v += blockDim.x) {
+            const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
+            const R* fib = sf + (size_t)(kz * VY + jy) * QX2;
+            R fx = R(0), fy = R(0), fz = R(0);
+            for (int i = 0; i < QX2; ++i) fx += Kx[ix * QX2 + i] * fib[i];
+            if (g.Qy)
+                for (int j = 0; j < VY; ++j) fy += Ky[jy * VY + j] * sf[(size_t)(kz * VY + j) * QX2 + ix];
+            if (g.Qz)
+                for (int k = 0; k < VZ; ++k) fz += Kz[kz * VZ + k] * sf[(size_t)(k * VY + jy) * QX2 + ix];
+            fo[off + v] -= w * (ax * fx + ay * fy + az * fz);
+        }
+    }
+}
+
+size_t force_field_smem_bytes(const GroupDev& g, int precision) {
+    const size_t es = precision == HLB_FP64_ ? 8 : 4;
+    const int nK = g.QX2 * g.QX2 + g.VY * g.VY + g.VZ * g.VZ;
+    return es * (((size_t)nK + 1) / 2 * 2 + (size_t)g.V);
+}
+
+cudaError_t prepare_force_field() {
+    cudaError_t e = cudaFuncSetAttribute(force_field_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(force_field_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+}
+
+void launch_force_field(int precision, const GroupDev& g, const double* afield, const void* fs, void* fo, int stage,
+                        cudaStream_t st) {
+    const size_t smem = force_field_smem_bytes(g, precision);
+    const int grid = g.nnodes < 152 * 16 ? g.nnodes : 152 * 16;
+    if (precision == HLB_FP64_)
+        force_field_kernel<double><<<grid, 256, smem, st>>>(g, afield, (const double*)fs, (double*)fo, stage);
+    else
+        force_field_kernel<float><<<grid, 256, smem, st>>>(g, afield, (const float*)fs, (float*)fo, stage);
+}
+
 void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out, cudaStream_t st) {
     const int block = 256;
     const int grid = (g.nnodes + 7) / 8 < 4096 ? (g.nnodes + 7) / 8 : 4096;

@@ -64,6 +64,7 @@ SIGNATURES = {
     "hlb_set_state": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_get_state_dev": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_set_state_dev": (C.c_int, [_P, _P, C.c_size_t]),
+    "hlb_set_force_field": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "hlb_prefetch_state": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_commit_state": (C.c_int, [_P]),
     "hlb_diag": (C.c_int, [_P, _D, _D]),
@@ -150,6 +151,22 @@ class Handle:
 
     def set_force(self, ax, ay=0.0, az=0.0, inst=-1):
         _check(lib().hlb_set_force(self._h, inst, ax, ay, az))
+
+    def set_force_field(self, inst, ax=None, ay=None, az=None):
+        """hlb_set_force_field: per-node accelerations (arrays of nx * ny, node order), None = zero."""
+        keep = []
+        c = self.cfgs[inst]
+        nodes = int(c["nx"]) * int(c.get("ny", 1))
+
+        def ptr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+            if a.size != nodes:
+                raise ValueError(f"acceleration field of instance {inst} needs {nodes} values, got {a.size}")
+            keep.append(a)
+            return a.ctypes.data_as(_D)
+        _check(lib().hlb_set_force_field(self._h, inst, ptr(ax), ptr(ay), ptr(az)))
 
     def set_Kn(self, Kn, inst=-1):
         _check(lib().hlb_set_Kn(self._h, inst, Kn))
