@@ -271,26 +271,44 @@ def h_equilibrium(Q: int, N: int, u, T) -> np.ndarray:
 class VelocitySet:
     """Direct product p_{ijk} = (p_x,i, p_y,j, p_z,k); f index order (kz, jy, ix).
 
-    Qx >= 1 half-range points per half (2 Qx values of p_x); Qy, Qz in
+    Qx >= 1 half-range points per half (2 Qx values of p_x), or with
+    x_full=True an even full-range order Qx (Qx values of p_x); Qy, Qz in
     {0, 2, 4, ...} (0 = axis absent, which contributes a single p = 0 with
-    weight 1 and no degree of freedom).  N* = equilibrium orders.
+    weight 1 and no degree of freedom).  N* = equilibrium orders.  QH is the
+    number of p_x > 0 values; they come first.
     """
 
-    def __init__(self, Qx: int, Qy: int = 0, Qz: int = 0, Nx=None, Ny=None, Nz=None):
+    def __init__(self, Qx: int, Qy: int = 0, Qz: int = 0, Nx=None, Ny=None, Nz=None, x_full: bool = False):
         if Qx < 1:
             raise ValueError("Qx >= 1")
-        for q in (Qy, Qz):
+        for q in (Qy, Qz) + ((Qx,) if x_full else ()):
             if q < 0 or q % 2:
                 raise ValueError("full-range orders must be 0 or even (Sec. IV.A.1)")
         self.Qx, self.Qy, self.Qz = Qx, Qy, Qz
+        self.x_full = bool(x_full)
         self.Nx = Qx - 1 if Nx is None or Nx < 0 else Nx
         self.Ny = (Qy - 1 if Ny is None or Ny < 0 else Ny) if Qy else 0
         self.Nz = (Qz - 1 if Nz is None or Nz < 0 else Nz) if Qz else 0
-        zx = to_f64(half_range_hermite(Qx)["z"])
-        wx = to_f64(half_range_hermite(Qx)["w"])
-        self.px = np.concatenate([zx, -zx])
-        self.wx = np.concatenate([wx, wx])
-        self.Kx = hh_force_matrix(Qx)
+        if x_full:
+            # the HLB(N; Q) models of Sec. V along p_x: full-range Gauss-Hermite
+            # of order Qx, K^H (Eq. "eq:H_Kk", no jump term) and Eq. "eq:H_gk";
+            # nodes ordered +z_1 < ... < +z_{Q/2}, then -z_1, ..., -z_{Q/2}, the
+            # layout of the half-range set (px > 0 first)
+            d = gauss_hermite(Qx)
+            z = to_f64(d["z"])                      # ascending
+            h = Qx // 2
+            self._xperm = np.concatenate([np.arange(h, Qx), np.arange(h - 1, -1, -1)])
+            self.px = z[self._xperm]
+            self.wx = to_f64(d["w"])[self._xperm]
+            self.Kx = h_force_matrix(Qx)[np.ix_(self._xperm, self._xperm)]
+            self.QH = h
+        else:
+            zx = to_f64(half_range_hermite(Qx)["z"])
+            wx = to_f64(half_range_hermite(Qx)["w"])
+            self.px = np.concatenate([zx, -zx])
+            self.wx = np.concatenate([wx, wx])
+            self.Kx = hh_force_matrix(Qx)
+            self.QH = Qx                            # velocities with p_x > 0
         if Qy:
             gy = gauss_hermite(Qy)
             self.py, self.wy = to_f64(gy["z"]), to_f64(gy["w"])
@@ -308,6 +326,8 @@ class VelocitySet:
         self.V = int(np.prod(self.shape))
 
     def g_x(self, u, T):
+        if self.x_full:
+            return h_equilibrium(self.Qx, self.Nx, u, T)[..., self._xperm]
         return hh_equilibrium(self.Qx, self.Nx, u, T)
 
     def g_y(self, u, T):

@@ -69,6 +69,9 @@ class Config:
     ax_field: object = None
     ay_field: object = None
     az_field: object = None
+    # 0: half-range Hermite along p_x (the HHLB models); 1: full-range
+    # Gauss-Hermite of order Qx (the HLB models the paper compares with, Sec. V)
+    x_basis: int = 0
     extra: dict = field(default_factory=dict)
 
 
@@ -178,7 +181,7 @@ class Solver:
         self.cfg = cfg
         if cfg.nx < 3:
             raise ValueError("nx >= 3 (quadratic wall extrapolation)")
-        self.vs = VelocitySet(cfg.Qx, cfg.Qy, cfg.Qz, cfg.Nx_eq, cfg.Ny_eq, cfg.Nz_eq)
+        self.vs = VelocitySet(cfg.Qx, cfg.Qy, cfg.Qz, cfg.Nx_eq, cfg.Ny_eq, cfg.Nz_eq, x_full=cfg.x_basis == 1)
         vs = self.vs
         self.edges, self.xc, self.dx = grid_x(cfg.nx, cfg.Lx, cfg.stretch_A)
         self.two_d = cfg.ny > 1
@@ -216,7 +219,7 @@ class Solver:
         """
         nx = f.shape[1]
         vs = self.vs
-        Q = vs.Qx
+        Q = vs.QH
         pos = slice(0, Q)          # p_x = +z_k (Eq. "eq:hh_pk")
         neg = slice(Q, 2 * Q)      # p_x = -z_k
         fe = np.full((f.shape[0], nx + 6) + f.shape[2:], np.nan)

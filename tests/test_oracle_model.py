@@ -181,6 +181,35 @@ def test_h_equilibrium_by_projection_integrals(Q, u, T):
     assert ((z - u) ** 2 * g).sum() == pytest.approx(T, rel=1e-13)
 
 
+@pytest.mark.parametrize("Qx", [4, 8])
+def test_full_range_x_set_layout_and_moments(Qx):
+    # The HLB set along p_x (x_full): the Gauss-Hermite nodes re-ordered as
+    # +z (ascending) then -z, with weights, K^H and g_x permuted the same way.
+    # Pinned by the node layout, the K^H identities in that order (mass:
+    # sum_k K_kk' = 0; momentum: sum_k p_k K_kk' = -1 per column, the discrete
+    # form of int p d_p f = -int f) and exact equilibrium moments.
+    from oracle.quadrature import gauss_hermite, to_f64
+    vs = VelocitySet(Qx, 4, 0, x_full=True)
+    z = np.sort(np.abs(to_f64(gauss_hermite(Qx)["z"])))[::2]
+    np.testing.assert_allclose(vs.px, np.concatenate([z, -z]), rtol=1e-14)
+    assert vs.QH == Qx // 2 and (vs.px[:Qx // 2] > 0).all()
+    np.testing.assert_allclose(vs.Kx.sum(axis=0), 0.0, atol=1e-12)
+    np.testing.assert_allclose((vs.px[:, None] * vs.Kx).sum(axis=0), -1.0, atol=1e-12)
+    n, ux, uy, T = 1.1, 0.3, -0.2, 0.9
+    f = vs.equilibrium(np.float64(n), ux, uy, 0.0, np.float64(T))
+    px, py = vs.px[None, None, :], vs.py[None, :, None]
+    assert f.sum() == pytest.approx(n, rel=1e-13)
+    assert (f * px).sum() / n == pytest.approx(ux, abs=1e-13)
+    assert (f * py).sum() / n == pytest.approx(uy, abs=1e-13)
+    assert (f * ((px - ux) ** 2 + (py - uy) ** 2)).sum() / (2 * n) == pytest.approx(T, rel=1e-13)
+    # the permuted g_x is the full-range equilibrium at the permuted nodes
+    from oracle.model import h_equilibrium
+    g = h_equilibrium(Qx, Qx - 1, ux, T)
+    zz = to_f64(gauss_hermite(Qx)["z"])
+    for k, p in enumerate(vs.px):
+        assert vs.g_x(ux, T)[k] == pytest.approx(g[int(np.argmin(np.abs(zz - p)))], rel=1e-14)
+
+
 def test_direct_product_equilibrium_moments():
     # App. A: feq = n g_x g_y g_z reproduces n, u and T = sum |p-u|^2 f/(D n).
     vs = VelocitySet(4, 4, 4)   # N = Q - 1 >= 2 on every axis

@@ -126,6 +126,67 @@ def test_homogeneous_force_and_bgk_closed_form(Qx, Qy, Qz, ax, ay, az):
     np.testing.assert_allclose(T, T0, rtol=1e-12)
 
 
+@pytest.mark.parametrize("Qx,Qy,Qz", [(4, 0, 0), (8, 4, 0), (6, 4, 4)])
+def test_homogeneous_force_closed_form_full_range_x(Qx, Qy, Qz):
+    # The same closed form for the HLB set along p_x (K^H, no jump term).
+    ax, ay, az = -0.25, 0.15, -0.1
+    s = Solver(Config(Qx=Qx, Qy=Qy, Qz=Qz, nx=3, ax=ax, ay=ay, az=az, Kn=0.3, dt=0.01, x_basis=1))
+    s.init_equilibrium(1.1, 0.1, -0.05, 0.95)
+    rng = np.random.default_rng(4)
+    s.f = s.f * (1 + 0.1 * rng.uniform(-1, 1, s.f.shape))
+    n0, u0, T0, _ = s.moments()
+    for _ in range(50):
+        f = s.f
+        f1 = f + s.dt * s.source(f)
+        f2 = 0.75 * f + 0.25 * f1 + 0.25 * s.dt * s.source(f1)
+        s.f = f / 3 + 2 / 3 * f2 + 2 / 3 * s.dt * s.source(f2)
+    a = np.array([ax, ay if Qy else 0.0, az if Qz else 0.0])
+    n, u, T, _ = s.moments()
+    np.testing.assert_allclose(n, n0, rtol=1e-13)
+    np.testing.assert_allclose(u, u0 + a * 50 * s.dt, atol=1e-13)
+    np.testing.assert_allclose(T, T0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("Qx,Qy", [(4, 0), (8, 4)])
+def test_free_molecular_discrete_closed_form_full_range_x(Qx, Qy):
+    # HLB along p_x between walls at T_L != T_R, g = 0, Kn = inf: the steady
+    # state is f = n_L g_L (p_x > 0), n_R g_R (p_x < 0) at every node, with the
+    # zero-flux condition n_L J(T_L) = n_R J(T_R), J(T) = sum_{p_x > 0} p_x g_x(0, T)
+    # (the Gauss-Hermite half sums are not the continuous half-range moments,
+    # which is why HLB is inexact at walls, Sec. V).  So n = n_L A_L + n_R A_R with
+    # A(T) = sum_{p_x > 0} g_x(0, T), uniform in x.
+    TL, TR = 0.8, 1.7
+    s = Solver(Config(Qx=Qx, Qy=Qy, nx=12, advection="upwind2", T_left=TL, T_right=TR, x_basis=1))
+    s.init_equilibrium()
+    for _ in range(200):
+        fo = s.f.copy()
+        s.step(100)
+        if s.residual(fo, s.f) < 1e-13:
+            break
+    vs = s.vs
+    h = vs.QH
+    J = lambda T: float((vs.px[:h] * vs.g_x(0.0, T)[:h]).sum())
+    A = lambda T: float(vs.g_x(0.0, T)[:h].sum())
+    nl, nr = s.last_wall_density
+    np.testing.assert_allclose(nl * J(TL), nr * J(TR), rtol=1e-11)
+    n, u, T, q = s.moments()
+    np.testing.assert_allclose(n, nl[0] * A(TL) + nr[0] * A(TR), rtol=1e-11)
+    np.testing.assert_allclose(u, 0.0, atol=1e-11)
+
+
+def test_barometric_interior_residual_full_range_x():
+    # f = exp(-g x) g(0, 1) is the steady state for the HLB set too (K^H maps
+    # the Maxwellian at rest exactly); interior residual O(dx^2) for upwind2.
+    g = 0.5
+    res = []
+    for nx in (32, 64, 128):
+        s = Solver(Config(Qx=8, Qy=4, nx=nx, advection="upwind2", ax=-g, Kn=0.3, x_basis=1))
+        n = np.exp(-g * s.xc)
+        s.f = n[None, :, None, None, None] * s.vs.equilibrium(np.float64(1.0), 0.0, 0.0, 0.0, np.float64(1.0))[None, None]
+        res.append(np.abs(s.rhs(s.f)[:, 5:-5]).max())
+    assert res[0] / res[1] > 3.5 and res[1] / res[2] > 3.5
+
+
 @pytest.mark.parametrize("Qx,Qy,Qz", [(4, 0, 0), (4, 4, 0), (3, 4, 4)])
 def test_homogeneous_force_field_closed_form(Qx, Qy, Qz):
     # A per-node acceleration field on top of the uniform one: without
