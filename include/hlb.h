@@ -69,6 +69,10 @@ typedef enum {
 
 enum { HLB_UPWIND2 = 0, HLB_WENO5 = 1 };
 enum { HLB_FP64 = 0, HLB_FP32 = 1 };
+/* Quadrature along p_x: the half-range Hermite of Sec. IV.B (HHLB models,
+ * 2 Qx values) or the full-range Gauss-Hermite of Sec. IV.A (HLB models, Qx
+ * values, Qx even), the model the paper compares against in Sec. V. */
+enum { HLB_X_HALF_RANGE = 0, HLB_X_FULL_RANGE = 1 };
 
 /* One channel instance.  Field order and types are part of the ABI. */
 typedef struct {
@@ -86,6 +90,9 @@ typedef struct {
     double T_left, T_right;  /* wall temperatures (> 0) at x = 0 and x = Lx               */
     double ax, ay, az;   /* acceleration a = F/m; gravity g along -x is ax = -g            */
     double Kn;           /* Knudsen number > 0; +INFINITY = collisionless (no BGK term)   */
+    int x_basis;         /* HLB_X_HALF_RANGE (0, default) or HLB_X_FULL_RANGE: then Qx is
+                            the even full-range order and p_x holds Qx values, ordered
+                            +z_1 < ... < +z_{Qx/2}, then -z_1, ..., -z_{Qx/2}            */
 } hlb_config;
 
 /* Create a handle for `ninst` independent instances (ninst >= 1).  Instances

@@ -45,6 +45,7 @@ struct PinnedBuf {                           // page-locked host memory
 struct Group {
     int precision = HLB_FP32, adv = HLB_WENO5;
     int Qx = 0, Qy = 0, Qz = 0, Nx = 0, Ny = 0, Nz = 0;
+    bool x_full = false;                     // p_x on the full-range Gauss-Hermite axis
     hlb::AxisTables tx, ty, tz;
     int V = 0, QX2 = 0, VY = 1, VZ = 1;
     size_t esize = 4;
@@ -119,6 +120,9 @@ namespace {
 std::string check_config(const hlb_config& c, int i) {
     auto bad = [&](const char* what) { return "instance " + std::to_string(i) + ": " + what; };
     if (c.Qx < 1 || c.Qx > hlb::kMaxQ) return bad("Qx must be in [1, 32]");
+    if (c.x_basis != HLB_X_HALF_RANGE && c.x_basis != HLB_X_FULL_RANGE)
+        return bad("x_basis must be HLB_X_HALF_RANGE or HLB_X_FULL_RANGE");
+    if (c.x_basis == HLB_X_FULL_RANGE && (c.Qx < 2 || c.Qx % 2)) return bad("full-range Qx must be even in [2, 32]");
     for (int q : {c.Qy, c.Qz})
         if (q < 0 || q > hlb::kMaxQ || (q % 2)) return bad("Qy, Qz must be 0 or even in [2, 32]");
     if (c.Nx_eq >= c.Qx || c.Nx_eq < -1) return bad("Nx_eq must be -1 or in [0, Qx - 1]");
@@ -205,7 +209,7 @@ constexpr unsigned long long kDefaultWaitNs = 1000000000ull;   // 1 s
 
 void fill_dev(Group& G) {
     hlb::GroupDev& d = G.dev;
-    d.V = G.V; d.QX2 = G.QX2; d.VY = G.VY; d.VZ = G.VZ; d.Qx = G.Qx;
+    d.V = G.V; d.QX2 = G.QX2; d.VY = G.VY; d.VZ = G.VZ; d.Qx = G.tx.Q; d.x_full = G.x_full ? 1 : 0;
     d.Nx = G.Nx; d.Ny = G.Qy ? G.Ny : 0; d.Nz = G.Qz ? G.Nz : 0;
     d.Qy = G.Qy; d.Qz = G.Qz;
     d.D = 1 + (G.Qy > 0) + (G.Qz > 0);
@@ -241,13 +245,14 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     G.Nx = c0.Nx_eq < 0 ? c0.Qx - 1 : c0.Nx_eq;
     G.Ny = c0.Qy ? (c0.Ny_eq < 0 ? c0.Qy - 1 : c0.Ny_eq) : 0;
     G.Nz = c0.Qz ? (c0.Nz_eq < 0 ? c0.Qz - 1 : c0.Nz_eq) : 0;
-    std::string e = hlb::build_half_axis(G.Qx, G.Nx, G.tx);
+    G.x_full = c0.x_basis == HLB_X_FULL_RANGE;
+    std::string e = G.x_full ? hlb::build_full_x_axis(G.Qx, G.Nx, G.tx) : hlb::build_half_axis(G.Qx, G.Nx, G.tx);
     if (!e.empty()) return fail(HLB_EINVAL, e);
     if (G.Qy) { e = hlb::build_full_axis(G.Qy, G.Ny, G.ty); if (!e.empty()) return fail(HLB_EINVAL, e); }
     else hlb::absent_axis(G.ty);
     if (G.Qz) { e = hlb::build_full_axis(G.Qz, G.Nz, G.tz); if (!e.empty()) return fail(HLB_EINVAL, e); }
     else hlb::absent_axis(G.tz);
-    G.QX2 = 2 * G.Qx; G.VY = G.ty.count; G.VZ = G.tz.count;
+    G.QX2 = G.tx.count; G.VY = G.ty.count; G.VZ = G.tz.count;
     G.V = G.QX2 * G.VY * G.VZ;
     G.esize = G.precision == HLB_FP64 ? 8 : 4;
 
@@ -310,6 +315,7 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     rec.insert(rec.end(), G.tx.rc.begin(), G.tx.rc.end());
     rec.insert(rec.end(), G.tx.h0.begin(), G.tx.h0.end());
     for (double a : G.tx.ra) rec.push_back(1.0 / a);
+    if (G.x_full) rec.assign(5 * (size_t)G.Nx + 1, 0.0);     // the full-range x roles read no recurrence table
     std::vector<double> invdx(G.dx_all.size()), wscale(G.V);
     for (size_t i = 0; i < invdx.size(); ++i) invdx[i] = 1.0 / G.dx_all[i];
     for (int k = 0; k < G.VZ; ++k)
@@ -587,14 +593,14 @@ hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_h
         h->own_stream = true;
     }
     // group by velocity model
-    std::map<std::tuple<int, int, int, int, int, int, int>, int> key2g;
+    std::map<std::tuple<int, int, int, int, int, int, int, int>, int> key2g;
     h->inst_group.resize(ninst);
     h->inst_local.resize(ninst);
     for (int i = 0; i < ninst; ++i) {
         const hlb_config& c = cfg[i];
         auto key = std::make_tuple(c.Qx, c.Qy, c.Qz, c.Nx_eq < 0 ? c.Qx - 1 : c.Nx_eq,
                                    c.Qy ? (c.Ny_eq < 0 ? c.Qy - 1 : c.Ny_eq) : 0,
-                                   c.Qz ? (c.Nz_eq < 0 ? c.Qz - 1 : c.Nz_eq) : 0, c.advection);
+                                   c.Qz ? (c.Nz_eq < 0 ? c.Qz - 1 : c.Nz_eq) : 0, c.advection, c.x_basis);
         auto it = key2g.find(key);
         int gi;
         if (it == key2g.end()) {

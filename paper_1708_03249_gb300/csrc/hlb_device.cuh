@@ -344,7 +344,14 @@ __device__ __forceinline__ T warp_sum(T v) {
 __device__ inline void node_coefficients(const GroupDev& g, int r, double ux, double uy, double uz,
                                   double T, const double* rec, double* coef) {
     const int Nx = g.Nx;
-    if (r < 2) {
+    if (r < 2 && g.x_full) {
+        // full-range p_x (Eq. "eq:H_gk"): G_l(+-u_x) for the +z and -z rows
+        const double u = r ? -ux : ux;
+        double* G = coef + r * (Nx + 1);
+        G[0] = 1.0;
+        if (Nx >= 1) G[1] = u;
+        for (int l = 1; l < Nx; ++l) G[l + 1] = u * G[l] + l * (T - 1.0) * G[l - 1];
+    } else if (r < 2) {
         const double* ra = rec;
         (void)ra;
         const double* rb = rec + Nx;
@@ -542,7 +549,14 @@ __device__ inline void node_coefficients_df(const GroupDev& g, int r, const Node
     const int Nx = g.Nx;
     // same slots as node_coefficients: G^+ | G^- | G_y | G_z
     float2* G = coef + (r < 2 ? r * (Nx + 1) : 2 * (Nx + 1) + (r == 2 ? 0 : g.Ny + 1));
-    if (r < 2) {
+    if (r < 2 && g.x_full) {
+        // full-range p_x (Eq. "eq:H_gk"): G_l(+-u_x) for the +z and -z rows
+        const float2 u = r ? make_float2(-in.ux.x, -in.ux.y) : in.ux;
+        G[0] = make_float2(1.0f, 0.0f);
+        if (Nx >= 1) G[1] = u;
+        for (int l = 1; l < Nx; ++l)
+            G[l + 1] = df_add(df_mul(u, G[l]), df_mul(df_mul(make_float2((float)l, 0.0f), in.Tm1), G[l - 1]));
+    } else if (r < 2) {
         const float2* ra = recf;
         const float2* rb = recf + Nx;
         const float2* rc = recf + 2 * Nx;

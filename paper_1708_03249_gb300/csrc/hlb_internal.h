@@ -18,8 +18,10 @@ constexpr int kMaxN = kMaxQ;       // largest equilibrium order + 1
 
 // One momentum axis of the direct-product velocity set (App. A).
 struct AxisTables {
-    int Q = 0;                       // quadrature order (per half for the half-range axis)
+    int Q = 0;                       // quadrature order (per half for the half-range axis and
+                                     // for the mirrored full-range p_x axis)
     bool half = false;               // half-range Hermite (p_x) or full-range Gauss-Hermite
+    bool mirror = false;             // full-range p_x axis laid out +z then -z (two roles, +-u)
     int count = 1;                   // velocities on the axis: 2Q, Q, or 1 if absent
     int N = 0;                       // equilibrium order
     std::vector<double> p, w;        // [count]
@@ -35,6 +37,11 @@ struct AxisTables {
 // Returns "" on success or an error message.
 std::string build_half_axis(int Q, int N, AxisTables& out);
 std::string build_full_axis(int Q, int N, AxisTables& out);
+// Full-range Gauss-Hermite of even order Q along p_x, in the layout of the
+// half-range axis: p = (+z_1 .. +z_{Q/2}, -z_1 .. -z_{Q/2}) with z ascending,
+// w and K^H permuted alike; out.Q = Q/2 and T holds the rows of the +z nodes
+// only (g at -z_k with u equals g at +z_k with -u).
+std::string build_full_x_axis(int Q, int N, AxisTables& out);
 void absent_axis(AxisTables& out);
 
 // g(u, T) on the axis (count values), FP64, by the same recurrences the
@@ -87,6 +94,8 @@ struct GroupDev {
     const float2* recf;      // double-float (hi, lo) copies of rec
     const float2* Tf;        // double-float (hi, lo) copies of Tx, Ty, Tz
     int use_df;              // FP32 groups with Nx <= 11: equilibrium in double-float
+    int x_full;              // p_x on the mirrored full-range axis: the x roles use the
+                             // full-range recurrence with +-u_x (rec unused)
     const double* dx;        // FP64 x-cell widths, concatenated per instance
     const void* gw;          // R: wall Maxwellians
     double* nw;              // FP64 [nrows][2] emitted densities

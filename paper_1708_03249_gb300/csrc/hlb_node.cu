@@ -402,7 +402,10 @@ __global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const fl
             float2 G[NM];
 #pragma unroll 1
             for (int r = 0; r < 2; ++r) {                    // n g_x, p_x > 0 then p_x < 0
-                half_range_G_df<NM>(r, in, sRec, Nx, G);
+                if (g.x_full)                                 // full-range p_x: G_l(+-u_x)
+                    full_range_G_df<NM>(r ? make_float2(-in.ux.x, -in.ux.y) : in.ux, in.Tm1, Nx, G);
+                else
+                    half_range_G_df<NM>(r, in, sRec, Nx, G);
                 lines_dot2<NM>(line + r * Qx, sPx, Qx, G, Nx, &in.n);
             }
             if (g.Qy) {

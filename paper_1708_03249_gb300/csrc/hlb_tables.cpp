@@ -330,6 +330,36 @@ std::string build_full_axis(int Q, int N, AxisTables& out) {
     return "";
 }
 
+std::string build_full_x_axis(int Q, int N, AxisTables& out) {
+    AxisTables full;
+    std::string e = build_full_axis(Q, N, full);
+    if (!e.empty()) return e;
+    const int h = Q / 2;
+    std::vector<int> perm(Q);
+    for (int i = 0; i < h; ++i) {
+        perm[i] = h + i;            // +z_{i+1}
+        perm[h + i] = h - 1 - i;    // -z_{i+1}
+    }
+    out = AxisTables();
+    out.Q = h;
+    out.half = false;
+    out.mirror = true;
+    out.count = Q;
+    out.N = N;
+    out.p.resize(Q);
+    out.w.resize(Q);
+    out.K.assign((size_t)Q * Q, 0.0);
+    for (int i = 0; i < Q; ++i) {
+        out.p[i] = full.p[perm[i]];
+        out.w[i] = full.w[perm[i]];
+        for (int j = 0; j < Q; ++j) out.K[(size_t)i * Q + j] = full.K[(size_t)perm[i] * Q + perm[j]];
+    }
+    out.T.assign((size_t)h * (N + 1), 0.0);
+    for (int k = 0; k < h; ++k)
+        for (int l = 0; l <= N; ++l) out.T[(size_t)k * (N + 1) + l] = full.T[(size_t)perm[k] * (N + 1) + l];
+    return "";
+}
+
 void axis_equilibrium(const AxisTables& ax, double u, double T, double* g) {
     if (ax.count == 1 && !ax.half && ax.Q == 0) {
         g[0] = 1.0;
@@ -356,6 +386,19 @@ void axis_equilibrium(const AxisTables& ax, double u, double T, double* g) {
                 double acc = 0.0;
                 for (int l = 0; l <= N; ++l) acc += ax.T[k * (N + 1) + l] * G[l];
                 g[sgn * Q + k] = acc;
+            }
+        }
+    } else if (ax.mirror) {
+        // rows of the +z nodes; the -z nodes with -u (He_l(-z) = (-1)^l He_l(z))
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const double us = sgn ? -u : u;
+            G[0] = 1.0;
+            if (N >= 1) G[1] = us;
+            for (int l = 1; l < N; ++l) G[l + 1] = us * G[l] + l * (T - 1.0) * G[l - 1];
+            for (int k = 0; k < ax.Q; ++k) {
+                double acc = 0.0;
+                for (int l = 0; l <= N; ++l) acc += ax.T[k * (N + 1) + l] * G[l];
+                g[sgn * ax.Q + k] = acc;
             }
         }
     } else {

@@ -32,7 +32,7 @@ class HlbConfig(C.Structure):
                 ("cfl", C.c_double), ("dt", C.c_double),
                 ("T_left", C.c_double), ("T_right", C.c_double),
                 ("ax", C.c_double), ("ay", C.c_double), ("az", C.c_double),
-                ("Kn", C.c_double)]
+                ("Kn", C.c_double), ("x_basis", C.c_int)]
 
 
 class HlbError(RuntimeError):
@@ -108,7 +108,7 @@ def _dptr(a):
 def make_config(d: dict) -> HlbConfig:
     c = HlbConfig()
     for name, _ in HlbConfig._fields_:
-        setattr(c, name, d[name])
+        setattr(c, name, d.get(name, 0) if name == "x_basis" else d[name])
     return c
 
 

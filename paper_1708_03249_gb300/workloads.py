@@ -19,12 +19,13 @@ import numpy as np
 
 UPWIND2, WENO5 = 0, 1
 FP64, FP32 = 0, 1
+X_HALF, X_FULL = 0, 1      # quadrature along p_x: half-range Hermite (HHLB) or Gauss-Hermite (HLB)
 
 # Every workload is a plain dict of hlb_config fields (see include/hlb.h).
 _BASE = dict(Qx=4, Qy=0, Qz=0, Nx_eq=-1, Ny_eq=-1, Nz_eq=-1, nx=64, ny=1,
              Lx=1.0, Ly=1.0, stretch_A=0.0, advection=WENO5, precision=FP32,
              cfl=0.5, dt=0.0, T_left=1.0, T_right=1.0, ax=0.0, ay=0.0, az=0.0,
-             Kn=math.inf)
+             Kn=math.inf, x_basis=X_HALF)
 
 
 def make(**kw) -> dict:

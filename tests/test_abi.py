@@ -36,6 +36,7 @@ def test_version(hlb_lib):
 @pytest.mark.parametrize("field,value", [("Qx", 0), ("Qx", 33), ("Qy", 3), ("Qz", -2), ("nx", 5),
                                           ("ny", 2), ("Kn", 0.0), ("T_left", -1.0), ("stretch_A", 1.0),
                                           ("advection", 7), ("precision", 3), ("Nx_eq", 4), ("Lx", 0.0),
+                                          ("x_basis", 2),
                                           ("ax", math.nan)])
 def test_invalid_config_is_rejected(hlb_lib, field, value):
     cfg = W.make(Qx=4, Qy=4, nx=16, Kn=1.0)
@@ -44,6 +45,13 @@ def test_invalid_config_is_rejected(hlb_lib, field, value):
         hlb.Handle(cfg)
     assert e.value.status == hlb.HLB_EINVAL
     assert "instance 0" in str(e.value)
+
+
+def test_odd_full_range_x_order_is_rejected(hlb_lib):
+    cfg = W.make(Qx=3, Qy=4, nx=16, Kn=1.0, x_basis=W.X_FULL)
+    with pytest.raises(hlb.HlbError) as e:
+        hlb.Handle(cfg)
+    assert e.value.status == hlb.HLB_EINVAL
 
 
 def test_mixed_precision_batch_is_rejected(hlb_lib):

@@ -233,6 +233,21 @@ def test_fp32_1d_q16_tensor_core_force(adv):
     _check_fp32(got, mom, refs)
 
 
+@pytest.mark.parametrize("Qx,Qy,ny,prec,adv", [(16, 8, 1, W.FP32, W.WENO5), (8, 4, 5, W.FP32, W.WENO5),
+                                                (32, 16, 1, W.FP32, W.UPWIND2), (8, 4, 1, W.FP64, W.UPWIND2)])
+def test_full_range_x_models(Qx, Qy, ny, prec, adv):
+    # HLB(N; Q) along p_x (Gauss-Hermite of order Qx, K^H without the jump
+    # term): the line kernel (16 x 8, and 32 x 16 with the tensor-core force
+    # term), the pair kernel (8 x 4) and the FP64 kernel, against the oracle
+    cfg = W.make(Qx=Qx, Qy=Qy, nx=23, ny=ny, Ly=0.25, advection=adv, precision=prec, T_left=0.8, T_right=1.4,
+                 Kn=0.4, x_basis=W.X_FULL, **W.gravity(0.5, 30.0))
+    got, mom, N, refs = run_pair(cfg, 6, init=(1.0, 0.05, 0.0, 1.0))
+    if prec == W.FP64:
+        _check_fp64(got, refs, 1e-10)
+    else:
+        _check_fp32(got, mom, refs)
+
+
 def test_fp32_batched_mixed_instances():
     insts = W.batched_instances(6)
     insts = [W.scaled(c, nx=min(c["nx"], 40)) for c in insts]
