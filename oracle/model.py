@@ -15,8 +15,15 @@ throughout, so momenta and velocities coincide (p_k = z_k).
   G_l = sum_s l!/(2^s s! (l-2s)!) (T-1)^s u^{l-2s}.  The printed exponent of
   (T - 1) is "2"; it is read as s (the only reading with G_l(u=0, T=1) =
   delta_{l0}, i.e. g_k = w_k at rest and unit temperature).
-* ``VelocitySet``: the mixed quadrature of App. A: half-range along p_x,
-  full-range along p_y and p_z (an axis with Q = 0 is absent).
+* ``hl_force_matrix(Q)``: K^L_{kk'} of Eq. "eq:hh_Kk_L", the half-range
+  Gauss-Laguerre counterpart (same index order).
+* ``hl_equilibrium(Q, N, u, T)``: the half-range projection of the
+  Maxwellian on the Laguerre basis, g_k = w_k sum_{l<=N} L_l(z_k) G_l^{+-} with
+  G_l^{+-} = int_0^inf g(+-p) L_l(p) dp written out from the half-range moments
+  M_s^{+-} = int_0^inf p^s g(+-p) dp.
+* ``VelocitySet``: the mixed quadrature of App. A: half-range along p_x
+  (Hermite, Laguerre, or full-range Gauss-Hermite), full-range along p_y and
+  p_z (an axis with Q = 0 is absent).
 """
 from __future__ import annotations
 
@@ -27,7 +34,7 @@ from functools import lru_cache
 import numpy as np
 from scipy.special import erf as _erf
 
-from .quadrature import (PREC, _ctx, dec_inv_sqrt_2pi, dec_pi, gauss_hermite,
+from .quadrature import (PREC, _ctx, dec_inv_sqrt_2pi, dec_pi, gauss_hermite, gauss_laguerre_half,
                          half_range_hermite, poly_eval, to_f64)
 
 
@@ -75,6 +82,67 @@ def hh_force_matrix(Q: int) -> np.ndarray:
 # full-range Hermite: K^H  (Eq. "eq:H_Kk")
 # ----------------------------------------------------------------------------
 @lru_cache(maxsize=None)
+# ----------------------------------------------------------------------------
+# half-range Gauss-Laguerre: K^L  (Eq. "eq:hh_Kk_L")
+# ----------------------------------------------------------------------------
+@lru_cache(maxsize=None)
+def hl_force_matrix(Q: int) -> np.ndarray:
+    d = gauss_laguerre_half(Q)
+    L, z, w = d["L"], d["z"], d["w"]
+    with _ctx():
+        Lv = [[poly_eval(L[l], zk) for l in range(Q)] for zk in z]       # L_l(z_k), l <= Q-1
+        Phi0 = [sum(Lv[k]) for k in range(Q)]                            # sum_{s<Q} L_s(z_k)
+        # same-half bracket: B[k][k'] = sum_{l=0}^{Q-2} L_l(z_k') sum_{s=l+1}^{Q-1} L_s(z_k)
+        K = np.zeros((2 * Q, 2 * Q))
+        for k in range(2 * Q):
+            kk, sk = k % Q, (1 if k < Q else -1)
+            for kp in range(2 * Q):
+                kkp, skp = kp % Q, (1 if kp < Q else -1)
+                acc = Decimal(0)
+                if sk == skp:
+                    for l in range(Q - 1):
+                        acc += Lv[kkp][l] * sum(Lv[kk][s] for s in range(l + 1, Q))
+                acc -= Phi0[kk] * Phi0[kkp] / 2
+                K[k, kp] = float(w[kk] * sk * acc)
+    return K
+
+
+def _hl_moments_dec(N: int, u: float, T: float, sgn: int):
+    """M_s = int_0^inf p^s g(sgn p) dp, s <= N, for g = exp(-(p-u)^2/(2T))/sqrt(2 pi T)
+    (Decimal): M_0 = (1 + erf(sgn u/sqrt(2T)))/2, M_1 = sgn u M_0 + T g(0),
+    M_{s+1} = sgn u M_s + s T M_{s-1} (integration by parts of (p - sgn u) g)."""
+    with _ctx():
+        uD, TD = Decimal(float(u)) * sgn, Decimal(float(T))
+        g0 = (-(uD * uD) / (2 * TD)).exp() / (2 * dec_pi() * TD).sqrt()
+        M = [(1 + _dec_erf(uD / (2 * TD).sqrt())) / 2]
+        if N >= 1:
+            M.append(uD * M[0] + TD * g0)
+        for s_ in range(1, N):
+            M.append(uD * M[s_] + s_ * TD * M[s_ - 1])
+    return M
+
+
+def hl_equilibrium(Q: int, N: int, u, T) -> np.ndarray:
+    """Half-range Gauss-Laguerre projection of the Maxwellian, shape u.shape + (2Q,)
+    (entries 0..Q-1 at +z_k, Q..2Q-1 at -z_k), n = 1; each node in Decimal."""
+    if not 0 <= N < Q:
+        raise ValueError("0 <= N < Q")
+    d = gauss_laguerre_half(Q)
+    L, z, w = d["L"], d["z"], d["w"]
+    u = np.asarray(u, dtype=np.float64)
+    T = np.broadcast_to(np.asarray(T, dtype=np.float64), u.shape)
+    out = np.zeros(u.shape + (2 * Q,))
+    with _ctx():
+        Lz = [[poly_eval(L[l], zk) for l in range(N + 1)] for zk in z]
+        for ix in np.ndindex(u.shape):
+            for half, sgn in ((0, 1), (1, -1)):
+                M = _hl_moments_dec(N, float(u[ix]), float(T[ix]), sgn)
+                G = [sum(L[l][s_] * M[s_] for s_ in range(l + 1)) for l in range(N + 1)]
+                for k in range(Q):
+                    out[ix + (half * Q + k,)] = float(w[k] * sum(Lz[k][l] * G[l] for l in range(N + 1)))
+    return out
+
+
 def h_force_matrix(Q: int) -> np.ndarray:
     d = gauss_hermite(Q)
     z, w, He = d["z"], d["w"], d["He"]
@@ -278,7 +346,8 @@ class VelocitySet:
     number of p_x > 0 values; they come first.
     """
 
-    def __init__(self, Qx: int, Qy: int = 0, Qz: int = 0, Nx=None, Ny=None, Nz=None, x_full: bool = False):
+    def __init__(self, Qx: int, Qy: int = 0, Qz: int = 0, Nx=None, Ny=None, Nz=None, x_full: bool = False,
+                 x_laguerre: bool = False):
         if Qx < 1:
             raise ValueError("Qx >= 1")
         for q in (Qy, Qz) + ((Qx,) if x_full else ()):
@@ -286,6 +355,7 @@ class VelocitySet:
                 raise ValueError("full-range orders must be 0 or even (Sec. IV.A.1)")
         self.Qx, self.Qy, self.Qz = Qx, Qy, Qz
         self.x_full = bool(x_full)
+        self.x_laguerre = bool(x_laguerre) and not x_full
         self.Nx = Qx - 1 if Nx is None or Nx < 0 else Nx
         self.Ny = (Qy - 1 if Ny is None or Ny < 0 else Ny) if Qy else 0
         self.Nz = (Qz - 1 if Nz is None or Nz < 0 else Nz) if Qz else 0
@@ -302,6 +372,14 @@ class VelocitySet:
             self.wx = to_f64(d["w"])[self._xperm]
             self.Kx = h_force_matrix(Qx)[np.ix_(self._xperm, self._xperm)]
             self.QH = h
+        elif x_laguerre:
+            # the half-range Gauss-Laguerre family (Sec. IV.B, Eq. "eq:hh_Kk_L")
+            d = gauss_laguerre_half(Qx)
+            zx, wx = to_f64(d["z"]), to_f64(d["w"])
+            self.px = np.concatenate([zx, -zx])
+            self.wx = np.concatenate([wx, wx])
+            self.Kx = hl_force_matrix(Qx)
+            self.QH = Qx
         else:
             zx = to_f64(half_range_hermite(Qx)["z"])
             wx = to_f64(half_range_hermite(Qx)["w"])
@@ -328,6 +406,8 @@ class VelocitySet:
     def g_x(self, u, T):
         if self.x_full:
             return h_equilibrium(self.Qx, self.Nx, u, T)[..., self._xperm]
+        if self.x_laguerre:
+            return hl_equilibrium(self.Qx, self.Nx, u, T)
         return hh_equilibrium(self.Qx, self.Nx, u, T)
 
     def g_y(self, u, T):

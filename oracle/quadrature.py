@@ -15,6 +15,9 @@ takes the Q (positive) roots z_k of h_Q, and the weights of Eq. "eq:wk_half":
 with a_Q = h_{Q+1,Q+1} / h_{Q,Q} (Eq. "eq:a_def").  The full velocity set is
 p_k = z_k, p_{k+Q} = -z_k (Eq. "eq:hh_pk", p_0 = 1).
 
+Half-range Gauss-Laguerre (Sec. IV.B, weight exp(-z) on [0, inf)): roots of
+L_Q, weights z_k / ((Q+1)^2 L_{Q+1}(z_k)^2) (Eq. "eq:wk_half").
+
 Full-range Gauss-Hermite (Sec. IV.A.1): roots of the probabilists' Hermite
 polynomial He_Q (Eq. "eq:H_ortho" normalisation <He_l, He_l'> = l! delta),
 weights w_k = Q! / He_{Q+1}(z_k)^2 (Eq. "eq:H_wk"), summing to 1.
@@ -206,6 +209,35 @@ def gauss_hermite(Q: int):
         fac = Decimal(math.factorial(Q))
         w = [fac / poly_eval(cQ1, zk) ** 2 for zk in z]
     return {"z": z, "w": w, "He": He}
+
+
+def _laguerre_coeffs(M: int):
+    """Exact coefficients (Fractions, ascending) of the Laguerre polynomials
+    L_0..L_{M-1}: L_n(z) = sum_s (-1)^s C(n, s) z^s / s!, orthonormal on
+    [0, inf) with weight exp(-z)."""
+    from fractions import Fraction
+    return [[Fraction((-1) ** s * math.comb(n, s), math.factorial(s)) for s in range(n + 1)] for n in range(M)]
+
+
+@functools.lru_cache(maxsize=None)
+def gauss_laguerre_half(Q: int):
+    """Half-range Gauss-Laguerre quadrature of order Q (Decimal data), the
+    first half-range family of Sec. IV.B (weight omega(z) = exp(-z), gamma = 1).
+
+    Roots z_k of L_Q, Newton-polished in Decimal from numpy's laggauss nodes;
+    weights w_k = z_k / ((Q + 1)^2 L_{Q+1}(z_k)^2) (the Gauss-Laguerre form of
+    Eq. "eq:wk_half").  Returns dict(z=..., w=..., L=coefficient lists for
+    l <= Q + 1 as Decimals).
+    """
+    if Q < 1:
+        raise ValueError("Q >= 1")
+    Lf = _laguerre_coeffs(Q + 2)
+    x0, _ = np.polynomial.laguerre.laggauss(Q)
+    with _ctx():
+        L = [[Decimal(c.numerator) / Decimal(c.denominator) for c in row] for row in Lf]
+        z = [_newton_polish(L[Q], g) for g in np.sort(x0)]
+        w = [zk / ((Q + 1) ** 2 * poly_eval(L[Q + 1], zk) ** 2) for zk in z]
+    return {"z": z, "w": w, "L": L}
 
 
 def to_f64(seq) -> np.ndarray:

@@ -70,7 +70,8 @@ class Config:
     ay_field: object = None
     az_field: object = None
     # 0: half-range Hermite along p_x (the HHLB models); 1: full-range
-    # Gauss-Hermite of order Qx (the HLB models the paper compares with, Sec. V)
+    # Gauss-Hermite of order Qx (the HLB models the paper compares with, Sec. V);
+    # 2: half-range Gauss-Laguerre (Sec. IV.B, Eq. "eq:hh_Kk_L")
     x_basis: int = 0
     extra: dict = field(default_factory=dict)
 
@@ -181,7 +182,8 @@ class Solver:
         self.cfg = cfg
         if cfg.nx < 3:
             raise ValueError("nx >= 3 (quadratic wall extrapolation)")
-        self.vs = VelocitySet(cfg.Qx, cfg.Qy, cfg.Qz, cfg.Nx_eq, cfg.Ny_eq, cfg.Nz_eq, x_full=cfg.x_basis == 1)
+        self.vs = VelocitySet(cfg.Qx, cfg.Qy, cfg.Qz, cfg.Nx_eq, cfg.Ny_eq, cfg.Nz_eq, x_full=cfg.x_basis == 1,
+                              x_laguerre=cfg.x_basis == 2)
         vs = self.vs
         self.edges, self.xc, self.dx = grid_x(cfg.nx, cfg.Lx, cfg.stretch_A)
         self.two_d = cfg.ny > 1

@@ -210,6 +210,73 @@ def test_full_range_x_set_layout_and_moments(Qx):
         assert vs.g_x(ux, T)[k] == pytest.approx(g[int(np.argmin(np.abs(zz - p)))], rel=1e-14)
 
 
+@pytest.mark.parametrize("Q", [1, 3, 8, 16])
+def test_gauss_laguerre_half_quadrature(Q):
+    # Half-range Gauss-Laguerre (Sec. IV.B, weights of Eq. "eq:wk_half"):
+    # exact on z^s exp(-z) for s <= 2Q - 1 (int = s!), and the nodes/weights
+    # of numpy's laggauss (a library routine).
+    import math
+    from oracle.quadrature import gauss_laguerre_half, to_f64
+    d = gauss_laguerre_half(Q)
+    z, w = to_f64(d["z"]), to_f64(d["w"])
+    for s_ in range(2 * Q):
+        assert (w * z ** s_).sum() == pytest.approx(math.factorial(s_), rel=1e-12)
+    x0, w0 = np.polynomial.laguerre.laggauss(Q)
+    np.testing.assert_allclose(z, x0, rtol=1e-12)
+    np.testing.assert_allclose(w, w0, rtol=1e-10, atol=1e-300)
+
+
+@pytest.mark.parametrize("Q", [3, 4, 8])
+def test_hl_force_matrix_identities(Q):
+    # K^L of Eq. "eq:hh_Kk_L": the discrete d/dp conserves mass (sum_k K = 0),
+    # gives -1 for the momentum (sum_k p_k K_kk' = -1) and -2 p_k' for the
+    # energy; without the jump term (-Phi0 Phi0 / 2) mass is not conserved.
+    from oracle.model import hl_force_matrix
+    vs = VelocitySet(Q, x_laguerre=True)
+    K, p = vs.Kx, vs.px
+    scale = np.abs(K).max()
+    np.testing.assert_allclose(K.sum(axis=0), 0.0, atol=1e-12 * scale)
+    np.testing.assert_allclose((p[:, None] * K).sum(axis=0), -1.0, atol=1e-12 * scale)
+    np.testing.assert_allclose((p[:, None] ** 2 * K).sum(axis=0), -2 * p, atol=1e-12 * scale * p.max())
+    # planted mistake: the jump term replaced by what differentiating each half
+    # separately gives (-omega(0) Phi0 Phi0 within a half, omega(0) = 1), as in
+    # the half-range Hermite test above: mass is no longer conserved
+    from oracle.quadrature import gauss_laguerre_half, to_f64
+    d = gauss_laguerre_half(Q)
+    w = to_f64(d["w"])
+    Phi0 = np.array([sum(float(poly_eval(d["L"][l], zk)) for l in range(Q)) for zk in d["z"]])
+    P, W = np.concatenate([Phi0, Phi0]), np.concatenate([w, -w])
+    same = np.kron(np.eye(2), np.ones((Q, Q)))
+    bad = hl_force_matrix(Q) + W[:, None] * (0.5 - same) * np.outer(P, P)
+    assert np.abs(bad.sum(axis=0)).max() > 1e-3
+
+
+@pytest.mark.parametrize("u,T", [(0.0, 1.0), (0.4, 0.8), (-0.7, 1.5)])
+def test_hl_equilibrium_by_projection_integrals(u, T):
+    # G_l^{+-} = int_0^inf g(+-p) L_l(p) dp by adaptive quadrature (scipy), and
+    # the moments n, u, T of the projected equilibrium (exact for N >= 2).
+    from scipy.integrate import quad
+    from scipy.special import eval_laguerre
+    from oracle.model import hl_equilibrium
+    from oracle.quadrature import gauss_laguerre_half, to_f64
+    Q, N = 6, 5
+    d = gauss_laguerre_half(Q)
+    z, w = to_f64(d["z"]), to_f64(d["w"])
+    g = lambda p: math.exp(-(p - u) ** 2 / (2 * T)) / math.sqrt(2 * math.pi * T)
+    ref = np.zeros(2 * Q)
+    for half, sgn in ((0, 1), (1, -1)):
+        G = [quad(lambda p: g(sgn * p) * eval_laguerre(l, p), 0, np.inf, epsabs=1e-14, epsrel=1e-13)[0]
+             for l in range(N + 1)]
+        for k in range(Q):
+            ref[half * Q + k] = w[k] * sum(eval_laguerre(l, z[k]) * G[l] for l in range(N + 1))
+    got = hl_equilibrium(Q, N, u, T)
+    np.testing.assert_allclose(got, ref, atol=1e-11)
+    vs = VelocitySet(Q, x_laguerre=True)
+    assert got.sum() == pytest.approx(1.0, rel=1e-12)
+    assert (got * vs.px).sum() == pytest.approx(u, abs=1e-12)
+    assert (got * (vs.px - u) ** 2).sum() == pytest.approx(T, rel=1e-11)
+
+
 def test_direct_product_equilibrium_moments():
     # App. A: feq = n g_x g_y g_z reproduces n, u and T = sum |p-u|^2 f/(D n).
     vs = VelocitySet(4, 4, 4)   # N = Q - 1 >= 2 on every axis

@@ -187,6 +187,58 @@ def test_barometric_interior_residual_full_range_x():
     assert res[0] / res[1] > 3.5 and res[1] / res[2] > 3.5
 
 
+@pytest.mark.parametrize("x_basis", [1, 2])
+def test_half_range_laguerre_and_full_range_x_closed_forms(x_basis):
+    # The closed forms of the tests above for the other p_x families: the
+    # homogeneous force (u = u0 + a t exactly, n and T constant), the
+    # free-molecular state in its discrete form (n_L J(T_L) = n_R J(T_R),
+    # J(T) = sum_{p_x > 0} p_x g_x(0, T); n = n_L A(T_L) + n_R A(T_R)), and the
+    # second-order barometric residual (Gauss-Hermite only: the Laguerre weight
+    # exp(-z) does not match the Maxwellian, so the projected rest state is not
+    # mapped exactly by K^L and the residual stays O(1) at small Q, a model
+    # error, not a discretisation one).  x_basis 2 is the half-range
+    # Gauss-Laguerre set (K^L of Eq. "eq:hh_Kk_L").
+    Qx = 4 if x_basis == 2 else 8
+    s = Solver(Config(Qx=Qx, Qy=4, nx=3, ax=-0.25, ay=0.15, Kn=0.3, dt=0.005, x_basis=x_basis))
+    s.init_equilibrium(1.1, 0.1, -0.05, 0.95)
+    rng = np.random.default_rng(5)
+    s.f = s.f * (1 + 0.1 * rng.uniform(-1, 1, s.f.shape))
+    n0, u0, T0, _ = s.moments()
+    for _ in range(40):
+        f = s.f
+        f1 = f + s.dt * s.source(f)
+        f2 = 0.75 * f + 0.25 * f1 + 0.25 * s.dt * s.source(f1)
+        s.f = f / 3 + 2 / 3 * f2 + 2 / 3 * s.dt * s.source(f2)
+    n, u, T, _ = s.moments()
+    np.testing.assert_allclose(n, n0, rtol=1e-12)
+    np.testing.assert_allclose(u, u0 + np.array([-0.25, 0.15, 0.0]) * 40 * s.dt, atol=1e-12)
+    np.testing.assert_allclose(T, T0, rtol=1e-11)
+    TL, TR = 0.8, 1.7
+    s = Solver(Config(Qx=Qx, nx=10, advection="upwind2", T_left=TL, T_right=TR, x_basis=x_basis))
+    s.init_equilibrium()
+    for _ in range(400):
+        fo = s.f.copy()
+        s.step(100)
+        if s.residual(fo, s.f) < 1e-13:
+            break
+    vs, h = s.vs, s.vs.QH
+    J = lambda T_: float((vs.px[:h] * vs.g_x(0.0, T_)[:h]).sum())
+    A = lambda T_: float(vs.g_x(0.0, T_)[:h].sum())
+    nl, nr = s.last_wall_density
+    np.testing.assert_allclose(nl * J(TL), nr * J(TR), rtol=1e-10)
+    np.testing.assert_allclose(s.moments()[0], nl[0] * A(TL) + nr[0] * A(TR), rtol=1e-10)
+    if x_basis == 2:
+        return
+    g = 0.5
+    res = []
+    for nx in (32, 64, 128):
+        s = Solver(Config(Qx=Qx, nx=nx, advection="upwind2", ax=-g, Kn=0.3, x_basis=x_basis))
+        n = np.exp(-g * s.xc)
+        s.f = n[None, :, None, None, None] * s.vs.equilibrium(np.float64(1.0), 0.0, 0.0, 0.0, np.float64(1.0))[None, None]
+        res.append(np.abs(s.rhs(s.f)[:, 5:-5]).max())
+    assert res[0] / res[1] > 3.5 and res[1] / res[2] > 3.5
+
+
 @pytest.mark.parametrize("Qx,Qy,Qz", [(4, 0, 0), (4, 4, 0), (3, 4, 4)])
 def test_homogeneous_force_field_closed_form(Qx, Qy, Qz):
     # A per-node acceleration field on top of the uniform one: without
