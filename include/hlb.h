@@ -70,9 +70,11 @@ typedef enum {
 enum { HLB_UPWIND2 = 0, HLB_WENO5 = 1 };
 enum { HLB_FP64 = 0, HLB_FP32 = 1 };
 /* Quadrature along p_x: the half-range Hermite of Sec. IV.B (HHLB models,
- * 2 Qx values) or the full-range Gauss-Hermite of Sec. IV.A (HLB models, Qx
- * values, Qx even), the model the paper compares against in Sec. V. */
-enum { HLB_X_HALF_RANGE = 0, HLB_X_FULL_RANGE = 1 };
+ * 2 Qx values), the full-range Gauss-Hermite of Sec. IV.A (HLB models, Qx
+ * values, Qx even), the model the paper compares against in Sec. V, or the
+ * half-range Gauss-Laguerre of Sec. IV.B (2 Qx values, Qx <= 16; force matrix
+ * Eq. "eq:hh_Kk_L", weights Eq. "eq:wk_half"). */
+enum { HLB_X_HALF_RANGE = 0, HLB_X_FULL_RANGE = 1, HLB_X_HALF_LAGUERRE = 2 };
 
 /* One channel instance.  Field order and types are part of the ABI. */
 typedef struct {
@@ -90,9 +92,10 @@ typedef struct {
     double T_left, T_right;  /* wall temperatures (> 0) at x = 0 and x = Lx               */
     double ax, ay, az;   /* acceleration a = F/m; gravity g along -x is ax = -g            */
     double Kn;           /* Knudsen number > 0; +INFINITY = collisionless (no BGK term)   */
-    int x_basis;         /* HLB_X_HALF_RANGE (0, default) or HLB_X_FULL_RANGE: then Qx is
-                            the even full-range order and p_x holds Qx values, ordered
-                            +z_1 < ... < +z_{Qx/2}, then -z_1, ..., -z_{Qx/2}            */
+    int x_basis;         /* HLB_X_HALF_RANGE (0, default), HLB_X_HALF_LAGUERRE (2), or
+                            HLB_X_FULL_RANGE: then Qx is the even full-range order and
+                            p_x holds Qx values, ordered +z_1 < ... < +z_{Qx/2}, then
+                            -z_1, ..., -z_{Qx/2}                                        */
 } hlb_config;
 
 /* Create a handle for `ninst` independent instances (ninst >= 1).  Instances
@@ -229,11 +232,13 @@ hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, dou
                       double* wx, double* wy, double* wz, double* Kx, double* Ky, double* Kz,
                       double* dx);
 
-/* One momentum axis built on the host (no handle, no device work): half != 0
+/* One momentum axis built on the host (no handle, no device work): half == 1
  * gives the half-range Hermite axis of order Q (2Q points, Eq. "eq:hh_pk",
- * K^h of Eq. "eq:hh_Kk_hh"), half == 0 the full-range Gauss-Hermite axis of
- * even order Q (Q points, K^H of Eq. "eq:H_Kk").  p and w have the axis'
- * point count, K its square (row-major [k][k']); any pointer may be NULL. */
+ * K^h of Eq. "eq:hh_Kk_hh"), half == 2 the half-range Gauss-Laguerre axis
+ * (2Q points, K^L of Eq. "eq:hh_Kk_L", Q <= 16), half == 0 the full-range
+ * Gauss-Hermite axis of even order Q (Q points, K^H of Eq. "eq:H_Kk").  p and
+ * w have the axis' point count, K its square (row-major [k][k']); any pointer
+ * may be NULL. */
 hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K);
 
 /* Equilibrium g_x(u, T) (2Qx values) of a velocity set, computed on the host

@@ -120,8 +120,9 @@ namespace {
 std::string check_config(const hlb_config& c, int i) {
     auto bad = [&](const char* what) { return "instance " + std::to_string(i) + ": " + what; };
     if (c.Qx < 1 || c.Qx > hlb::kMaxQ) return bad("Qx must be in [1, 32]");
-    if (c.x_basis != HLB_X_HALF_RANGE && c.x_basis != HLB_X_FULL_RANGE)
-        return bad("x_basis must be HLB_X_HALF_RANGE or HLB_X_FULL_RANGE");
+    if (c.x_basis != HLB_X_HALF_RANGE && c.x_basis != HLB_X_FULL_RANGE && c.x_basis != HLB_X_HALF_LAGUERRE)
+        return bad("x_basis must be HLB_X_HALF_RANGE, HLB_X_FULL_RANGE or HLB_X_HALF_LAGUERRE");
+    if (c.x_basis == HLB_X_HALF_LAGUERRE && c.Qx > hlb::kMaxQLaguerre) return bad("Gauss-Laguerre Qx must be in [1, 16]");
     if (c.x_basis == HLB_X_FULL_RANGE && (c.Qx < 2 || c.Qx % 2)) return bad("full-range Qx must be even in [2, 32]");
     for (int q : {c.Qy, c.Qz})
         if (q < 0 || q > hlb::kMaxQ || (q % 2)) return bad("Qy, Qz must be 0 or even in [2, 32]");
@@ -210,6 +211,11 @@ constexpr unsigned long long kDefaultWaitNs = 1000000000ull;   // 1 s
 void fill_dev(Group& G) {
     hlb::GroupDev& d = G.dev;
     d.V = G.V; d.QX2 = G.QX2; d.VY = G.VY; d.VZ = G.VZ; d.Qx = G.tx.Q; d.x_full = G.x_full ? 1 : 0;
+    d.om0 = G.tx.om0;
+    {
+        const float hi = (float)(-G.tx.om0);
+        d.m_om0f = make_float2(hi, (float)(-G.tx.om0 - (double)hi));
+    }
     d.Nx = G.Nx; d.Ny = G.Qy ? G.Ny : 0; d.Nz = G.Qz ? G.Nz : 0;
     d.Qy = G.Qy; d.Qz = G.Qz;
     d.D = 1 + (G.Qy > 0) + (G.Qz > 0);
@@ -246,7 +252,8 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     G.Ny = c0.Qy ? (c0.Ny_eq < 0 ? c0.Qy - 1 : c0.Ny_eq) : 0;
     G.Nz = c0.Qz ? (c0.Nz_eq < 0 ? c0.Qz - 1 : c0.Nz_eq) : 0;
     G.x_full = c0.x_basis == HLB_X_FULL_RANGE;
-    std::string e = G.x_full ? hlb::build_full_x_axis(G.Qx, G.Nx, G.tx) : hlb::build_half_axis(G.Qx, G.Nx, G.tx);
+    std::string e = G.x_full ? hlb::build_full_x_axis(G.Qx, G.Nx, G.tx)
+                             : hlb::build_half_axis(G.Qx, G.Nx, G.tx, c0.x_basis == HLB_X_HALF_LAGUERRE);
     if (!e.empty()) return fail(HLB_EINVAL, e);
     if (G.Qy) { e = hlb::build_full_axis(G.Qy, G.Ny, G.ty); if (!e.empty()) return fail(HLB_EINVAL, e); }
     else hlb::absent_axis(G.ty);
@@ -314,7 +321,7 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     rec.insert(rec.end(), G.tx.rb.begin(), G.tx.rb.end());
     rec.insert(rec.end(), G.tx.rc.begin(), G.tx.rc.end());
     rec.insert(rec.end(), G.tx.h0.begin(), G.tx.h0.end());
-    for (double a : G.tx.ra) rec.push_back(1.0 / a);
+    rec.insert(rec.end(), G.tx.dcoef.begin(), G.tx.dcoef.end());
     if (G.x_full) rec.assign(5 * (size_t)G.Nx + 1, 0.0);     // the full-range x roles read no recurrence table
     std::vector<double> invdx(G.dx_all.size()), wscale(G.V);
     for (size_t i = 0; i < invdx.size(); ++i) invdx[i] = 1.0 / G.dx_all[i];
@@ -322,6 +329,10 @@ hlb_status build_group(hlb_handle* h, Group& G) {
         for (int j = 0; j < G.VY; ++j)
             for (int i = 0; i < G.QX2; ++i)
                 wscale[(k * G.VY + j) * G.QX2 + i] = 1.0 / (G.tx.w[i] * G.ty.w[j] * G.tz.w[k]);
+    if (G.precision == HLB_FP32)
+        for (double ws : wscale)
+            if (!(ws < 1e36))
+                return fail(HLB_EUNSUPPORTED, "velocity set with weights below 1e-36: the FP32 state cannot hold it");
     hlb_status s;
     {
         auto split = [](const std::vector<double>& v) {
@@ -1041,7 +1052,7 @@ hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, dou
 
 hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K) {
     hlb::AxisTables ax;
-    std::string e = half ? hlb::build_half_axis(Q, Q - 1, ax) : hlb::build_full_axis(Q, Q - 1, ax);
+    std::string e = half ? hlb::build_half_axis(Q, Q - 1, ax, half == 2) : hlb::build_full_axis(Q, Q - 1, ax);
     if (!e.empty()) return fail(HLB_EINVAL, e);
     if (p) std::copy(ax.p.begin(), ax.p.end(), p);
     if (w) std::copy(ax.w.begin(), ax.w.end(), w);

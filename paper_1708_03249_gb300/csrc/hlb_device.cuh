@@ -7,7 +7,6 @@
 
 namespace hlb {
 
-constexpr double kInvSqrt2Pi = 0.39894228040143267793994605993438;
 constexpr double kSqrt2Pi = 2.5066282746310005024157652848110;
 
 template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
@@ -365,7 +364,7 @@ __device__ inline void node_coefficients(const GroupDev& g, int r, double ux, do
         double S = 0.0;
         double gm1 = 0.0;
         for (int l = 0; l < Nx; ++l) {
-            const double ig = (l ? gm1 * inv_ra[l - 1] : 0.0) - kInvSqrt2Pi * h0[l] * S;
+            const double ig = (l ? gm1 * inv_ra[l - 1] : 0.0) - g.om0 * h0[l] * S;
             const double pg = us * G[l] + T * (g0 * h0[l] + ig);
             G[l + 1] = ra[l] * pg + rb[l] * G[l] + rc[l] * gm1;
             S += h0[l] * G[l];
@@ -567,7 +566,7 @@ __device__ inline void node_coefficients_df(const GroupDev& g, int r, const Node
         // int_0^inf g(+-p) dp = (1 +- erf(u_x/sqrt(2T)))/2, with h_0 = h0[0]
         const float2 half = df_add(make_float2(0.5f, 0.0f), make_float2(0.5f * sg * in.erf_z.x, 0.5f * sg * in.erf_z.y));
         G[0] = df_mul(h0[0], half);
-        const float2 m_om0 = make_float2(-3.989422917e-01f, 1.133517014e-08f);   // -1/sqrt(2 pi)
+        const float2 m_om0 = g.m_om0f;                 // -omega(0) of the half-range family
         float2 S = make_float2(0.0f, 0.0f), gm1 = make_float2(0.0f, 0.0f);
         for (int l = 0; l < Nx; ++l) {
             float2 ig = df_mul(df_mul(m_om0, h0[l]), S);

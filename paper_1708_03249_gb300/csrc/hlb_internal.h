@@ -14,6 +14,7 @@ constexpr int HLB_UPWIND2_ = 0, HLB_WENO5_ = 1;
 constexpr int HLB_FP64_ = 0, HLB_FP32_ = 1;
 
 constexpr int kMaxQ = 32;          // largest quadrature order per axis
+constexpr int kMaxQLaguerre = 16;  // half-range Gauss-Laguerre: beyond, weights < 1e-22 and |p| > 50
 constexpr int kMaxN = kMaxQ;       // largest equilibrium order + 1
 
 // One momentum axis of the direct-product velocity set (App. A).
@@ -31,11 +32,14 @@ struct AxisTables {
     // Full-range: T[j][l] = w_j He_l(z_j) / l!.
     std::vector<double> T;
     std::vector<double> ra, rb, rc, h0;
+    // half-range families: omega(0) and d_{l+1} of p_{l+1}' = d_{l+1} p_l - omega(0) p_{l+1}(0) sum ...
+    double om0 = 0.0;
+    std::vector<double> dcoef;
 };
 
 // Build the tables of a half-range (p_x) or full-range (p_y, p_z) axis.
 // Returns "" on success or an error message.
-std::string build_half_axis(int Q, int N, AxisTables& out);
+std::string build_half_axis(int Q, int N, AxisTables& out, bool laguerre = false);
 std::string build_full_axis(int Q, int N, AxisTables& out);
 // Full-range Gauss-Hermite of even order Q along p_x, in the layout of the
 // half-range axis: p = (+z_1 .. +z_{Q/2}, -z_1 .. -z_{Q/2}) with z ascending,
@@ -96,6 +100,8 @@ struct GroupDev {
     int use_df;              // FP32 groups with Nx <= 11: equilibrium in double-float
     int x_full;              // p_x on the mirrored full-range axis: the x roles use the
                              // full-range recurrence with +-u_x (rec unused)
+    double om0;              // omega(0) of the half-range family (1/sqrt(2 pi) Hermite, 1 Laguerre)
+    float2 m_om0f;           // -omega(0) in double-float
     const double* dx;        // FP64 x-cell widths, concatenated per instance
     const void* gw;          // R: wall Maxwellians
     double* nw;              // FP64 [nrows][2] emitted densities

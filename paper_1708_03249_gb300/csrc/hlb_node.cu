@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __r
 // reads from shared memory); a warp's 32 factor lines are assembled in shared
 // memory and written out contiguously.
 template <int NM>
-__device__ __forceinline__ void half_range_G_df(int r, const NodeDF& in, const float2* recf, int Nx, float2 (&G)[NM]) {
+__device__ __forceinline__ void half_range_G_df(int r, const NodeDF& in, const float2* recf, int Nx, float2 m_om0,
+                                                float2 (&G)[NM]) {
     const float2* ra = recf;
     const float2* rb = recf + Nx;
     const float2* rc = recf + 2 * Nx;
@@ -274,7 +275,6 @@ __device__ __forceinline__ void half_range_G_df(int r, const NodeDF& in, const f
     const float2 us = make_float2(sg * in.ux.x, sg * in.ux.y);
     const float2 half = df_add(make_float2(0.5f, 0.0f), make_float2(0.5f * sg * in.erf_z.x, 0.5f * sg * in.erf_z.y));
     G[0] = df_mul(h0[0], half);
-    const float2 m_om0 = make_float2(-3.989422917e-01f, 1.133517014e-08f);   // -1/sqrt(2 pi)
     float2 S = make_float2(0.0f, 0.0f), gm1 = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int l = 0; l < NM - 1; ++l) {
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const fl
                 if (g.x_full)                                 // full-range p_x: G_l(+-u_x)
                     full_range_G_df<NM>(r ? make_float2(-in.ux.x, -in.ux.y) : in.ux, in.Tm1, Nx, G);
                 else
-                    half_range_G_df<NM>(r, in, sRec, Nx, G);
+                    half_range_G_df<NM>(r, in, sRec, Nx, g.m_om0f, G);
                 lines_dot2<NM>(line + r * Qx, sPx, Qx, G, Nx, &in.n);
             }
             if (g.Qy) {

@@ -133,6 +133,18 @@ Recurrence hermite_recurrence(int M) {
     return r;
 }
 
+// Laguerre, weight exp(-z) on [0, inf) (unit mass): with p_l = (-1)^l L_l
+// (positive leading coefficient), z p_l = (l+1) p_{l+1} + (2l+1) p_l + l p_{l-1}.
+Recurrence laguerre_recurrence(int M) {
+    Recurrence r;
+    r.alpha.resize(M);
+    for (int l = 0; l < M; ++l) r.alpha[l] = 2.0 * l + 1.0;
+    r.sb.assign(M + 1, 0.0);
+    r.sb[0] = 1.0;
+    for (int l = 1; l <= M; ++l) r.sb[l] = (double)l;
+    return r;
+}
+
 // Orthonormal polynomial values p_0..p_L at z, and p_L'(z).
 void ortho_values(const Recurrence& r, int L, double z, double* vals, double* dL = nullptr) {
     double pm = 0.0, p = 1.0 / r.sb[0];
@@ -204,12 +216,24 @@ void absent_axis(AxisTables& out) {
     out.T = {1.0};
 }
 
-std::string build_half_axis(int Q, int N, AxisTables& out) {
-    if (Q < 1 || Q > kMaxQ) return "Qx must be in [1, 32]";
+// Both half-range families (App. B): the orthonormal p_l of the weight omega
+// on [0, inf) with derivative expansion
+//   p_l' = d_l p_{l-1} - omega(0) p_l(0) sum_{s<l} p_s(0) p_s,
+// half-range Hermite: omega(z) = exp(-z^2/2)/sqrt(2 pi), d_l = 1/a_{l-1}
+// (Eqs. "eq:phip", "eq:hh_varphi"); Gauss-Laguerre: omega(z) = exp(-z),
+// d_l = 0 (L_l' = -sum_{s<l} L_s, in the sign convention p_l = (-1)^l L_l).
+// K of Eq. "eq:hh_Kk" then reads, for k, k' on the same half,
+//   w_k s_k [ sum_{l<=Q-2} p_l(z_k') (omega(0) p_l(0) sum_{s=l+1}^{Q-1} p_s(0) p_s(z_k) - d_{l+1} p_{l+1}(z_k))
+//            - omega(0)/2 Phi0(z_k) Phi0(z_k') ],
+// and only the last term across halves (Eqs. "eq:hh_Kk_hh", "eq:hh_Kk_L").
+std::string build_half_axis(int Q, int N, AxisTables& out, bool laguerre) {
+    if (Q < 1 || Q > (laguerre ? kMaxQLaguerre : kMaxQ))
+        return laguerre ? "Gauss-Laguerre Qx must be in [1, 16]" : "Qx must be in [1, 32]";
     if (N < 0 || N >= Q) return "Nx_eq must be in [0, Qx - 1]";
-    const Recurrence r = half_range_recurrence(Q + 2);
-    const double om0 = 1.0 / std::sqrt(2.0 * kPi);
+    const Recurrence r = laguerre ? laguerre_recurrence(Q + 2) : half_range_recurrence(Q + 2);
+    const double om0 = laguerre ? 1.0 : 1.0 / std::sqrt(2.0 * kPi);
     out = AxisTables();
+    out.om0 = om0;
     out.Q = Q;
     out.half = true;
     out.count = 2 * Q;
@@ -255,7 +279,7 @@ std::string build_half_axis(int Q, int N, AxisTables& out) {
             double val = 0.0;
             if (sk == skp) {
                 for (int l = 0; l <= Q - 2; ++l)
-                    val += H[kkp][l] * (h0[l] * om0 * tail[kk][l] - r.sb[l + 1] * H[kk][l + 1]);
+                    val += H[kkp][l] * (h0[l] * om0 * tail[kk][l] - (laguerre ? 0.0 : r.sb[l + 1]) * H[kk][l + 1]);
             }
             val -= 0.5 * om0 * Phi0[kk] * Phi0[kkp];
             out.K[k * 2 * Q + kp] = w[kk] * sk * val;
@@ -268,12 +292,14 @@ std::string build_half_axis(int Q, int N, AxisTables& out) {
     out.ra.resize(N);
     out.rb.resize(N);
     out.rc.resize(N);
+    out.dcoef.resize(N);
     out.h0.assign(h0.begin(), h0.begin() + N + 1);
     for (int l = 0; l < N; ++l) {
         // h_{l+1} = ((z - alpha_l) h_l - sb_l h_{l-1}) / sb_{l+1}
         out.ra[l] = 1.0 / r.sb[l + 1];
         out.rb[l] = -r.alpha[l] / r.sb[l + 1];
         out.rc[l] = l ? -r.sb[l] / r.sb[l + 1] : 0.0;
+        out.dcoef[l] = laguerre ? 0.0 : r.sb[l + 1];      // d_{l+1}: coefficient of p_l in p_{l+1}'
     }
     return "";
 }
@@ -369,7 +395,7 @@ void axis_equilibrium(const AxisTables& ax, double u, double T, double* g) {
     double G[kMaxN + 2];
     if (ax.half) {
         const int Q = ax.Q;
-        const double om0 = 1.0 / std::sqrt(2.0 * kPi);
+        const double om0 = ax.om0;
         const double g0 = std::exp(-u * u / (2.0 * T)) / std::sqrt(2.0 * kPi * T);
         for (int sgn = 0; sgn < 2; ++sgn) {
             const double us = sgn ? -u : u;
@@ -377,7 +403,7 @@ void axis_equilibrium(const AxisTables& ax, double u, double T, double* g) {
             double S = 0.0;
             for (int l = 0; l < N; ++l) {
                 const double gm1 = l ? G[l - 1] : 0.0;
-                const double ig = (l ? gm1 / ax.ra[l - 1] : 0.0) - om0 * ax.h0[l] * S;
+                const double ig = (l ? gm1 * ax.dcoef[l - 1] : 0.0) - om0 * ax.h0[l] * S;
                 const double pg = us * G[l] + T * (g0 * ax.h0[l] + ig);
                 G[l + 1] = ax.ra[l] * pg + ax.rb[l] * G[l] + ax.rc[l] * gm1;
                 S += ax.h0[l] * G[l];

@@ -271,11 +271,12 @@ def equilibrium_x(Qx: int, u: float, T: float, Nx_eq: int = -1) -> np.ndarray:
     return g
 
 
-def axis(Q: int, half: bool):
-    """(p, w, K) of a half-range (2Q points) or full-range (Q points) axis, host-built."""
+def axis(Q: int, half, laguerre: bool = False):
+    """(p, w, K) of a half-range (2Q points; Hermite, or Gauss-Laguerre with
+    ``laguerre``) or full-range (Q points) axis, host-built."""
     n = 2 * Q if half else Q
     p, w, K = np.empty(n), np.empty(n), np.empty(n * n)
-    _check(lib().hlb_axis(Q, int(bool(half)), _dptr(p), _dptr(w), _dptr(K)))
+    _check(lib().hlb_axis(Q, (2 if laguerre else 1) if half else 0, _dptr(p), _dptr(w), _dptr(K)))
     return p, w, K.reshape(n, n)
 
 

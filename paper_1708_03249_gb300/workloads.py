@@ -19,7 +19,8 @@ import numpy as np
 
 UPWIND2, WENO5 = 0, 1
 FP64, FP32 = 0, 1
-X_HALF, X_FULL = 0, 1      # quadrature along p_x: half-range Hermite (HHLB) or Gauss-Hermite (HLB)
+X_HALF, X_FULL, X_LAGUERRE = 0, 1, 2   # along p_x: half-range Hermite (HHLB), Gauss-Hermite (HLB),
+                                       # half-range Gauss-Laguerre
 
 # Every workload is a plain dict of hlb_config fields (see include/hlb.h).
 _BASE = dict(Qx=4, Qy=0, Qz=0, Nx_eq=-1, Ny_eq=-1, Nz_eq=-1, nx=64, ny=1,

@@ -36,7 +36,7 @@ def test_version(hlb_lib):
 @pytest.mark.parametrize("field,value", [("Qx", 0), ("Qx", 33), ("Qy", 3), ("Qz", -2), ("nx", 5),
                                           ("ny", 2), ("Kn", 0.0), ("T_left", -1.0), ("stretch_A", 1.0),
                                           ("advection", 7), ("precision", 3), ("Nx_eq", 4), ("Lx", 0.0),
-                                          ("x_basis", 2),
+                                          ("x_basis", 3),
                                           ("ax", math.nan)])
 def test_invalid_config_is_rejected(hlb_lib, field, value):
     cfg = W.make(Qx=4, Qy=4, nx=16, Kn=1.0)
@@ -45,6 +45,26 @@ def test_invalid_config_is_rejected(hlb_lib, field, value):
         hlb.Handle(cfg)
     assert e.value.status == hlb.HLB_EINVAL
     assert "instance 0" in str(e.value)
+
+
+@pytest.mark.parametrize("Q", [1, 3, 8, 16])
+def test_laguerre_axis_matches_oracle(hlb_lib, Q):
+    # The library's half-range Gauss-Laguerre tables (built from the generic
+    # orthonormal recurrence) against the oracle's (Decimal roots, Eq.
+    # "eq:wk_half" weights, K^L of Eq. "eq:hh_Kk_L" term by term).
+    from oracle.model import VelocitySet
+    p, w, K = hlb.axis(Q, True, laguerre=True)
+    vs = VelocitySet(Q, x_laguerre=True)
+    np.testing.assert_allclose(p, vs.px, rtol=1e-13)
+    np.testing.assert_allclose(w, vs.wx, rtol=1e-10)
+    np.testing.assert_allclose(K, vs.Kx, atol=1e-11 * np.abs(vs.Kx).max())
+
+
+def test_laguerre_order_above_16_is_rejected(hlb_lib):
+    cfg = W.make(Qx=17, nx=16, Kn=1.0, x_basis=W.X_LAGUERRE)
+    with pytest.raises(hlb.HlbError) as e:
+        hlb.Handle(cfg)
+    assert e.value.status == hlb.HLB_EINVAL
 
 
 def test_odd_full_range_x_order_is_rejected(hlb_lib):

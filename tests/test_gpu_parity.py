@@ -248,6 +248,33 @@ def test_full_range_x_models(Qx, Qy, ny, prec, adv):
         _check_fp32(got, mom, refs)
 
 
+@pytest.mark.parametrize("Qx,Qy,ny,prec,adv", [(4, 4, 1, W.FP32, W.WENO5), (8, 8, 4, W.FP32, W.WENO5),
+                                                (4, 4, 1, W.FP64, W.UPWIND2)])
+def test_half_range_laguerre_models(Qx, Qy, ny, prec, adv):
+    # Half-range Gauss-Laguerre along p_x (K^L of Eq. "eq:hh_Kk_L"): the line
+    # kernel (8 x 4), the pair kernel (16 x 8) and the FP64 kernel, with the
+    # library's equilibrium recurrence (omega(0) = 1, no 1/a term) for the
+    # node pass and the walls, against the oracle's moment projection
+    cfg = W.make(Qx=Qx, Qy=Qy, nx=19, ny=ny, Ly=0.2, advection=adv, precision=prec, T_left=0.9, T_right=1.3,
+                 Kn=0.3, x_basis=W.X_LAGUERRE, **W.gravity(0.4, 20.0))
+    got, mom, N, refs = run_pair(cfg, 5, init=(1.0, 0.05, 0.0, 1.0))
+    if prec == W.FP64:
+        _check_fp64(got, refs, 1e-10)
+    else:
+        _check_fp32(got, mom, refs)
+
+
+def test_laguerre_initial_equilibrium_matches_oracle():
+    from oracle.model import VelocitySet
+    from paper_1708_03249_gb300 import hlb
+    cfg = W.make(Qx=8, Qy=4, nx=7, precision=W.FP64, x_basis=W.X_LAGUERRE, Kn=1.0)
+    with hlb.Handle(cfg, stream=_stream()) as h:
+        h.init_equilibrium(1.2, -0.3, 0.1, 0.8)
+        got = h.get_state().reshape(7, -1)
+    ref = VelocitySet(8, 4, x_laguerre=True).equilibrium(np.float64(1.2), -0.3, 0.1, 0.0, np.float64(0.8)).reshape(-1)
+    np.testing.assert_allclose(got, np.broadcast_to(ref, got.shape), atol=1e-13 * np.abs(ref).max())
+
+
 def test_fp32_batched_mixed_instances():
     insts = W.batched_instances(6)
     insts = [W.scaled(c, nx=min(c["nx"], 40)) for c in insts]
