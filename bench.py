@@ -304,7 +304,7 @@ def run_gpu(args):
     pinned = torch.empty(values, dtype=torch.float32, pin_memory=True)
     h.get_state(pinned.numpy())
     h.set_options(use_graphs=True, time_kernels=False)
-    e2e_iters = max(2, min(args.steps, 10))
+    e2e_iters = max(2, min(args.steps, 20))
     # page-locked result arrays, like the input: the moments land by DMA
     moms = [torch.empty(k * nodes, dtype=torch.float64, pin_memory=True).numpy() for k in (1, 3, 1, 1)]
     import ctypes

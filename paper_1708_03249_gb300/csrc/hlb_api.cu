@@ -989,6 +989,26 @@ hlb_status hlb_commit_state(hlb_handle* h) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (!h->staged) return fail(HLB_EINVAL, "no state staged: call hlb_prefetch_state first");
     HLB_CUDA(cudaStreamWaitEvent(h->stream, h->stage_filled, 0));
+    // One group whose state layout is the caller's: the staging buffer becomes
+    // the state buffer and the old state buffer the next staging buffer (no
+    // copy).  The next prefetch writes it only after the work enqueued so far
+    // (which may still read it) has run.  A captured graph holds the old
+    // pointers, so it is dropped; hlb_step captures a new one when it needs it.
+    bool same_layout = h->groups.size() == 1;
+    if (same_layout) {
+        const Group& G = *h->groups[0];
+        same_layout = G.nvalues == h->total_values;
+        for (size_t k = 0; same_layout && k < G.members.size(); ++k)
+            same_layout = G.inst[k].f_off == h->inst_value_off[G.members[k]];
+    }
+    if (same_layout) {
+        Group& G = *h->groups[0];
+        std::swap(G.buf[G.cur].p, h->stage_buf);
+        if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+        h->have_residual = false;
+        h->staged = false;
+        return HLB_OK;
+    }
     const hlb_status s = state_copy(h, h->stage_buf, (size_t)(h->total_values * (long long)h->esize), false,
                                     cudaMemcpyDeviceToDevice, false);
     if (s == HLB_OK) h->staged = false;

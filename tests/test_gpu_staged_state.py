@@ -4,8 +4,9 @@ A state staged from page-locked memory while steps run on the current one,
 then committed, must be exactly the state that hlb_set_state would have set
 (byte for byte), and the steps that follow must give the same bits as after
 hlb_set_state.  Several instances of two velocity sets exercise the
-per-instance copies out of the staging buffer.  A commit with nothing staged
-and a buffer of the wrong size are rejected.
+per-instance copies out of the staging buffer; one velocity set the buffer
+swap (twice, so the old state buffer serves as staging buffer once).  A
+commit with nothing staged and a buffer of the wrong size are rejected.
 """
 import numpy as np
 import pytest
@@ -17,15 +18,21 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _cfgs():
+def _cfgs(kind="groups"):
+    if kind == "one_group":
+        # one velocity set: the commit swaps the staging and state buffers
+        return [W.make(Qx=8, Qy=8, nx=30, ny=5, Ly=0.2, Kn=0.5, ax=-0.2, precision=W.FP32),
+                W.make(Qx=8, Qy=8, nx=16, Kn=1.0, T_right=1.5, precision=W.FP32)]
+    # two velocity sets: the commit copies the staging buffer into the groups
     return [W.make(Qx=4, Qy=4, nx=24, Kn=0.3, ax=-0.2, precision=W.FP32),
             W.make(Qx=8, Qy=8, nx=16, Kn=1.0, T_right=1.5, precision=W.FP32),
             W.make(Qx=4, Qy=4, nx=40, Kn=0.1, precision=W.FP32)]
 
 
-def test_committed_state_equals_set_state_and_steps_agree():
+@pytest.mark.parametrize("kind", ["groups", "one_group"])
+def test_committed_state_equals_set_state_and_steps_agree(kind):
     from paper_1708_03249_gb300 import hlb
-    with hlb.Handle(_cfgs()) as a, hlb.Handle(_cfgs()) as b:
+    with hlb.Handle(_cfgs(kind)) as a, hlb.Handle(_cfgs(kind)) as b:
         a.init_equilibrium(1.0, 0.0, 0.0, 1.0)
         f1 = a.get_state().astype(np.float64) * W.perturbation(a.values, seed=11, amplitude=0.05)
         pinned = torch.empty(a.values, dtype=torch.float32, pin_memory=True)
@@ -37,12 +44,22 @@ def test_committed_state_equals_set_state_and_steps_agree():
         got = a.get_state()
         np.testing.assert_array_equal(got, pinned.numpy())
         b.set_state(pinned.numpy())
-        a.step(4)
+        a.step(4)                                   # a graph is captured again after a swap
         b.step(4)
         np.testing.assert_array_equal(a.get_state(), b.get_state())
         with pytest.raises(hlb.HlbError) as e:     # the staged state was consumed
             a.commit_state()
         assert e.value.status == hlb.HLB_EINVAL
+        # a second round through the same buffers (the old state buffer is now staging)
+        f2 = pinned.numpy() * np.float32(1.01)
+        pinned2 = torch.from_numpy(f2).pin_memory()
+        a.prefetch_state(pinned2.data_ptr(), a.state_bytes)
+        a.step(1)
+        a.commit_state()
+        b.set_state(pinned2.numpy())
+        a.step(3)
+        b.step(3)
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
 
 
 def test_second_prefetch_replaces_the_first_and_bad_size_is_rejected():
