@@ -313,6 +313,14 @@ __device__ __forceinline__ void csum_add(double& s, double& c, double x) {
     s += x;
 }
 
+// csum_add on two independent sums at once in the packed FP32 pipe.
+__device__ __forceinline__ void csum_add2(float2& s, float2& c, float2 x) {
+    const float2 t = __fadd2_rn(s, x);
+    const float2 bp = fsub2(t, s);
+    c = __fadd2_rn(c, __fadd2_rn(fsub2(s, fsub2(t, bp)), fsub2(x, bp)));
+    s = t;
+}
+
 // Butterfly reduction of (s, c) over groups of 2 O consecutive lanes (O = 16:
 // the whole warp); every lane of a group ends with the group's sum.
 template <typename R, int O = 16>

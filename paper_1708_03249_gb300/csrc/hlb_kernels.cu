@@ -447,6 +447,42 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
                     const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
                     const InstDev& I = g.inst[ii];
                     const R4* f4 = reinterpret_cast<const R4*>(fs + (size_t)I.f_off + (size_t)(node - I.node_off) * V);
+                    if constexpr (sizeof(R) == 4) {
+                        // FP32: the nine sums in the lanes of f32x2 registers, compensated
+                        // pairwise (n, j_x), (j_y, j_z), (P_xx, E - P_xx), (P_xy, P_xz), (Q, -)
+                        float2 s2[5], c2[5];
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) s2[q] = c2[q] = make_float2(0.0f, 0.0f);
+                        float2 pjx[4], p13[4];                   // (p_x, p_x^2), (1, p_x^3) per element
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            pjx[e] = make_float2((float)px[e], (float)px2[e]);
+                            p13[e] = make_float2(1.0f, (float)px3[e]);
+                        }
+#pragma unroll 4
+                        for (int k = sl; k < (V >> 2); k += 8) {
+                            const float4 x = reinterpret_cast<const float4*>(f4)[k];
+                            const float4 yz = reinterpret_cast<const float4*>(sYZ)[k >> (lg - 2)];
+                            const float xe[4] = {x.x, x.y, x.z, x.w};
+                            float2 jp = make_float2(0.0f, 0.0f), sq = make_float2(0.0f, 0.0f);   // (j_x, P_xx), (n, Q_x)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                jp = __ffma2_rn(pjx[e], f2(xe[e]), jp);
+                                sq = __ffma2_rn(p13[e], f2(xe[e]), sq);
+                            }
+                            const float2 yzv = make_float2(yz.x, yz.y);
+                            csum_add2(s2[0], c2[0], make_float2(sq.x, jp.x));
+                            csum_add2(s2[1], c2[1], __fmul2_rn(yzv, f2(sq.x)));
+                            csum_add2(s2[2], c2[2], make_float2(jp.y, yz.z * sq.x));
+                            csum_add2(s2[3], c2[3], __fmul2_rn(yzv, f2(jp.x)));
+                            csum_add2(s2[4], c2[4], make_float2(fmaf(yz.z, jp.x, sq.y), 0.0f));
+                        }
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) {
+                            a[2 * q] = (R)s2[q].x; c[2 * q] = (R)c2[q].x;
+                            if (q < 4) { a[2 * q + 1] = (R)s2[q].y; c[2 * q + 1] = (R)c2[q].y; }
+                        }
+                    } else {
 #pragma unroll 4
                     for (int k = sl; k < (V >> 2); k += 8) {
                         const R4 x = f4[k];
@@ -460,6 +496,7 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
                         csum_add(a[4], c[4], pxx); csum_add(a[5], c[5], yz.z * sm);
                         csum_add(a[6], c[6], yz.x * jx); csum_add(a[7], c[7], yz.y * jx);
                         csum_add(a[8], c[8], pxxx + yz.z * jx);
+                    }
                     }
                 }
                 // eight-lane trees; lane L keeps node L's sums (lane 8 (L & 3) of sub-batch L >> 2)
