@@ -265,6 +265,7 @@ def run_gpu(args):
     nodes, values, state_bytes = h.nodes, h.values, h.state_bytes
     V = values // nodes
     h.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+    segments = h.autotune()              # marching-kernel segment length, timed per group (untimed here)
 
     def barrier():
         if dist is not None:
@@ -373,7 +374,7 @@ def run_gpu(args):
                    "nodes": nodes, "values_per_copy": values, "precision": "fp32",
                    "advection": "weno5", "parallelism": f"replicas{world}",
                    "l2": f"state ({state_bytes / 1e9:.2f} GB per copy) larger than L2; no flush needed",
-                   "moments_finite": finite},
+                   "moments_finite": finite, "segment_cells": segments},
         "roofline": roofline_of(achieved, peak, peak_kind, alu_achieved, alu_peak, sm_mhz, traffic,
                                 stage_avg_ms, kt, flop_nv),
         "cpu_baseline": {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": cpu_cores,
@@ -416,6 +417,7 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     h = hlb.Handle(insts, stream=stream.cuda_stream)
     h.init_equilibrium()
+    segments = h.autotune()
     h.set_options(use_graphs=True, time_kernels=False)
     h.step(args.warmup)
     torch.cuda.synchronize()
@@ -452,7 +454,7 @@ def run_batched(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"batched_{args.ninst}_channels_splitmix64_seed{W.BATCH_SEED}",
-                       "values_per_copy": nv, "moments_finite": finite},
+                       "values_per_copy": nv, "moments_finite": finite, "segment_cells": segments},
             "fp64_per_instance": {"value": rate64, "unit": "node-velocity updates/s",
                                   "instances": len(sample), "dtype": "f64",
                                   "desc": "each sampled instance its own FP64 handle, stepped alone"},
@@ -469,6 +471,10 @@ OTHER_WORKLOADS = {
     "stretched_channel": ("1D FP32 channel, 512 cells tanh A=0.9, Qx=8 x Qy=8, WENO5, Kn=0.1, g=0.5 at 30 deg",
                           lambda: W.channel_1d_stretched(0.1)),
     "box2d": ("2D FP32 box 256x256, Qx=16 x Qy=16, WENO5, Kn=0.05, g=0.2 at 45 deg", lambda: W.BOX_2D),
+    "long_channel_q16": ("1D FP32 channel, 131072 cells, Qx=16 x Qy=16 (the batched set's largest slab, "
+                         "tensor-core force term), WENO5, Kn=0.1, g=0.36 at 34 deg; 268 MB per copy",
+                         lambda: W.make(Qx=16, Qy=16, nx=131072, T_left=1.0, T_right=1.5, ax=-0.3, ay=-0.2,
+                                        Kn=0.1, advection=W.WENO5, precision=W.FP32)),
 }
 
 
@@ -487,6 +493,7 @@ def run_other(args):
     stream = torch.cuda.Stream()
     with hlb.Handle(cfg, stream=stream.cuda_stream) as h:
         h.init_equilibrium()
+        segments = h.autotune()
         h.set_options(use_graphs=True, time_kernels=False)
         h.step(max(args.warmup, 30))
         torch.cuda.synchronize()
@@ -503,7 +510,7 @@ def run_other(args):
             "steps": steps, "warmup": max(args.warmup, 30), "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if cfg["precision"] == W.FP64 else "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": desc, "values_per_copy": nv,
+            "config": {"workload": args.workload, "desc": desc, "values_per_copy": nv, "segment_cells": segments,
                        "moments_finite": bool(np.isfinite(n).all() and np.isfinite(T).all())}}
     print(json.dumps(line), flush=True)
 

@@ -200,6 +200,19 @@ hlb_status hlb_set_state(hlb_handle* h, const void* host_f, size_t bytes);
 hlb_status hlb_get_state_dev(hlb_handle* h, void* f_dev, size_t bytes);
 hlb_status hlb_set_state_dev(hlb_handle* h, const void* f_dev, size_t bytes);
 
+/* Autotuner of the marching kernels' launch shape: for every velocity-set
+ * group that runs them, times the three stage launches of one step for x-
+ * segment lengths from a quarter to four times the built-in heuristic's (CUDA
+ * events on the handle's stream, one untimed round, three timed) and keeps the
+ * fastest.  The state is only read (the launches write the two scratch
+ * buffers), so the call may come at any time between steps; it synchronises
+ * the handle's streams and drops the captured graph.  The results do not
+ * depend on the segment length (every cell's update is computed the same way),
+ * only the time does.  segments_out (may be NULL): one entry per group in
+ * creation order, the chosen length in cells (0: the group does not march).
+ * No counterpart in the paper.  Errors: HLB_ECUDA, HLB_ETIMEOUT. */
+hlb_status hlb_autotune(hlb_handle* h, int* segments_out);
+
 /* Staged state input, so that the upload of the next state overlaps the
  * steps still running (no counterpart in the paper: host I/O only).
  * hlb_prefetch_state enqueues a host-to-device copy of host_f (exactly

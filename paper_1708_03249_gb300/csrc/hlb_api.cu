@@ -243,6 +243,25 @@ void fill_dev(Group& G) {
     d.inject_stall = 0;
 }
 
+// The marching kernel's work list: one CTA per (p_z slab, instance, strip of
+// TY rows, x-segment of SX cells).
+hlb_status set_segments(hlb_handle* h, Group& G, int SX) {
+    G.SX = SX;
+    std::vector<hlb::Work> works;
+    for (int kz = 0; kz < G.VZ; ++kz)
+        for (size_t m = 0; m < G.members.size(); ++m) {
+            const hlb_config& c = h->cfg[G.members[m]];
+            for (int xa = 0; xa < c.nx; xa += G.SX)
+                for (int y0 = 0; y0 < c.ny; y0 += G.TY) {
+                    hlb::Work w{};
+                    w.inst = (int)m; w.y0 = y0; w.xa = xa; w.xb = std::min(c.nx, xa + G.SX); w.kz = kz;
+                    works.push_back(w);
+                }
+        }
+    G.nworks = (int)works.size();
+    return upload(G.d_works, works);
+}
+
 hlb_status build_group(hlb_handle* h, Group& G) {
     const hlb_config& c0 = h->cfg[G.members[0]];
     G.precision = c0.precision;
@@ -411,20 +430,7 @@ hlb_status build_group(hlb_handle* h, Group& G) {
             const long long rows = xwork / std::max(1LL, (long long)G.TY);
             long long sx = rows / (two_d ? 4096 : 1216);
             sx = std::max(24LL, std::min(512LL, (sx + 5) / 6 * 6));
-            G.SX = (int)sx;
-            std::vector<hlb::Work> works;
-            for (int kz = 0; kz < G.VZ; ++kz)
-                for (size_t m = 0; m < G.members.size(); ++m) {
-                    const hlb_config& c = h->cfg[G.members[m]];
-                    for (int xa = 0; xa < c.nx; xa += G.SX)
-                        for (int y0 = 0; y0 < c.ny; y0 += G.TY) {
-                            hlb::Work w{};
-                            w.inst = (int)m; w.y0 = y0; w.xa = xa; w.xb = std::min(c.nx, xa + G.SX); w.kz = kz;
-                            works.push_back(w);
-                        }
-                }
-            G.nworks = (int)works.size();
-            if ((s = upload(G.d_works, works)) != HLB_OK) return s;
+            if ((s = set_segments(h, G, (int)sx)) != HLB_OK) return s;
             HLB_CUDA(hlb::prepare_march(G.precision, G.adv, G.QX2, G.VY, G.TY));
             HLB_CUDA(hlb::prepare_node());
         }
@@ -1088,6 +1094,65 @@ hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g) {
     if (!e.empty()) return fail(HLB_EINVAL, e);
     hlb::axis_equilibrium(ax, u, T, g);
     return HLB_OK;
+}
+
+hlb_status hlb_autotune(hlb_handle* h, int* segments_out) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    for (cudaStream_t s2 : h->group_stream) HLB_CUDA(cudaStreamSynchronize(s2));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HLB_CUDA(cudaEventCreate(&e0));
+    HLB_CUDA(cudaEventCreate(&e1));
+    hlb_status result = HLB_OK;
+    for (size_t gi = 0; gi < h->groups.size() && result == HLB_OK; ++gi) {
+        Group& G = *h->groups[gi];
+        if (!G.march_ok || group_has_z_force(h, G)) {
+            if (segments_out) segments_out[gi] = 0;
+            continue;
+        }
+        // candidates around the heuristic's segment length, multiples of 6 cells
+        const int base = G.SX;
+        std::vector<int> cand;
+        for (int f : {-2, -1, 0, 1, 2}) {
+            int sx = f < 0 ? base >> (-f) : base << f;
+            sx = std::max(12, std::min(1024, (sx + 5) / 6 * 6));
+            if (std::find(cand.begin(), cand.end(), sx) == cand.end()) cand.push_back(sx);
+        }
+        // each candidate: one untimed and three timed rounds of the three stage
+        // launches; inputs are the state buffer (read only) and the two scratch
+        // buffers, outputs only the scratch buffers, so the state is kept
+        void* S = G.buf[G.cur].p;
+        void* X = G.buf[(G.cur + 1) % 3].p;
+        void* Y = G.buf[(G.cur + 2) % 3].p;
+        const void* ins[3] = {S, X, Y};
+        void* outs[3] = {X, Y, X};
+        int best = base;
+        float best_ms = 0.0f;
+        for (int sx : cand) {
+            hlb_status s = set_segments(h, G, sx);
+            if (s != HLB_OK) { result = s; break; }
+            for (int round = 0; round < 4; ++round) {
+                if (round == 1) HLB_CUDA(cudaEventRecord(e0, h->stream));
+                for (int st = 0; st < 3; ++st)
+                    hlb::launch_march(G.precision, G.adv, G.QX2, G.VY, G.TY, G.dev, (const hlb::Work*)G.d_works.p,
+                                      G.nworks, ins[st], S, outs[st], st, h->stream);
+            }
+            HLB_CUDA(cudaGetLastError());
+            HLB_CUDA(cudaEventRecord(e1, h->stream));
+            HLB_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            HLB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (sx == cand.front() || ms < best_ms) { best_ms = ms; best = sx; }
+        }
+        if (result == HLB_OK) result = set_segments(h, G, best);
+        if (segments_out) segments_out[gi] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }   // it holds the old work list
+    h->have_residual = false;
+    if (result != HLB_OK) return result;
+    return check_device_error(h);
 }
 
 hlb_status hlb_set_options(hlb_handle* h, int use_graphs, int time_kernels) {

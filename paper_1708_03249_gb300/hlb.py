@@ -65,6 +65,7 @@ SIGNATURES = {
     "hlb_get_state_dev": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_set_state_dev": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_set_force_field": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "hlb_autotune": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "hlb_prefetch_state": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_commit_state": (C.c_int, [_P]),
     "hlb_diag": (C.c_int, [_P, _D, _D]),
@@ -222,6 +223,12 @@ class Handle:
 
     def set_state_dev(self, ptr: int, nbytes: int):
         _check(lib().hlb_set_state_dev(self._h, ptr, nbytes))
+
+    def autotune(self):
+        """hlb_autotune: time segment lengths per velocity-set group, keep the fastest; returns them."""
+        out = (C.c_int * len(self.cfgs))(*([-1] * len(self.cfgs)))     # groups <= instances
+        _check(lib().hlb_autotune(self._h, out))
+        return [v for v in out if v >= 0]
 
     def prefetch_state(self, ptr: int, nbytes: int):
         """hlb_prefetch_state: stage the host buffer at ptr (keep it alive and unchanged until the commit has run)."""

@@ -76,3 +76,25 @@ def test_second_prefetch_replaces_the_first_and_bad_size_is_rejected():
         with pytest.raises(hlb.HlbError) as e:
             h.prefetch_state(first.data_ptr(), h.state_bytes - 4)
         assert e.value.status == hlb.HLB_EINVAL
+
+
+def test_autotune_keeps_the_state_and_the_results():
+    # hlb_autotune only changes the segment length of the marching kernels: the
+    # state survives the tuning launches and the steps after it give the same
+    # bits as an untuned handle's (each cell's update does not depend on where
+    # the segments end).  Two velocity sets, 1D and 2D instances.
+    from paper_1708_03249_gb300 import hlb
+    cfgs = [W.make(Qx=8, Qy=8, nx=300, Kn=0.3, ax=-0.2, precision=W.FP32),
+            W.make(Qx=4, Qy=4, nx=90, ny=7, Ly=0.3, Kn=0.5, precision=W.FP32)]
+    with hlb.Handle(cfgs) as a, hlb.Handle(cfgs) as b:
+        for h in (a, b):
+            h.init_equilibrium(1.0, 0.05, 0.0, 1.0)
+            h.step(2)
+        before = a.get_state()
+        seg = a.autotune()
+        assert len(seg) == 2 and all(v >= 12 and v % 6 == 0 for v in seg)
+        np.testing.assert_array_equal(a.get_state(), before)
+        a.step(5)
+        b.step(5)
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
+
