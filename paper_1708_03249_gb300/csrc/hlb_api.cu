@@ -1115,7 +1115,7 @@ hlb_status hlb_autotune(hlb_handle* h, int* segments_out) {
         std::vector<int> cand;
         for (int f : {-2, -1, 0, 1, 2}) {
             int sx = f < 0 ? base >> (-f) : base << f;
-            sx = std::max(12, std::min(1024, (sx + 5) / 6 * 6));
+            sx = std::max(12, std::min(1020, (sx + 5) / 6 * 6));
             if (std::find(cand.begin(), cand.end(), sx) == cand.end()) cand.push_back(sx);
         }
         // each candidate: one untimed and three timed rounds of the three stage
