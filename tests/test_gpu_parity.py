@@ -275,6 +275,48 @@ def test_laguerre_initial_equilibrium_matches_oracle():
     np.testing.assert_allclose(got, np.broadcast_to(ref, got.shape), atol=1e-13 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("Qx,Qy,nx,ny,adv,prec", [
+    (8, 8, 6, 1, W.WENO5, W.FP32),      # shortest WENO-5 channel: line kernel, one partial iteration
+    (8, 8, 6, 5, W.WENO5, W.FP32),      # pair kernel at the fewest rows it takes (5: two strips, one ragged)
+    (8, 8, 6, 3, W.WENO5, W.FP32),      # ny = 3: the generic per-node kernel (halo wraps more than once)
+    (4, 4, 3, 1, W.UPWIND2, W.FP64),    # shortest upwind2 channel, FP64
+    (4, 4, 3, 1, W.UPWIND2, W.FP32),    # ... FP32 (scalar kernel: 8 x 4 slabs)
+])
+def test_minimum_sizes(Qx, Qy, nx, ny, adv, prec):
+    # The smallest grids each kernel accepts: wall ghosts and periodic halos
+    # overlap the interior everywhere.
+    cfg = W.make(Qx=Qx, Qy=Qy, nx=nx, ny=ny, Ly=0.1 * ny, advection=adv, precision=prec, T_left=0.9,
+                 T_right=1.2, Kn=0.4, **W.gravity(0.3, 40.0))
+    got, mom, N, refs = run_pair(cfg, 4, init=(1.0, 0.05, 0.0, 1.0))
+    if prec == W.FP64:
+        _check_fp64(got, refs, 1e-10)
+    else:
+        _check_fp32(got, mom, refs)
+
+
+def test_fp32_collisionless_2d_with_force():
+    # Kn = +inf (no BGK term, 1/tau = 0 in the factor lines) with an oblique force
+    cfg = W.make(Qx=8, Qy=8, nx=20, ny=6, Ly=0.3, precision=W.FP32, T_left=0.8, T_right=1.5,
+                 Kn=math.inf, **W.gravity(0.5, 30.0))
+    got, mom, N, refs = run_pair(cfg, 6)
+    _check_fp32(got, mom, refs)
+
+
+def test_rest_state_is_a_fixed_point():
+    # No force, walls at the gas temperature, f = the rest Maxwellian: the
+    # half-range quadrature represents it exactly, every flux balances and the
+    # BGK term vanishes, so the state stays put (up to FP32 rounding) on the 2D
+    # pair kernel, 1024 velocities.
+    from paper_1708_03249_gb300 import hlb
+    cfg = W.scaled(W.LARGE_2D, nx=64, ny=16, ax=0.0, ay=0.0, az=0.0, T_left=1.3, T_right=1.3)
+    with hlb.Handle(cfg, stream=_stream()) as h:
+        h.init_equilibrium(1.0, 0.0, 0.0, 1.3)
+        f0 = h.get_state().astype(np.float64)
+        h.step(20)
+        f1 = h.get_state().astype(np.float64)
+    assert np.abs(f1 - f0).max() < 1e-5 * np.abs(f0).max()
+
+
 def test_fp32_batched_mixed_instances():
     insts = W.batched_instances(6)
     insts = [W.scaled(c, nx=min(c["nx"], 40)) for c in insts]
