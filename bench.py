@@ -41,7 +41,8 @@ def flops_per_nv_stage(cfg) -> float:
     K_y contractions (2 flop per term), WENO-5 at ~60 flop per spatial axis
     (one face per axis and node-velocity, each shared by two cells), ~20 for
     the moments' share, the equilibrium product, BGK and the RK-3 combination."""
-    qx2, vy = 2 * cfg["Qx"], max(cfg["Qy"], 1)
+    qx2 = cfg["Qx"] if cfg.get("x_basis", 0) == W.X_FULL else 2 * cfg["Qx"]
+    vy = max(cfg["Qy"], 1)
     axes = 2 if cfg["ny"] > 1 else 1
     weno = 60 if cfg["advection"] == W.WENO5 else 4
     return 2 * qx2 + (2 * vy if cfg["Qy"] else 0) + weno * axes + 20
@@ -471,6 +472,8 @@ OTHER_WORKLOADS = {
     "stretched_channel": ("1D FP32 channel, 512 cells tanh A=0.9, Qx=8 x Qy=8, WENO5, Kn=0.1, g=0.5 at 30 deg",
                           lambda: W.channel_1d_stretched(0.1)),
     "box2d": ("2D FP32 box 256x256, Qx=16 x Qy=16, WENO5, Kn=0.05, g=0.2 at 45 deg", lambda: W.BOX_2D),
+    "large2d_upwind2": ("the large 2D channel (1024x512, 16x8x8 velocities, FP32) with 2nd-order upwind "
+                        "advection instead of WENO5", lambda: W.scaled(W.LARGE_2D, advection=W.UPWIND2)),
     "long_channel_q16": ("1D FP32 channel, 131072 cells, Qx=16 x Qy=16 (the batched set's largest slab, "
                          "tensor-core force term), WENO5, Kn=0.1, g=0.36 at 34 deg; 268 MB per copy",
                          lambda: W.make(Qx=16, Qy=16, nx=131072, T_left=1.0, T_right=1.5, ax=-0.3, ay=-0.2,
@@ -506,12 +509,27 @@ def run_other(args):
         ms = e0.elapsed_time(e1)
         n, u, T, q = h.moments()
         nv = h.values
+        # the stage kernels alone (CUDA events around each stage launch, 3 steps)
+        h.set_options(use_graphs=False, time_kernels=True)
+        h.kernel_times(reset=True)
+        h.step(3)
+        torch.cuda.synchronize()
+        kt = h.kernel_times(reset=True)
+    stage_ms = kt["stage_ms"] / max(kt["stage_launches"], 1)
+    bytes_nv = BYTES_PER_NV_STAGE * (2 if cfg["precision"] == W.FP64 else 1)
+    peak, peak_kind = measured_peaks()
+    hbm = nv * bytes_nv / (stage_ms * 1e-3) / 1e9
+    alu = nv * flops_per_nv_stage(cfg) / (stage_ms * 1e-3) / 1e12
+    stage = {"stage_avg_ms": stage_ms, "hbm_gbs": hbm, "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind,
+             "alu_tflops": alu, "alu_frac": alu / (SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12),
+             "per_unit_bytes": bytes_nv, "per_unit_flops": flops_per_nv_stage(cfg)}
     line = {"metric": METRIC, "value": nv * steps / (ms * 1e-3), "unit": "node-velocity updates/s", "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 30), "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if cfg["precision"] == W.FP64 else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "values_per_copy": nv, "segment_cells": segments,
-                       "moments_finite": bool(np.isfinite(n).all() and np.isfinite(T).all())}}
+                       "moments_finite": bool(np.isfinite(n).all() and np.isfinite(T).all())},
+            "stage_kernel": stage}
     print(json.dumps(line), flush=True)
 
 
