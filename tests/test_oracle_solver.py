@@ -409,3 +409,29 @@ def test_stretched_grid():
     # first cell: x(eta) = L/2 + L/(2A) tanh(eta) between -artanh A and -artanh A + d_eta
     de = 2 * math.atanh(0.9) / 512
     assert dx[0] == pytest.approx((math.tanh(-math.atanh(0.9) + de) + 0.9) / 1.8, rel=1e-12)
+
+
+def test_ballistic_reference_profiles():
+    # The free-streaming solution of Sec. V (Eq. "eq:f_bal") that the paper's
+    # convergence test uses as reference, pinned by: zero mass flux everywhere
+    # (its moments against Eq. "eq:bal_npnm"); equal wall temperatures giving
+    # the isothermal barometric profile n = N (g/T) e^{-g x/T} / (1 - e^{-g L/T})
+    # at T = T_w (Eq. "eq:iso_n"); g -> 0 giving the free-molecular state
+    # (uniform n, T = sqrt(T_L T_R)).
+    from oracle.ballistic import ballistic_profiles, epsilon
+    x = np.linspace(0.0, 1.0, 41)
+    n, u, T = ballistic_profiles(x, 1.0, 0.1, 1.4, 0.6)
+    np.testing.assert_allclose(u, 0.0, atol=1e-14)
+    from scipy.integrate import trapezoid
+    xf = np.linspace(0.0, 1.0, 4001)
+    assert trapezoid(ballistic_profiles(xf, 1.0, 0.1, 1.4, 0.6)[0], xf) == pytest.approx(1.0, rel=1e-6)
+    g, Tw = 0.7, 1.3
+    n, u, T = ballistic_profiles(x, 1.0, g, Tw, Tw, N=2.0)
+    np.testing.assert_allclose(n, 2.0 * (g / Tw) * np.exp(-g * x / Tw) / (1 - np.exp(-g / Tw)), rtol=1e-12)
+    np.testing.assert_allclose(T, Tw, rtol=1e-12)
+    # (the turning momentum c(x) = sqrt(g (L - 2x')) makes the limit O(sqrt g))
+    n, u, T = ballistic_profiles(x, 1.0, 1e-16, 0.8, 1.7)
+    np.testing.assert_allclose(n, 1.0, rtol=1e-7)
+    np.testing.assert_allclose(T, math.sqrt(0.8 * 1.7), rtol=1e-7)
+    assert epsilon([1.0, 1.2], [1.0, 1.0]) == pytest.approx(1.0)     # 0.2 / max(0.2, 0.1)
+    assert epsilon([1.0, 1.01], [1.0, 1.0]) == pytest.approx(0.1)    # 0.01 / 0.1 (spread floor)
