@@ -1096,60 +1096,75 @@ hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g) {
     return HLB_OK;
 }
 
+namespace {
+// Timing of one group's candidates; errors leave the group on a valid work list.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+hlb_status tune_group(hlb_handle* h, Group& G, EventPair& ev, int* chosen) {
+    // candidates around the heuristic's segment length, multiples of 6 cells
+    const int base = G.SX;
+    std::vector<int> cand;
+    for (int f : {-2, -1, 0, 1, 2}) {
+        int sx = f < 0 ? base >> (-f) : base << f;
+        sx = std::max(12, std::min(1020, (sx + 5) / 6 * 6));
+        if (std::find(cand.begin(), cand.end(), sx) == cand.end()) cand.push_back(sx);
+    }
+    // each candidate: one untimed and three timed rounds of the three stage
+    // launches; inputs are the state buffer (read only) and the two scratch
+    // buffers, outputs only the scratch buffers, so the state is kept
+    void* S = G.buf[G.cur].p;
+    void* X = G.buf[(G.cur + 1) % 3].p;
+    void* Y = G.buf[(G.cur + 2) % 3].p;
+    const void* ins[3] = {S, X, Y};
+    void* outs[3] = {X, Y, X};
+    int best = base;
+    float best_ms = 0.0f;
+    hlb_status s = HLB_OK;
+    for (int sx : cand) {
+        if ((s = set_segments(h, G, sx)) != HLB_OK) break;
+        for (int round = 0; round < 4; ++round) {
+            if (round == 1) cudaEventRecord(ev.e0, h->stream);
+            for (int st = 0; st < 3; ++st)
+                hlb::launch_march(G.precision, G.adv, G.QX2, G.VY, G.TY, G.dev, (const hlb::Work*)G.d_works.p,
+                                  G.nworks, ins[st], S, outs[st], st, h->stream);
+        }
+        cudaEventRecord(ev.e1, h->stream);
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(ev.e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+        if (e != cudaSuccess) { s = fail(HLB_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(e)); break; }
+        if (sx == cand.front() || ms < best_ms) { best_ms = ms; best = sx; }
+    }
+    // the chosen length (the heuristic's after an error), or no marching at all
+    const hlb_status s2 = set_segments(h, G, s == HLB_OK ? best : base);
+    if (s2 != HLB_OK) G.march_ok = false;
+    *chosen = G.march_ok ? G.SX : 0;
+    return s != HLB_OK ? s : s2;
+}
+}  // namespace
+
 hlb_status hlb_autotune(hlb_handle* h, int* segments_out) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     HLB_CUDA(cudaStreamSynchronize(h->stream));
     for (cudaStream_t s2 : h->group_stream) HLB_CUDA(cudaStreamSynchronize(s2));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    HLB_CUDA(cudaEventCreate(&e0));
-    HLB_CUDA(cudaEventCreate(&e1));
+    EventPair ev;
+    HLB_CUDA(cudaEventCreate(&ev.e0));
+    HLB_CUDA(cudaEventCreate(&ev.e1));
     hlb_status result = HLB_OK;
-    for (size_t gi = 0; gi < h->groups.size() && result == HLB_OK; ++gi) {
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
         Group& G = *h->groups[gi];
-        if (!G.march_ok || group_has_z_force(h, G)) {
-            if (segments_out) segments_out[gi] = 0;
-            continue;
-        }
-        // candidates around the heuristic's segment length, multiples of 6 cells
-        const int base = G.SX;
-        std::vector<int> cand;
-        for (int f : {-2, -1, 0, 1, 2}) {
-            int sx = f < 0 ? base >> (-f) : base << f;
-            sx = std::max(12, std::min(1020, (sx + 5) / 6 * 6));
-            if (std::find(cand.begin(), cand.end(), sx) == cand.end()) cand.push_back(sx);
-        }
-        // each candidate: one untimed and three timed rounds of the three stage
-        // launches; inputs are the state buffer (read only) and the two scratch
-        // buffers, outputs only the scratch buffers, so the state is kept
-        void* S = G.buf[G.cur].p;
-        void* X = G.buf[(G.cur + 1) % 3].p;
-        void* Y = G.buf[(G.cur + 2) % 3].p;
-        const void* ins[3] = {S, X, Y};
-        void* outs[3] = {X, Y, X};
-        int best = base;
-        float best_ms = 0.0f;
-        for (int sx : cand) {
-            hlb_status s = set_segments(h, G, sx);
-            if (s != HLB_OK) { result = s; break; }
-            for (int round = 0; round < 4; ++round) {
-                if (round == 1) HLB_CUDA(cudaEventRecord(e0, h->stream));
-                for (int st = 0; st < 3; ++st)
-                    hlb::launch_march(G.precision, G.adv, G.QX2, G.VY, G.TY, G.dev, (const hlb::Work*)G.d_works.p,
-                                      G.nworks, ins[st], S, outs[st], st, h->stream);
-            }
-            HLB_CUDA(cudaGetLastError());
-            HLB_CUDA(cudaEventRecord(e1, h->stream));
-            HLB_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            HLB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (sx == cand.front() || ms < best_ms) { best_ms = ms; best = sx; }
-        }
-        if (result == HLB_OK) result = set_segments(h, G, best);
-        if (segments_out) segments_out[gi] = best;
+        const bool marches = G.march_ok && !group_has_z_force(h, G);
+        int chosen = marches ? G.SX : 0;
+        if (result == HLB_OK && marches) result = tune_group(h, G, ev, &chosen);
+        if (segments_out) segments_out[gi] = chosen;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }   // it holds the old work list
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }   // it holds the old work lists
     h->have_residual = false;
     if (result != HLB_OK) return result;
     return check_device_error(h);
