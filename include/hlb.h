@@ -184,6 +184,22 @@ hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* 
  * Enqueued on the handle's stream; outputs are device arrays (NULL skips one). */
 hlb_status hlb_moments_noalloc(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev);
 
+/* Asynchronous hlb_moments: enqueues the moments of the current state and
+ * their copies into the caller's host arrays (layout as hlb_moments) on a
+ * result stream of the handle's own, after the work already enqueued on the
+ * handle's stream, and returns at once; the next steps run meanwhile.  The
+ * arrays should be page-locked (pageable memory makes the copies
+ * synchronous) and must stay valid until hlb_moments_wait returns.  Later
+ * calls that would overwrite the state buffer the moments read (a second
+ * step, a graph replay, hlb_set_state, hlb_init_equilibrium, the upload of
+ * hlb_prefetch_state into a swapped-out buffer) or reuse the moments scratch
+ * wait for them on the device.  hlb_moments_wait blocks until the last
+ * request has landed and reports non-finite moments (HLB_ENONFINITE) and
+ * device errors like hlb_moments; with nothing pending it returns HLB_OK.
+ * No counterpart in the paper (host I/O).  Errors: HLB_ENOMEM, HLB_ECUDA. */
+hlb_status hlb_moments_async(hlb_handle* h, double* n, double* u, double* T, double* q);
+hlb_status hlb_moments_wait(hlb_handle* h);
+
 /* Number of nodes and of values in the state (all instances), and the bytes
  * of one state copy.  Any output pointer may be NULL. */
 hlb_status hlb_sizes(const hlb_handle* h, long long* nodes, long long* values, long long* bytes);

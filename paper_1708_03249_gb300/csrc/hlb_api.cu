@@ -72,6 +72,7 @@ struct Group {
     DevBuf d_afield;
     std::vector<char> field_on;
     bool has_field = false;
+    const void* mom_buf = nullptr;           // state buffer read by a pending hlb_moments_async
 };
 
 struct KernelTimer {
@@ -106,6 +107,12 @@ struct hlb_handle {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t stage_free = nullptr, stage_filled = nullptr;
     bool staged = false;
+    // asynchronous moments (hlb_moments_async / hlb_moments_wait): a result
+    // stream of the handle's own; mom_done completes when the last request's
+    // copies have landed; each group records the state buffer it reads
+    cudaStream_t mom_stream = nullptr;
+    cudaEvent_t mom_state = nullptr, mom_done = nullptr;
+    bool mom_pending = false;
     // velocity-set groups after the first step on streams of their own (the
     // groups share no data within a step): forked from and joined back into
     // the handle's stream, also inside a captured graph
@@ -458,6 +465,12 @@ bool group_has_z_force(const hlb_handle* h, const Group& G) {
     return false;
 }
 
+// Make stream s wait, on the device, for the pending asynchronous moments
+// (their kernels read a state buffer and reuse the moments scratch).
+void wait_moments(hlb_handle* h, cudaStream_t s) {
+    if (h->mom_pending) cudaStreamWaitEvent(s, h->mom_done, 0);
+}
+
 // One RK-3 step of one group on stream st: three (node pass, wall, stage)
 // triples; buffer roles rotate.
 void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
@@ -667,6 +680,9 @@ void hlb_destroy(hlb_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     collect_timer(h);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->mom_stream) { cudaStreamSynchronize(h->mom_stream); cudaStreamDestroy(h->mom_stream); }
+    if (h->mom_state) cudaEventDestroy(h->mom_state);
+    if (h->mom_done) cudaEventDestroy(h->mom_done);
     if (h->copy_stream) { cudaStreamSynchronize(h->copy_stream); cudaStreamDestroy(h->copy_stream); }
     if (h->stage_free) cudaEventDestroy(h->stage_free);
     if (h->stage_filled) cudaEventDestroy(h->stage_filled);
@@ -784,6 +800,7 @@ hlb_status hlb_init_equilibrium(hlb_handle* h, double n, double ux, double uy, d
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (!(n > 0) || !(T > 0) || !std::isfinite(n) || !std::isfinite(T) || !std::isfinite(ux) || !std::isfinite(uy))
         return fail(HLB_EINVAL, "need finite n > 0, T > 0, ux, uy");
+    wait_moments(h, h->stream);                         // the state buffer may be read by pending moments
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
         std::vector<double> gx(G.QX2), gy(G.VY), gz(G.VZ), gv(G.V);
@@ -807,6 +824,15 @@ hlb_status hlb_init_equilibrium(hlb_handle* h, double n, double ux, double uy, d
 hlb_status hlb_step(hlb_handle* h, long nsteps) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(HLB_EINVAL, "nsteps < 0");
+    if (h->mom_pending && nsteps > 0) {
+        // one step reads the state the pending moments read and writes the
+        // other two buffers, so it need not wait; more steps reuse that buffer
+        bool conflict = nsteps > 1;
+        for (auto& G : h->groups)
+            if (G->mom_buf && (G->buf[(G->cur + 1) % 3].p == G->mom_buf || G->buf[(G->cur + 2) % 3].p == G->mom_buf))
+                conflict = true;
+        if (conflict) wait_moments(h, h->stream);
+    }
     long left = nsteps;
     while (left > 0) {
         const bool phase0 = std::all_of(h->groups.begin(), h->groups.end(), [](const std::unique_ptr<Group>& G) { return G->cur == 0; });
@@ -837,6 +863,7 @@ hlb_status hlb_step(hlb_handle* h, long nsteps) {
 
 hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    wait_moments(h, h->stream);
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
         double* m = (double*)G.d_mom.p;
@@ -859,6 +886,7 @@ hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* 
 
 hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    wait_moments(h, h->stream);                         // the moments scratch is shared
     {
         hlb_status e = check_device_error(h);
         if (e != HLB_OK) return e;
@@ -906,6 +934,65 @@ hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q
     return HLB_OK;
 }
 
+hlb_status hlb_moments_async(hlb_handle* h, double* n, double* u, double* T, double* q) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (!h->mom_stream) {
+        HLB_CUDA(cudaStreamCreateWithFlags(&h->mom_stream, cudaStreamNonBlocking));
+        HLB_CUDA(cudaEventCreateWithFlags(&h->mom_state, cudaEventDisableTiming));
+        HLB_CUDA(cudaEventCreateWithFlags(&h->mom_done, cudaEventDisableTiming));
+    }
+    // after the work already on the handle's stream (the state to read)
+    HLB_CUDA(cudaEventRecord(h->mom_state, h->stream));
+    HLB_CUDA(cudaStreamWaitEvent(h->mom_stream, h->mom_state, 0));
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        if (!G.h_mom.p) {
+            if (cudaMallocHost(&G.h_mom.p, 16) != cudaSuccess) {
+                cudaGetLastError();
+                G.h_mom.p = nullptr;
+                return fail(HLB_ENOMEM, "cudaMallocHost of the moments flag failed");
+            }
+            G.h_mom.bytes = 16;
+        }
+        double* m = (double*)G.d_mom.p;
+        HLB_CUDA(cudaMemsetAsync(G.dev.nonfinite, 0, sizeof(int), h->mom_stream));
+        hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + G.nnodes, m + 4LL * G.nnodes,
+                            m + 5LL * G.nnodes, 0, h->mom_stream);
+        HLB_CUDA(cudaGetLastError());
+        G.mom_buf = G.buf[G.cur].p;
+        for (size_t k = 0; k < G.members.size(); ++k) {
+            const long long go = h->inst_node_off[G.members[k]];
+            const int j0 = G.node_start[k];
+            const size_t cnt = (size_t)(G.node_start[k + 1] - j0);
+            const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+            if (n) HLB_CUDA(cudaMemcpyAsync(n + go, m + j0, cnt * 8, d2h, h->mom_stream));
+            if (u) HLB_CUDA(cudaMemcpyAsync(u + 3 * go, m + G.nnodes + 3LL * j0, 3 * cnt * 8, d2h, h->mom_stream));
+            if (T) HLB_CUDA(cudaMemcpyAsync(T + go, m + 4LL * G.nnodes + j0, cnt * 8, d2h, h->mom_stream));
+            if (q) HLB_CUDA(cudaMemcpyAsync(q + go, m + 5LL * G.nnodes + j0, cnt * 8, d2h, h->mom_stream));
+        }
+        HLB_CUDA(cudaMemcpyAsync(G.h_mom.p, G.dev.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->mom_stream));
+    }
+    HLB_CUDA(cudaEventRecord(h->mom_done, h->mom_stream));
+    h->mom_pending = true;
+    return HLB_OK;
+}
+
+hlb_status hlb_moments_wait(hlb_handle* h) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (!h->mom_pending) return HLB_OK;
+    HLB_CUDA(cudaEventSynchronize(h->mom_done));
+    h->mom_pending = false;
+    bool finite = true;
+    for (auto& Gp : h->groups) {
+        Gp->mom_buf = nullptr;
+        if (Gp->h_mom.p && *(const int*)Gp->h_mom.p) finite = false;
+    }
+    hlb_status e = check_device_error(h);
+    if (e != HLB_OK) return e;
+    if (!finite) return fail(HLB_ENONFINITE, "non-finite moments in the state");
+    return HLB_OK;
+}
+
 hlb_status hlb_sizes(const hlb_handle* h, long long* nodes, long long* values, long long* bytes) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (nodes) *nodes = h->total_nodes;
@@ -931,6 +1018,7 @@ hlb_status hlb_get_nsteps(const hlb_handle* h, long long* nsteps) {
 static hlb_status state_copy(hlb_handle* h, void* ext, size_t bytes, bool to_ext, cudaMemcpyKind kind, bool sync) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (!ext) return fail(HLB_EINVAL, "buffer is NULL");
+    if (!to_ext) wait_moments(h, h->stream);            // the state buffer may be read by pending moments
     if (bytes != (size_t)(h->total_values * (long long)h->esize))
         return fail(HLB_EINVAL, "state buffer must be exactly " + std::to_string(h->total_values * (long long)h->esize) + " bytes");
     for (auto& Gp : h->groups) {
@@ -985,6 +1073,7 @@ hlb_status hlb_prefetch_state(hlb_handle* h, const void* host_f, size_t bytes) {
     // stream (an earlier commit's copy out of it) has run
     HLB_CUDA(cudaEventRecord(h->stage_free, h->stream));
     HLB_CUDA(cudaStreamWaitEvent(h->copy_stream, h->stage_free, 0));
+    wait_moments(h, h->copy_stream);                    // after a swap the staging buffer may be one they read
     HLB_CUDA(cudaMemcpyAsync(h->stage_buf, host_f, total, cudaMemcpyHostToDevice, h->copy_stream));
     HLB_CUDA(cudaEventRecord(h->stage_filled, h->copy_stream));
     h->staged = true;
@@ -1151,6 +1240,7 @@ hlb_status tune_group(hlb_handle* h, Group& G, EventPair& ev, int* chosen) {
 
 hlb_status hlb_autotune(hlb_handle* h, int* segments_out) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (h->mom_stream) HLB_CUDA(cudaStreamSynchronize(h->mom_stream));
     HLB_CUDA(cudaStreamSynchronize(h->stream));
     for (cudaStream_t s2 : h->group_stream) HLB_CUDA(cudaStreamSynchronize(s2));
     EventPair ev;
@@ -1259,6 +1349,7 @@ hlb_status noalloc_scratch(double** out) {
 extern "C" hlb_status hlb_moments_noalloc(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev,
                                           double* q_dev) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    wait_moments(h, h->stream);
     for (auto& Gp : h->groups)
         if (Gp->nnodes > kNoAllocMaxNodes)
             return fail(HLB_EINVAL, "hlb_moments_noalloc: a group of this handle has " +

@@ -66,6 +66,8 @@ SIGNATURES = {
     "hlb_set_state_dev": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_set_force_field": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "hlb_autotune": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "hlb_moments_async": (C.c_int, [_P, _D, _D, _D, _D]),
+    "hlb_moments_wait": (C.c_int, [_P]),
     "hlb_prefetch_state": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_commit_state": (C.c_int, [_P]),
     "hlb_diag": (C.c_int, [_P, _D, _D]),
@@ -223,6 +225,15 @@ class Handle:
 
     def set_state_dev(self, ptr: int, nbytes: int):
         _check(lib().hlb_set_state_dev(self._h, ptr, nbytes))
+
+    def moments_async(self, n, u, T, q):
+        """hlb_moments_async into caller-owned float64 arrays (page-locked for overlap; keep them alive
+        until moments_wait)."""
+        ptr = lambda a: None if a is None else a.ctypes.data_as(_D)
+        _check(lib().hlb_moments_async(self._h, ptr(n), ptr(u), ptr(T), ptr(q)))
+
+    def moments_wait(self):
+        _check(lib().hlb_moments_wait(self._h))
 
     def autotune(self):
         """hlb_autotune: time segment lengths per velocity-set group, keep the fastest; returns them."""

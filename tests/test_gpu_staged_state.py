@@ -98,3 +98,43 @@ def test_autotune_keeps_the_state_and_the_results():
         b.step(5)
         np.testing.assert_array_equal(a.get_state(), b.get_state())
 
+
+
+def test_async_moments_match_and_overlap_the_next_steps():
+    # hlb_moments_async of each step in a staged-upload loop (the end-to-end
+    # pattern: commit, prefetch the next state, one step, moments) gives the
+    # same moments and the same final state, bit for bit, as the synchronous
+    # loop; a multi-step call after a request (which reuses the buffer the
+    # moments read) is ordered behind it.
+    from paper_1708_03249_gb300 import hlb
+    cfgs = _cfgs("one_group")
+    with hlb.Handle(cfgs) as a, hlb.Handle(cfgs) as b:
+        for h in (a, b):
+            h.init_equilibrium(1.0, 0.02, 0.0, 1.0)
+        base = a.get_state().astype(np.float64)
+        states = [torch.from_numpy((base * W.perturbation(a.values, seed=30 + k, amplitude=0.04))
+                                   .astype(np.float32)).pin_memory() for k in range(4)]
+        nodes = a.nodes
+        outs = [[torch.empty(c * nodes, dtype=torch.float64).pin_memory() for c in (1, 3, 1, 1)] for _ in range(4)]
+        a.prefetch_state(states[0].data_ptr(), a.state_bytes)
+        for k in range(4):
+            a.commit_state()
+            if k + 1 < 4:
+                a.prefetch_state(states[k + 1].data_ptr(), a.state_bytes)
+            a.step(1)
+            a.moments_async(*[t.numpy() for t in outs[k]])
+        a.moments_wait()
+        for k in range(4):
+            b.set_state(states[k].numpy())
+            b.step(1)
+            ref = b.moments()
+            for got, r in zip(outs[k], ref):
+                np.testing.assert_array_equal(got.numpy(), np.asarray(r).reshape(-1))
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
+        # a request, then three steps (the third writes the buffer it reads)
+        a.moments_async(*[t.numpy() for t in outs[0]])
+        a.step(3)
+        b.step(3)
+        a.moments_wait()
+        np.testing.assert_array_equal(a.get_state(), b.get_state())
+        np.testing.assert_array_equal(outs[0][0].numpy(), np.asarray(ref[0]).reshape(-1))
