@@ -11,13 +11,17 @@
  * p_0 = 1 (momenta equal velocities); a = F/m.
  *
  *  - momentum set (App. A): p_x on the half-range Gauss-Hermite quadrature
- *    of order Qx per half (2 Qx values, Sec. IV.B.1, Eq. "eq:hh_pk"); p_y and
- *    p_z on full-range Gauss-Hermite quadratures of even order Qy, Qz
- *    (Sec. IV.A.1; 0 = axis absent);
+ *    of order Qx per half (2 Qx values, Sec. IV.B.1, Eq. "eq:hh_pk"; or, by
+ *    hlb_config.x_basis, the half-range Gauss-Laguerre quadrature or the
+ *    full-range Gauss-Hermite one of the HLB models); p_y and p_z on
+ *    full-range Gauss-Hermite quadratures of even order Qy, Qz (Sec. IV.A.1;
+ *    0 = axis absent);
  *  - force: (grad_p f)_k = sum_k' K_kk' f_k' per axis, with K^h of Eq.
  *    "eq:hh_Kk_hh" along p_x (the paper's main result: the distributional
- *    derivative across the p_x = 0 jump) and K^H of Eq. "eq:H_Kk" along p_y,
- *    p_z;
+ *    derivative across the p_x = 0 jump; K^L of Eq. "eq:hh_Kk_L" for the
+ *    Laguerre set, K^H for the full-range one) and K^H of Eq. "eq:H_Kk" along
+ *    p_y, p_z; the acceleration is uniform per instance, plus an optional
+ *    per-node field (hlb_set_force_field);
  *  - collision: BGK towards feq = n g_x g_y g_z (Eqs. "eq:hh_gk", "eq:H_gk"),
  *    tau = Kn/n (Eq. "eq:tau");
  *  - advection: WENO-5 without epsilon (Sec. IV.C.2, Tab. "weno") or linear
@@ -36,8 +40,9 @@
  *
  * State layout (the "logical state" of get/set_state): for each instance in
  * creation order, f[y][x][kz][jy][ix], ix fastest (2 Qx entries, the first Qx
- * for p_x = +z_k, the next Qx for p_x = -z_k), then jy (max(Qy,1)), kz
- * (max(Qz,1)); element type double for HLB_FP64 handles, float for HLB_FP32.
+ * for p_x = +z_k, the next Qx for p_x = -z_k; Qx entries split Qx/2 + Qx/2 the
+ * same way for the full-range p_x set), then jy (max(Qy,1)), kz (max(Qz,1));
+ * element type double for HLB_FP64 handles, float for HLB_FP32.
  *
  * Errors.  Every call returns an hlb_status; nothing aborts.  On failure
  * hlb_last_error() returns a message describing the most recent failing call
