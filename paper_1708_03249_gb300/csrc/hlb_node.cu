@@ -451,13 +451,30 @@ cudaError_t prepare_node() {
     return cudaFuncSetAttribute(sums_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
 }
 
+// Blocks of `func` resident on the whole GPU at once (one wave), at most
+// `want`: a grid-stride kernel then has no partly filled last wave.
+static int one_wave(const void* func, int block, size_t smem, int want) {
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 152;
+    }
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, block, smem) != cudaSuccess || per < 1) per = 1;
+    return want < nsm * per ? (want > 0 ? want : 1) : nsm * per;
+}
+
 // Node pass of a stage: the quadrature sums of every node, then the factor
 // lines.  The sums live in the first 8 R of each node's factor line slot of
 // an auxiliary buffer (g.sums).
 void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t st) {
     const size_t es = precision == HLB_FP64_ ? 8 : 4;
     const size_t smem_a = 4 * (g.V + g.VY * g.VZ) * es;
-    const int blocks_a = (g.nnodes + 7) / 8 < 152 * 16 ? (g.nnodes + 7) / 8 : 152 * 16;
+    const int want_a = (g.nnodes + 7) / 8;
+    const int blocks_a = precision == HLB_FP64_
+                             ? one_wave(reinterpret_cast<const void*>(&sums_kernel<double>), 256, smem_a, want_a)
+                             : one_wave(reinterpret_cast<const void*>(&sums_kernel<float>), 256, smem_a, want_a);
     const int nrec = 5 * g.Nx + 1;
     const int nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
     const int ncoef = 2 * (g.Nx + 1) + (g.Ny + 1) + (g.Nz + 1);
