@@ -17,6 +17,10 @@ quadrature  half-range Hermite polynomials and quadrature (Sec. IV.B.1, App. B,
 model       the discrete force matrices K^h (Eq. "eq:hh_Kk_hh") and K^H
             (Eq. "eq:H_Kk"), the projected equilibria (Eqs. "eq:hh_gk",
             "eq:H_gk") and the direct-product velocity set (App. A).
+highorder   the half-range quadrature and K^h at orders up to 200 (the
+            HHLB(20;200) model of Sec. V) by the Golub-Welsch recurrence of the
+            Cholesky-factorised Hankel matrix in mpmath (2.5 Q + 60 digits).
+ballistic   the free-streaming reference profiles of Sec. V and eps_max.
 solver      grid (Eqs. "eq:x_eta", "eq:etai"), WENO-5 without epsilon
             (Sec. IV.C.2, Tab. "weno"), 2nd-order upwind, diffuse-reflection
             walls (Sec. IV.C.3), BGK with tau = Kn/n (Eq. "eq:tau"), the TVD

@@ -90,3 +90,55 @@ def test_gauss_hermite_matches_numpy(Q):
     np.testing.assert_allclose(to_f64(d["z"]), x, rtol=1e-13, atol=1e-14)
     np.testing.assert_allclose(to_f64(d["w"]), w / math.sqrt(2 * math.pi), rtol=1e-12)
     assert np.abs(to_f64(d["z"])).max() < 2 * math.sqrt(Q)   # envelope +-2 sqrt(Q)
+
+
+# --- orders up to the paper's HHLB(20;200) (oracle/highorder.py) ---------------------
+@pytest.mark.parametrize("Q", [4, 16, 32])
+def test_highorder_route_matches_the_80_digit_route(Q):
+    # Two independent constructions (monomial coefficients in Decimal; the
+    # Golub-Welsch recurrence in mpmath): nodes, weights and K^h agree to the
+    # last FP64 bit.
+    from oracle.highorder import half_range_hermite_hp, hh_force_matrix_hp
+    from oracle.model import hh_force_matrix
+    hp, dec = half_range_hermite_hp(Q), half_range_hermite(Q)
+    np.testing.assert_allclose([float(x) for x in hp["z"]], to_f64(dec["z"]), rtol=1e-15)
+    np.testing.assert_allclose([float(x) for x in hp["w"]], to_f64(dec["w"]), rtol=1e-14)
+    K0 = hh_force_matrix(Q)
+    np.testing.assert_allclose(hh_force_matrix_hp(Q), K0, atol=1e-14 * np.abs(K0).max())
+
+
+@pytest.mark.slow
+def test_highorder_quadrature_at_order_200():
+    # HHLB(20;200)'s half-range quadrature (Sec. V): exact on z^s omega(z) for
+    # every s < 2Q = 400 (relative to mu_s, at the working precision), all
+    # nodes inside the 2.5 sqrt(Q) envelope of the paper's Fig. "fig:hh_hyp",
+    # positive weights summing to mu_0 = 1/2.
+    import mpmath as mp
+    from oracle.highorder import half_moment_mp, half_range_hermite_hp
+    Q = 200
+    d = half_range_hermite_hp(Q)
+    z, w = d["z"], d["w"]
+    with mp.workdps(d["dps"]):
+        worst = max(abs(mp.fsum(wk * zk ** s for zk, wk in zip(z, w)) / half_moment_mp(s) - 1) for s in range(2 * Q))
+        assert worst < mp.mpf(10) ** -300
+        assert abs(mp.fsum(w) - mp.mpf(1) / 2) < mp.mpf(10) ** -300
+    assert all(x > 0 for x in w)
+    assert 0 < float(z[0]) and float(z[-1]) < 2.5 * Q ** 0.5
+    assert all(float(z[k]) < float(z[k + 1]) for k in range(Q - 1))
+
+
+def test_highorder_force_matrix_identities():
+    # K^h at Q = 64 from the recurrence-based route: per column, mass
+    # (sum_k K = 0), momentum (sum_k p_k K = -1) and the derivative of the rest
+    # Maxwellian (K w = -p w), each relative to the column's magnitude (the
+    # entries span 30 orders of magnitude at this order).
+    from oracle.highorder import half_range_hermite_hp, hh_force_matrix_hp
+    Q = 64
+    d = half_range_hermite_hp(Q)
+    K = hh_force_matrix_hp(Q)
+    z = np.array([float(x) for x in d["z"]])
+    w = np.array([float(x) for x in d["w"]])
+    p, W = np.concatenate([z, -z]), np.concatenate([w, w])
+    assert (np.abs(K.sum(axis=0)) / np.abs(K).sum(axis=0)).max() < 1e-14
+    assert (np.abs((p[:, None] * K).sum(axis=0) + 1) / np.abs(p[:, None] * K).sum(axis=0)).max() < 1e-14
+    assert np.abs(K @ W + p * W).max() < 1e-12 * np.abs(p * W).max()
