@@ -92,12 +92,13 @@ def test_gauss_hermite_matches_numpy(Q):
     assert np.abs(to_f64(d["z"])).max() < 2 * math.sqrt(Q)   # envelope +-2 sqrt(Q)
 
 
-# --- orders up to the paper's HHLB(20;200) (oracle/highorder.py) ---------------------
+# --- orders up to the paper's HHLB(20;200) (oracle/highorder.py; needs mpmath) ----
 @pytest.mark.parametrize("Q", [4, 16, 32])
 def test_highorder_route_matches_the_80_digit_route(Q):
     # Two independent constructions (monomial coefficients in Decimal; the
     # Golub-Welsch recurrence in mpmath): nodes, weights and K^h agree to the
     # last FP64 bit.
+    pytest.importorskip("mpmath")
     from oracle.highorder import half_range_hermite_hp, hh_force_matrix_hp
     from oracle.model import hh_force_matrix
     hp, dec = half_range_hermite_hp(Q), half_range_hermite(Q)
@@ -113,7 +114,7 @@ def test_highorder_quadrature_at_order_200():
     # every s < 2Q = 400 (relative to mu_s, at the working precision), all
     # nodes inside the 2.5 sqrt(Q) envelope of the paper's Fig. "fig:hh_hyp",
     # positive weights summing to mu_0 = 1/2.
-    import mpmath as mp
+    mp = pytest.importorskip("mpmath")
     from oracle.highorder import half_moment_mp, half_range_hermite_hp
     Q = 200
     d = half_range_hermite_hp(Q)
@@ -132,6 +133,7 @@ def test_highorder_force_matrix_identities():
     # (sum_k K = 0), momentum (sum_k p_k K = -1) and the derivative of the rest
     # Maxwellian (K w = -p w), each relative to the column's magnitude (the
     # entries span 30 orders of magnitude at this order).
+    pytest.importorskip("mpmath")
     from oracle.highorder import half_range_hermite_hp, hh_force_matrix_hp
     Q = 64
     d = half_range_hermite_hp(Q)
