@@ -35,7 +35,21 @@ import numpy as np
 from scipy.special import erf as _erf
 
 from .quadrature import (PREC, _ctx, dec_inv_sqrt_2pi, dec_pi, gauss_hermite, gauss_laguerre_half,
-                         half_range_hermite, poly_eval, to_f64)
+                         half_hermite_coeffs, half_range_hermite, poly_eval, to_f64)
+
+# Orders above this come from oracle/highorder.py (the 80-digit monomial route
+# of quadrature.half_range_hermite loses about 2.5 digits per order).
+HH_DECIMAL_MAX_Q = 32
+
+
+def half_range_nodes(Q: int) -> dict:
+    """Nodes z and weights w (Decimal, ascending) of the half-range Hermite
+    quadrature of order Q: the 80-digit route up to Q = 32, the stored or
+    mpmath tables of ``highorder.half_range_data`` beyond."""
+    if Q <= HH_DECIMAL_MAX_Q:
+        return half_range_hermite(Q)
+    from . import highorder
+    return highorder.half_range_data(Q)
 
 
 # ----------------------------------------------------------------------------
@@ -43,6 +57,9 @@ from .quadrature import (PREC, _ctx, dec_inv_sqrt_2pi, dec_pi, gauss_hermite, ga
 # ----------------------------------------------------------------------------
 @lru_cache(maxsize=None)
 def hh_force_matrix(Q: int) -> np.ndarray:
+    if Q > HH_DECIMAL_MAX_Q:
+        from . import highorder
+        return highorder.hh_force_matrix_rec(Q)
     d = half_range_hermite(Q)
     C, z, w = d["C"], d["z"], d["w"]
     with _ctx():
@@ -211,9 +228,11 @@ def _polyval_asc(coeffs, x):
 
 @lru_cache(maxsize=None)
 def hh_phi_table_dec(Q: int, N: int):
-    """Phi_s^N(z_k) = sum_{l=s}^N h_{l,s} h_l(z_k) (Eq. "eq:Phi_def"), Decimal, [k][s]."""
-    d = half_range_hermite(Q)
-    C, z = d["C"], d["z"]
+    """Phi_s^N(z_k) = sum_{l=s}^N h_{l,s} h_l(z_k) (Eq. "eq:Phi_def"), Decimal, [k][s].
+    Only the coefficients of h_0 .. h_N enter (the rows of the Cholesky inverse
+    do not depend on how many are formed)."""
+    C = half_hermite_coeffs(N + 1)
+    z = half_range_nodes(Q)["z"]
     with _ctx():
         out = []
         for zk in z:
@@ -247,8 +266,7 @@ def _hh_equilibrium_node(Q: int, N: int, u: float, T: float):
     larger than their sum (|Phi_s^N| reaches 1e11 at Q = 16), so FP64 would
     lose up to nine digits; 80-digit arithmetic returns g_k correctly rounded.
     """
-    d = half_range_hermite(Q)
-    w = d["w"]
+    w = half_range_nodes(Q)["w"]
     Phi = hh_phi_table_dec(Q, N)
     Pp, _, Ps = p_polys(N)
     with _ctx():
@@ -286,7 +304,7 @@ def hh_equilibrium(Q: int, N: int, u, T, tol: float = 1e-12) -> np.ndarray:
         raise ValueError("0 <= N < Q")
     u = np.asarray(u, dtype=np.float64)
     T = np.broadcast_to(np.asarray(T, dtype=np.float64), u.shape)
-    w = to_f64(half_range_hermite(Q)["w"])
+    w = to_f64(half_range_nodes(Q)["w"])
     Phi = hh_phi_table(Q, N)                         # (Q, N+1)
     Pp, _, Ps = p_polys(N)
     zeta = u / np.sqrt(2.0 * T)
@@ -381,8 +399,8 @@ class VelocitySet:
             self.Kx = hl_force_matrix(Qx)
             self.QH = Qx
         else:
-            zx = to_f64(half_range_hermite(Qx)["z"])
-            wx = to_f64(half_range_hermite(Qx)["w"])
+            zx = to_f64(half_range_nodes(Qx)["z"])
+            wx = to_f64(half_range_nodes(Qx)["w"])
             self.px = np.concatenate([zx, -zx])
             self.wx = np.concatenate([wx, wx])
             self.Kx = hh_force_matrix(Qx)

@@ -116,15 +116,19 @@ def weno5_weights(s1, s2, s3):
     If any sigma_q is exactly zero, the weights are delta_q renormalised over
     the set of zero sigmas (the limits of delta_q/sigma_q^2 as those sigmas
     vanish); otherwise w_q = (delta_q/sigma_q^2) / sum_r (delta_r/sigma_r^2).
+    The quotients are formed in numpy's long double (exponent range to
+    1e4932 on x86 and Arm): a nonzero sigma below 1e-154 would overflow
+    delta_q/sigma_q^2 in FP64.
     """
     s = (np.asarray(s1, float), np.asarray(s2, float), np.asarray(s3, float))
     z = [si == 0.0 for si in s]
     anyz = z[0] | z[1] | z[2]
     with np.errstate(divide="ignore", invalid="ignore"):
-        wt = [np.where(anyz, np.where(z[q], _DELTA[q], 0.0), _DELTA[q] / (s[q] * s[q]))
+        wt = [np.where(anyz, np.where(z[q], _DELTA[q], 0.0),
+                       np.longdouble(_DELTA[q]) / (s[q].astype(np.longdouble) ** 2))
               for q in range(3)]
     tot = wt[0] + wt[1] + wt[2]
-    return wt[0] / tot, wt[1] / tot, wt[2] / tot
+    return tuple((wt[q] / tot).astype(np.float64) for q in range(3))
 
 
 def weno5_face(a, b, c, d, e):
@@ -136,6 +140,15 @@ def weno5_face(a, b, c, d, e):
     F1 = a / 3.0 - 7.0 * b / 6.0 + 11.0 * c / 6.0
     F2 = -b / 6.0 + 5.0 * c / 6.0 + d / 3.0
     F3 = c / 3.0 + 5.0 * d / 6.0 - e / 6.0
+    # The weights of Eq. "eq:weno5_omega" are invariant under f -> c f (each
+    # sigma_q scales as c^2), so the sigmas are formed from the stencil times
+    # the power of two 2^-k that brings its largest magnitude into [1/2, 1):
+    # exact in FP64, and sigma_q^2 stays in range for populations as small as
+    # the 5e-221 weights of the Q = 200 quadrature.
+    m = np.maximum(np.maximum(np.maximum(np.abs(a), np.abs(b)), np.maximum(np.abs(c), np.abs(d))), np.abs(e))
+    k = np.maximum(np.frexp(m)[1], -1020)
+    sc = np.ldexp(1.0, -k)
+    a, b, c, d, e = a * sc, b * sc, c * sc, d * sc, e * sc
     s1 = 13.0 / 12.0 * (a - 2 * b + c) ** 2 + 0.25 * (a - 4 * b + 3 * c) ** 2
     s2 = 13.0 / 12.0 * (b - 2 * c + d) ** 2 + 0.25 * (b - d) ** 2
     s3 = 13.0 / 12.0 * (c - 2 * d + e) ** 2 + 0.25 * (3 * c - 4 * d + e) ** 2

@@ -144,3 +144,54 @@ def test_highorder_force_matrix_identities():
     assert (np.abs(K.sum(axis=0)) / np.abs(K).sum(axis=0)).max() < 1e-14
     assert (np.abs((p[:, None] * K).sum(axis=0) + 1) / np.abs(p[:, None] * K).sum(axis=0)).max() < 1e-14
     assert np.abs(K @ W + p * W).max() < 1e-12 * np.abs(p * W).max()
+
+
+def test_stored_order_200_tables_match_the_mpmath_construction():
+    # tests/golden/half_range_hermite_q200.txt (written by
+    # tests/golden/make_half_range_tables.py from oracle.highorder) holds the
+    # 560-digit tables rounded to 40 digits.
+    mp = pytest.importorskip("mpmath")
+    from oracle.highorder import half_range_hermite_hp, read_store, store_path
+    Q = 200
+    st = read_store(store_path(Q))
+    d = half_range_hermite_hp(Q)
+    with mp.workdps(60):
+        for key in ("z", "w"):
+            assert max(abs(mp.mpf(str(x)) / y - 1) for x, y in zip(st[key], d[key])) < mp.mpf(10) ** -38
+        for key in ("a", "b"):
+            assert max(abs(mp.mpf(str(x)) / y - 1) for x, y in zip(st[key], d[key][:Q + 1])) < mp.mpf(10) ** -38
+        assert abs(mp.mpf(str(st["h0"])) / d["h0"] - 1) < mp.mpf(10) ** -38
+
+
+@pytest.mark.parametrize("Q", [16, 64])
+def test_fp64_force_matrix_from_the_recurrence_matches_mpmath(Q):
+    # hh_force_matrix_rec (FP64 values h_l(z_k) by the recurrence) against the
+    # mpmath evaluation of the same formula, per column.
+    pytest.importorskip("mpmath")
+    from oracle.highorder import hh_force_matrix_hp, hh_force_matrix_rec
+    K, ref = hh_force_matrix_rec(Q), hh_force_matrix_hp(Q)
+    assert (np.abs(K - ref) / np.abs(ref).max(axis=0)[None, :]).max() < 1e-12
+
+
+def test_order_200_velocity_set_reproduces_moments_and_derivatives():
+    # The oracle's HHLB(20;200) set (stored tables, no mpmath): the order-20
+    # projection of a Maxwellian keeps n, u and T (Eq. "eq:hh_gk" preserves
+    # the moments up to order N), K^h acts as -d/dp on moments (sum_k p_k^s
+    # (K f)_k = -s sum_k p_k^(s-1) f_k for s <= 3: integration by parts with
+    # the jump at p = 0 included), and K^h annihilates nothing of the mass.
+    from oracle.model import VelocitySet
+    vs = VelocitySet(200, Nx=20)
+    assert vs.V == 400 and vs.px.max() < 2.5 * 200 ** 0.5
+    for u, T in ((0.0, 1.0), (0.3, 0.7), (-0.5, 1.6)):
+        f = vs.g_x(np.array(u), np.array(T))
+        n = f.sum()
+        j = (vs.px * f).sum()
+        E = (vs.px ** 2 * f).sum()
+        assert n == pytest.approx(1.0, rel=1e-13)
+        assert j / n == pytest.approx(u, abs=1e-13)
+        assert E / n - (j / n) ** 2 == pytest.approx(T, rel=1e-13)
+        Kf = vs.Kx @ f
+        for s in range(4):
+            lhs = (vs.px ** s * Kf).sum()
+            rhs = -s * (vs.px ** (s - 1) * f).sum() if s else 0.0
+            assert lhs == pytest.approx(rhs, abs=1e-12 * max(1.0, abs(rhs)))

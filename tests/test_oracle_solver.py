@@ -435,3 +435,23 @@ def test_ballistic_reference_profiles():
     np.testing.assert_allclose(T, math.sqrt(0.8 * 1.7), rtol=1e-7)
     assert epsilon([1.0, 1.2], [1.0, 1.0]) == pytest.approx(1.0)     # 0.2 / max(0.2, 0.1)
     assert epsilon([1.0, 1.01], [1.0, 1.0]) == pytest.approx(0.1)    # 0.01 / 0.1 (spread floor)
+
+
+def test_weno_face_is_homogeneous_down_to_tiny_populations():
+    # Eq. "eq:weno5_omega": the weights depend on ratios of sigmas only, so the
+    # face value scales with the stencil.  Scaling by a power of two is exact
+    # in FP64, also at 2^-700 (populations of the Q = 200 set reach 5e-221,
+    # where sigma^2 of the raw values would underflow); a stencil spanning 300
+    # orders of magnitude still gives finite weights (delta/sigma^2 beyond the
+    # FP64 range) that pick the flattest sub-stencil.
+    rng = np.random.default_rng(5)
+    cells = rng.uniform(0.5, 2.0, size=(5, 64))
+    F = weno5_face(*cells)
+    for k in (-700, -300, 200):
+        np.testing.assert_array_equal(weno5_face(*(np.ldexp(cells, k))), np.ldexp(F, k))
+    st = np.array([1.0, 0.5, 1e-100, 3e-100, 2e-100])
+    got = weno5_face(*st)
+    # sigma_1, sigma_2 = O(1), sigma_3 = O(1e-200): delta_3/sigma_3^2 ~ 1e400,
+    # so the third candidate takes the whole weight
+    F3 = st[2] / 3.0 + 5.0 * st[3] / 6.0 - st[4] / 6.0
+    assert np.isfinite(got) and got == pytest.approx(F3, rel=1e-12)
