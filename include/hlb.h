@@ -83,9 +83,11 @@ enum { HLB_X_HALF_RANGE = 0, HLB_X_FULL_RANGE = 1, HLB_X_HALF_LAGUERRE = 2 };
 
 /* One channel instance.  Field order and types are part of the ABI. */
 typedef struct {
-    int Qx;              /* half-range order per half, 1..32 (2 Qx values of p_x)          */
+    int Qx;              /* half-range order per half, 1..32 (2 Qx values of p_x); up to
+                            200 on the half-range Hermite axis with HLB_FP64 (the
+                            HHLB(20;200) model of Sec. V: weights down to 5e-221)    */
     int Qy, Qz;          /* full-range orders: 0 (axis absent) or even 2..32 (Sec. IV.A.1) */
-    int Nx_eq, Ny_eq, Nz_eq; /* equilibrium orders N (0 <= N < Q); -1 => Q - 1            */
+    int Nx_eq, Ny_eq, Nz_eq; /* equilibrium orders N (0 <= N < Q, N <= 31); -1 => Q - 1    */
     int nx, ny;          /* cells: nx >= 6 (WENO5) or >= 3 (upwind2) between the walls;
                             ny >= 1 periodic cells in y (ny = 1: 1D channel)               */
     double Lx, Ly;       /* channel width (walls at x = 0, Lx) and periodic length in y   */
@@ -268,7 +270,7 @@ hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, dou
 
 /* One momentum axis built on the host (no handle, no device work): half == 1
  * gives the half-range Hermite axis of order Q (2Q points, Eq. "eq:hh_pk",
- * K^h of Eq. "eq:hh_Kk_hh"), half == 2 the half-range Gauss-Laguerre axis
+ * K^h of Eq. "eq:hh_Kk_hh", Q <= 200), half == 2 the half-range Gauss-Laguerre axis
  * (2Q points, K^L of Eq. "eq:hh_Kk_L", Q <= 16), half == 0 the full-range
  * Gauss-Hermite axis of even order Q (Q points, K^H of Eq. "eq:H_Kk").  p and
  * w have the axis' point count, K its square (row-major [k][k']); any pointer
@@ -276,7 +278,8 @@ hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, dou
 hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K);
 
 /* Equilibrium g_x(u, T) (2Qx values) of a velocity set, computed on the host
- * by the same per-node routine the kernels use (FP64).  No handle needed. */
+ * by the same per-node routine the kernels use (FP64).  No handle needed.
+ * Nx_eq (-1: Qx - 1) must be at most 31; HLB_EINVAL otherwise. */
 hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g);
 
 /* Enable (1) / disable (0) CUDA-graph replay in hlb_step, and per-launch

@@ -61,6 +61,8 @@ struct Group {
     DevBuf d_mom;                            // moments scratch: 6 doubles per node
     PinnedBuf h_mom;                         // pinned word for the non-finite flag (hlb_moments), first use
     DevBuf d_Td, d_invdx, d_wscale, d_coef, d_works, d_err, d_recf, d_Tf, d_sums;
+    DevBuf d_KxT, d_KxJ;                     // FP64 Kx transposed and its jump factors (kx_global groups only)
+    int vchunks = 1;                         // CTAs per node of the generic stage kernel
     hlb::GroupDev dev{};
     int block = 256, grid = 1;
     size_t smem = 0;
@@ -126,7 +128,10 @@ namespace {
 
 std::string check_config(const hlb_config& c, int i) {
     auto bad = [&](const char* what) { return "instance " + std::to_string(i) + ": " + what; };
-    if (c.Qx < 1 || c.Qx > hlb::kMaxQ) return bad("Qx must be in [1, 32]");
+    if (c.Qx < 1 || c.Qx > hlb::kMaxQHalf) return bad("Qx must be in [1, 32], or up to 200 for the half-range Hermite axis");
+    if (c.Qx > hlb::kMaxQ && c.x_basis == HLB_X_HALF_RANGE && c.precision != HLB_FP64)
+        return bad("Qx > 32 needs HLB_FP64 (the weights fall below the FP32 range)");
+    if (c.Qx > hlb::kMaxQ && c.x_basis != HLB_X_HALF_RANGE) return bad("Qx must be in [1, 32]");
     if (c.x_basis != HLB_X_HALF_RANGE && c.x_basis != HLB_X_FULL_RANGE && c.x_basis != HLB_X_HALF_LAGUERRE)
         return bad("x_basis must be HLB_X_HALF_RANGE, HLB_X_FULL_RANGE or HLB_X_HALF_LAGUERRE");
     if (c.x_basis == HLB_X_HALF_LAGUERRE && c.Qx > hlb::kMaxQLaguerre) return bad("Gauss-Laguerre Qx must be in [1, 16]");
@@ -134,6 +139,8 @@ std::string check_config(const hlb_config& c, int i) {
     for (int q : {c.Qy, c.Qz})
         if (q < 0 || q > hlb::kMaxQ || (q % 2)) return bad("Qy, Qz must be 0 or even in [2, 32]");
     if (c.Nx_eq >= c.Qx || c.Nx_eq < -1) return bad("Nx_eq must be -1 or in [0, Qx - 1]");
+    if ((c.Nx_eq < 0 ? c.Qx - 1 : c.Nx_eq) >= hlb::kMaxN)
+        return bad("Nx_eq must be at most 31 (give it explicitly when Qx > 32)");
     if (c.Qy && (c.Ny_eq >= c.Qy || c.Ny_eq < -1)) return bad("Ny_eq must be -1 or in [0, Qy - 1]");
     if (c.Qz && (c.Nz_eq >= c.Qz || c.Nz_eq < -1)) return bad("Nz_eq must be -1 or in [0, Qz - 1]");
     if (c.advection != HLB_WENO5 && c.advection != HLB_UPWIND2) return bad("advection must be HLB_UPWIND2 or HLB_WENO5");
@@ -233,6 +240,10 @@ void fill_dev(Group& G) {
     d.node_start = (const int*)G.d_node_start.p;
     d.row_start = (const int*)G.d_row_start.p;
     d.K = G.d_K.p; d.p = G.d_p.p; d.pd = (const double*)G.d_pd.p; d.Tt = G.d_T.p;
+    d.KxT = (const double*)G.d_KxT.p;
+    d.KxJ = (const double*)G.d_KxJ.p;
+    d.kx_global = G.d_KxT.p ? 1 : 0;
+    d.vchunks = G.vchunks;
     d.rec = (const double*)G.d_rec.p; d.dx = (const double*)G.d_dx.p;
     d.gw = G.d_gw.p; d.nw = (double*)G.d_nw.p;
     d.Td = (const double*)G.d_Td.p;
@@ -376,6 +387,19 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     if ((s = upload_real(G.d_invdx, invdx, G.precision)) != HLB_OK) return s;
     if ((s = upload_real(G.d_wscale, wscale, G.precision)) != HLB_OK) return s;
     if ((s = upload_real(G.d_K, K, G.precision)) != HLB_OK) return s;
+    if (G.QX2 > 2 * hlb::kMaxQ) {
+        if (G.tx.jc.size() != (size_t)G.QX2) return fail(HLB_EUNSUPPORTED, "large p_x sets need a half-range axis");
+        // Kx beyond the shared-memory budget of the generic stage kernel
+        // (400 x 400 doubles at Qx = 200): transposed, so that the threads of a
+        // warp read consecutive entries of one column
+        std::vector<double> KT((size_t)G.QX2 * G.QX2);
+        for (int i = 0; i < G.QX2; ++i)
+            for (int j = 0; j < G.QX2; ++j) KT[(size_t)j * G.QX2 + i] = G.tx.K[(size_t)i * G.QX2 + j];
+        if ((s = upload(G.d_KxT, KT)) != HLB_OK) return s;
+        std::vector<double> J(G.tx.jc);
+        J.insert(J.end(), G.tx.jd.begin(), G.tx.jd.end());
+        if ((s = upload(G.d_KxJ, J)) != HLB_OK) return s;
+    }
     if ((s = upload_real(G.d_p, p, G.precision)) != HLB_OK) return s;
     if ((s = upload(G.d_pd, p)) != HLB_OK) return s;
     if ((s = upload_real(G.d_T, T, G.precision)) != HLB_OK) return s;
@@ -444,16 +468,27 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     }
     fill_dev(G);
 
-    // launch shape of the stage kernel
-    G.block = std::min(256, std::max(32, ((G.V + 31) / 32) * 32));
-    G.smem = hlb::stage_smem_bytes(G.dev, G.precision, G.block);
-    if (G.smem > 200 * 1024) return fail(HLB_EUNSUPPORTED, "velocity set too large for the stage kernel's shared memory");
-    HLB_CUDA(hlb::prepare_stage(G.precision, G.adv, G.smem));
+    // launch shape of the stage kernel.  With Kx in global memory each
+    // velocity's force term is a 2Qx-term dot product (FP64), so the velocities
+    // of a node are split over several CTAs (about 64 each, enough CTAs for two
+    // per SM); the CTAs of one node form its moments redundantly.
     int per_sm = 1, dev = 0, nsm = 1;
     HLB_CUDA(cudaGetDevice(&dev));
     HLB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    G.vchunks = 1;
+    if (G.d_KxT.p) {
+        const int by_size = (G.V + 63) / 64;
+        const int by_fill = (2 * nsm + G.nnodes - 1) / G.nnodes;
+        G.vchunks = std::max(1, std::min(by_size, by_fill));
+    }
+    fill_dev(G);
+    G.block = std::min(256, std::max(32, ((G.V + G.vchunks - 1) / G.vchunks + 31) / 32 * 32));
+    G.smem = hlb::stage_smem_bytes(G.dev, G.precision, G.block);
+    if (G.smem > 200 * 1024) return fail(HLB_EUNSUPPORTED, "velocity set too large for the stage kernel's shared memory");
+    HLB_CUDA(hlb::prepare_stage(G.precision, G.adv, G.smem));
     HLB_CUDA(hlb::stage_occupancy(G.precision, G.adv, G.block, G.smem, &per_sm));
-    G.grid = std::max(1, std::min(G.nnodes, nsm * std::max(1, per_sm)));
+    const long long items = (long long)G.nnodes * G.vchunks;
+    G.grid = (int)std::max(1LL, std::min(items, (long long)nsm * std::max(1, per_sm)));
     return HLB_OK;
 }
 
@@ -1167,7 +1202,8 @@ hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, dou
 
 hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K) {
     hlb::AxisTables ax;
-    std::string e = half ? hlb::build_half_axis(Q, Q - 1, ax, half == 2) : hlb::build_full_axis(Q, Q - 1, ax);
+    const int N = std::min(Q - 1, hlb::kMaxN - 1);          // p, w and K do not depend on N
+    std::string e = half ? hlb::build_half_axis(Q, std::max(N, 0), ax, half == 2) : hlb::build_full_axis(Q, N, ax);
     if (!e.empty()) return fail(HLB_EINVAL, e);
     if (p) std::copy(ax.p.begin(), ax.p.end(), p);
     if (w) std::copy(ax.w.begin(), ax.w.end(), w);
@@ -1178,8 +1214,10 @@ hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K) {
 hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g) {
     if (!g) return fail(HLB_EINVAL, "g is NULL");
     if (!(T > 0) || !std::isfinite(u) || !std::isfinite(T)) return fail(HLB_EINVAL, "need finite u and T > 0");
+    const int N = Nx_eq < 0 ? Qx - 1 : Nx_eq;
+    if (N >= hlb::kMaxN) return fail(HLB_EINVAL, "Nx_eq must be at most 31");
     hlb::AxisTables ax;
-    std::string e = hlb::build_half_axis(Qx, Nx_eq < 0 ? Qx - 1 : Nx_eq, ax);
+    std::string e = hlb::build_half_axis(Qx, N, ax);
     if (!e.empty()) return fail(HLB_EINVAL, e);
     hlb::axis_equilibrium(ax, u, T, g);
     return HLB_OK;

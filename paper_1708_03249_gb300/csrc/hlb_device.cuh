@@ -12,13 +12,26 @@ constexpr double kSqrt2Pi = 2.5066282746310005024157652848110;
 template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 
+// 2^-k with m = x 2^k, x in [1/2, 1) (k clamped so that the result is finite).
+__device__ __forceinline__ double pow2_inverse(double m) {
+    int k;
+    frexp(m, &k);
+    return ldexp(1.0, -max(k, -1020));
+}
+__device__ __forceinline__ float pow2_inverse(float m) {
+    int k;
+    frexpf(m, &k);
+    return ldexpf(1.0f, -max(k, -120));
+}
+
 // WENO-5 face value per unit velocity for a positive velocity: (a..e) are the
 // values at cells i-2..i+2 of face i+1/2 (Sec. IV.C.2).  No epsilon: the
 // weights are delta_q/sigma_q^2 normalised, or, if any sigma_q vanishes,
 // delta_q over the vanishing set (Tab. "weno").
-//  - The sigmas are formed from the stencil values divided by their largest
-//    magnitude (the weights do not change under a common scaling), so that
-//    small populations do not underflow sigma in FP32.
+//  - The sigmas are formed from the stencil values times the power of two
+//    that brings their largest magnitude into [1/2, 1) (the weights do not
+//    change under a common scaling, and a power of two scales exactly), so
+//    that small populations do not underflow sigma.
 //  - delta_q/sigma_q^2 is evaluated as delta_q (sigma_min/sigma_q)^2, the
 //    same ratios multiplied by sigma_min^2: every factor lies in [0, 1], so
 //    nothing overflows, and a sigma far above sigma_min underflows to a zero
@@ -30,7 +43,7 @@ __device__ __forceinline__ R weno5_face(R a, R b, R c, R d, R e) {
     const R F3 = (R(2) * c + R(5) * d - e) * R(1.0 / 6.0);
     const R m = rmax(rmax(rmax(rabs(a), rabs(b)), rmax(rabs(c), rabs(d))), rabs(e));
     if (m == R(0)) return R(0);
-    const R r = R(1) / m;
+    const R r = pow2_inverse(m);
     const R A = a * r, B = b * r, C = c * r, Dd = d * r, E = e * r;
     const R t1 = A - R(2) * B + C, t2 = A - R(4) * B + R(3) * C;
     const R t3 = B - R(2) * C + Dd, t4 = B - Dd;

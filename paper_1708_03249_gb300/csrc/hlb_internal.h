@@ -14,8 +14,10 @@ constexpr int HLB_UPWIND2_ = 0, HLB_WENO5_ = 1;
 constexpr int HLB_FP64_ = 0, HLB_FP32_ = 1;
 
 constexpr int kMaxQ = 32;          // largest quadrature order per axis
+constexpr int kMaxQHalf = 200;     // half-range Hermite p_x (the HHLB(20;200) model): FP64 beyond kMaxQ
 constexpr int kMaxQLaguerre = 16;  // half-range Gauss-Laguerre: beyond, weights < 1e-22 and |p| > 50
 constexpr int kMaxN = kMaxQ;       // largest equilibrium order + 1
+constexpr int kStableRecurrenceN = 12;   // host half-range projections above this order by quadrature
 
 // One momentum axis of the direct-product velocity set (App. A).
 struct AxisTables {
@@ -35,6 +37,10 @@ struct AxisTables {
     // half-range families: omega(0) and d_{l+1} of p_{l+1}' = d_{l+1} p_l - omega(0) p_{l+1}(0) sum ...
     double om0 = 0.0;
     std::vector<double> dcoef;
+    // half-range families: the jump term of K, -omega(0)/2 w_k s_k Phi0(z_k) Phi0(z_k'),
+    // as c_k = -omega(0)/2 w_k s_k Phi0(z_k) and d_k' = Phi0(z_k') (2Q each); it is
+    // the whole of every cross-half block
+    std::vector<double> jc, jd;
 };
 
 // Build the tables of a half-range (p_x) or full-range (p_y, p_z) axis.
@@ -90,6 +96,12 @@ struct GroupDev {
     const int* node_start;   // [ninst + 1]
     const int* row_start;    // [ninst + 1]
     const void* K;           // R: Kx [QX2^2], Ky [VY^2], Kz [VZ^2] concatenated
+    const double* KxT;       // FP64 Kx transposed, [i'][i]: read from global memory by the
+                             // generic stage kernel when Kx does not fit in shared memory
+    const double* KxJ;       // FP64 [2][QX2]: c_k, d_k of the rank-one cross-half blocks
+                             // K[k][k'] = c_k d_k' (k, k' on opposite halves; kx_global)
+    int kx_global;           // 1: Kx is not staged in shared memory (KxT is read instead)
+    int vchunks;             // CTAs per node of the generic stage kernel (velocity ranges)
     const void* p;           // R: px [QX2], py [VY], pz [VZ]
     const double* pd;        // FP64 copies of px, py, pz
     const void* Tt;          // R: Tx [Qx (Nx+1)], Ty [VY (Ny+1)], Tz [VZ (Nz+1)]

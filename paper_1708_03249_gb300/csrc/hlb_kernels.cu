@@ -31,13 +31,14 @@ struct SmemLayout {
     size_t offK, offP, offT, offF, offG;      // in R elements
     size_t offD;                              // in bytes (8-aligned)
     int nRec, nCoef;
+    int nJ;                                   // doubles: per-fibre cross-half sums (kx_global)
     size_t bytes;
 };
 
 template <typename R>
 __host__ __device__ inline SmemLayout smem_layout(const GroupDev& g, int nwarps) {
     SmemLayout L;
-    L.nK = g.QX2 * g.QX2 + g.VY * g.VY + g.VZ * g.VZ;
+    L.nK = (g.kx_global ? 0 : g.QX2 * g.QX2) + g.VY * g.VY + g.VZ * g.VZ;
     L.nP = g.QX2 + g.VY + g.VZ;
     L.nT = g.Qx * (g.Nx + 1) + g.VY * (g.Ny + 1) + g.VZ * (g.Nz + 1);
     L.nG = g.QX2 + g.VY + g.VZ;
@@ -50,8 +51,9 @@ __host__ __device__ inline SmemLayout smem_layout(const GroupDev& g, int nwarps)
     L.offD = (rbytes + 15) & ~size_t(15);
     L.nRec = 5 * g.Nx + 1;
     L.nCoef = 2 * (g.Nx + 1) + (g.Ny + 1) + (g.Nz + 1);
-    // doubles: rec, coef, 8 scalars, 5 * nwarps reduction slots
-    L.bytes = L.offD + sizeof(double) * (L.nRec + L.nCoef + 8 + 5 * nwarps);
+    L.nJ = g.kx_global ? 2 * g.VY * g.VZ : 0;
+    // doubles: rec, coef, 8 scalars, 5 * nwarps reduction slots, cross-half sums
+    L.bytes = L.offD + sizeof(double) * (L.nRec + L.nCoef + 8 + 5 * nwarps + L.nJ);
     return L;
 }
 
@@ -119,9 +121,12 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
     double* sCoef = sRec + L.nRec;
     double* sScal = sCoef + L.nCoef;
     double* sRed = sScal + 8;
+    double* sJ = sRed + 5 * nwarps;           // [fibre][2]: sum_{k' in half} d_k' f_k'
 
     const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const R* gK = static_cast<const R*>(g.K);
+    // Kx stays in global memory (read through KxT) when it exceeds the
+    // shared-memory budget; sK then holds Ky and Kz only
+    const R* gK = static_cast<const R*>(g.K) + (g.kx_global ? g.QX2 * g.QX2 : 0);
     const R* gP = static_cast<const R*>(g.p);
     const R* gT = static_cast<const R*>(g.Tt);
     for (int i = tid; i < L.nK; i += bs) sK[i] = gK[i];
@@ -132,7 +137,7 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
 
     const int V = g.V, QX2 = g.QX2, VY = g.VY, VZ = g.VZ, Qx = g.Qx;
     const R* sKx = sK;
-    const R* sKy = sK + QX2 * QX2;
+    const R* sKy = sK + (g.kx_global ? 0 : QX2 * QX2);
     const R* sKz = sKy + VY * VY;
     const R* sPx = sP;
     const R* sPy = sP + QX2;
@@ -142,7 +147,12 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
     const R* sTz = sTy + VY * (g.Ny + 1);
     const R* gw = static_cast<const R*>(g.gw);
 
-    for (int node = blockIdx.x; node < g.nnodes; node += gridDim.x) {
+    // work items: (node, velocity range); one range per node unless Kx is
+    // read from global memory (vchunks > 1)
+    const int nvc = g.vchunks;
+    for (int item = blockIdx.x; item < g.nnodes * nvc; item += gridDim.x) {
+        const int node = item / nvc, chunk = item - node * nvc;
+        const int v0 = (int)((long long)chunk * V / nvc), v1 = (int)((long long)(chunk + 1) * V / nvc);
         const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
         const InstDev I = g.inst[ii];
         const int local = node - I.node_off;
@@ -192,8 +202,11 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
         // 2. equilibrium factors g_x (times n), g_y, g_z
         {
             const int nf = QX2 + VY + VZ;
+            // a velocity range of a 1D set (VY = VZ = 1) needs its own g_x only
+            const bool x_range = nvc > 1 && VY * VZ == 1;
             for (int t = tid; t < nf; t += bs) {
                 double acc = 0.0;
+                if (t < QX2 && x_range && (t < v0 || t >= v1)) continue;
                 if (t < QX2) {
                     const int k = t % Qx, sg = t / Qx;
                     const double* G = sCoef + sg * (g.Nx + 1);
@@ -221,6 +234,22 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
         }
         }  // collide
         __syncthreads();
+        if (g.kx_global) {
+            // K^h = blockdiag(same-half blocks) + the rank-one jump term
+            // c_k d_k' in every block (Eq. "eq:hh_Kk_hh"): the cross-half
+            // blocks enter through one sum per fibre and half
+            const double* jd = g.KxJ + QX2;
+            const int nfib = VY * VZ;
+            for (int fh = warp; fh < 2 * nfib; fh += nwarps) {
+                const int fb = fh >> 1, h = fh & 1;
+                const R* fr = sF + (size_t)fb * QX2 + h * Qx;
+                double acc = 0.0;
+                for (int i = lane; i < Qx; i += 32) acc += jd[h * Qx + i] * (double)fr[i];
+                acc = warp_sum(acc);
+                if (lane == 0) sJ[fh] = acc;
+            }
+            __syncthreads();
+        }
 
         const R inv_tau = collide ? (R)sScal[1] : R(0);
         const R dt = (R)I.dt;
@@ -233,18 +262,36 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
         const R* gwr = gwl + V;
         const int ny = I.ny;
 
-        // 3. per velocity
-        for (int v = tid; v < V; v += bs) {
+        // 3. per velocity of the range
+        for (int v = v0 + tid; v < v1; v += bs) {
             const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
             const R f = sF[v];
             const R feq = collide ? sG[ix] * sG[QX2 + jy] * sG[QX2 + VY + kz] : R(0);
             // force: sum_a a_a (K_a f)
             R force = 0;
             if (ax != R(0)) {
-                const R* Kr = sKx + ix * QX2;
                 const R* fr = sF + (v - ix);
                 R acc = 0;
-                for (int i = 0; i < QX2; ++i) acc += Kr[i] * fr[i];
+                if (g.kx_global) {
+                    // own half: column ix of Kx^T (consecutive threads read
+                    // consecutive entries; four partial sums shorten the
+                    // dependent chain); other half: c_ix times its fibre sum
+                    const int h = ix < Qx ? 0 : 1;
+                    const double* Kc = g.KxT + (size_t)h * Qx * QX2 + ix;
+                    const R* fh = fr + h * Qx;
+                    R a4[4] = {0, 0, 0, 0};
+                    int i = 0;
+                    for (; i + 4 <= Qx; i += 4) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) a4[q] += (R)Kc[(size_t)(i + q) * QX2] * fh[i + q];
+                    }
+                    for (; i < Qx; ++i) a4[0] += (R)Kc[(size_t)i * QX2] * fh[i];
+                    const int fb = (v - ix) / QX2;
+                    acc = (a4[0] + a4[1]) + (a4[2] + a4[3]) + (R)(g.KxJ[ix] * sJ[2 * fb + (1 - h)]);
+                } else {
+                    const R* Kr = sKx + ix * QX2;
+                    for (int i = 0; i < QX2; ++i) acc += Kr[i] * fr[i];
+                }
                 force += ax * acc;
             }
             if (ay != R(0) && g.Qy) {

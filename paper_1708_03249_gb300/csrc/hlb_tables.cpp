@@ -4,8 +4,12 @@
 // Half-range Hermite (App. B, weight omega(z) = exp(-z^2/2)/sqrt(2 pi) on
 // [0, inf), gamma_l = 1): the recurrence coefficients of the orthonormal
 // polynomials h_l come from the Stieltjes procedure run on a discretisation
-// of the weight (composite Gauss-Legendre, 20 nodes per panel of width 1/2),
-// in its orthonormal (Lanczos-like) form.  The Q quadrature points are the
+// of the weight (composite Gauss-Legendre on panels of width 1/2), in its
+// orthonormal (Lanczos-like) form.  The discrete measure must integrate
+// h_l^2 omega, of degree 2l, to rounding: 20 nodes per panel do so for the
+// first 34 terms, 60 up to the 202 terms of Q = 200 (with 20 the coefficients
+// drift from l ~ 50 on, by 1e-3 at l = 100; the procedure itself is not the
+// limit, a reorthogonalised Lanczos run on the same nodes drifts alike).  The Q quadrature points are the
 // eigenvalues of the Jacobi matrix (Sturm bisection, then Newton on h_Q);
 // the weights are the Christoffel numbers 1 / sum_{l<Q} h_l(z_k)^2, equal to
 // Eq. "eq:wk_half".  Full-range Gauss-Hermite (Sec. IV.A.1) uses the known
@@ -81,7 +85,7 @@ struct Recurrence {
 // Discretised Stieltjes procedure for the half-range Gaussian weight; M terms.
 Recurrence half_range_recurrence(int M) {
     const double zmax = 14.0 + 2.5 * std::sqrt((double)M + 2.0);
-    const int per = 20;
+    const int per = M <= 34 ? 20 : 60;
     const double width = 0.5;
     const int panels = (int)std::ceil(zmax / width);
     std::vector<double> gx, gw;
@@ -227,8 +231,8 @@ void absent_axis(AxisTables& out) {
 //            - omega(0)/2 Phi0(z_k) Phi0(z_k') ],
 // and only the last term across halves (Eqs. "eq:hh_Kk_hh", "eq:hh_Kk_L").
 std::string build_half_axis(int Q, int N, AxisTables& out, bool laguerre) {
-    if (Q < 1 || Q > (laguerre ? kMaxQLaguerre : kMaxQ))
-        return laguerre ? "Gauss-Laguerre Qx must be in [1, 16]" : "Qx must be in [1, 32]";
+    if (Q < 1 || Q > (laguerre ? kMaxQLaguerre : kMaxQHalf))
+        return laguerre ? "Gauss-Laguerre Qx must be in [1, 16]" : "Qx must be in [1, 200]";
     if (N < 0 || N >= Q) return "Nx_eq must be in [0, Qx - 1]";
     const Recurrence r = laguerre ? laguerre_recurrence(Q + 2) : half_range_recurrence(Q + 2);
     const double om0 = laguerre ? 1.0 : 1.0 / std::sqrt(2.0 * kPi);
@@ -268,6 +272,12 @@ std::string build_half_axis(int Q, int N, AxisTables& out, bool laguerre) {
             tail[k][l] = acc;
             acc += h0[l] * H[k][l];
         }
+    }
+    out.jc.resize(2 * Q);
+    out.jd.resize(2 * Q);
+    for (int k = 0; k < 2 * Q; ++k) {
+        out.jc[k] = -0.5 * om0 * w[k % Q] * (k < Q ? 1.0 : -1.0) * Phi0[k % Q];
+        out.jd[k] = Phi0[k % Q];
     }
     out.K.assign(4 * Q * Q, 0.0);
     for (int k = 0; k < 2 * Q; ++k) {
@@ -386,6 +396,42 @@ std::string build_full_x_axis(int Q, int N, AxisTables& out) {
     return "";
 }
 
+// G_l = int_0^inf g(p) h_l(p) dp for l <= N (g the Gaussian of mean us and
+// temperature T) by composite Gauss-Legendre quadrature over [0, max(us, 0) +
+// 40 sqrt(T)] (panels of width min(1, sqrt T)/4, 20 nodes each), h_l(p) by
+// the three-term recurrence.  The error is absolute, about eps times the
+// largest term; the integration-by-parts recurrence below instead carries its
+// rounding along a solution that grows about threefold per order (1e-11 of the
+// largest g_k at N = 10, 5e-7 at N = 20, 1e-1 at N = 31 at rest).
+void half_range_projection_quadrature(const AxisTables& ax, double us, double T, double* G) {
+    struct Rule { std::vector<double> x, w; };
+    static const Rule rule = [] { Rule r; gauss_legendre(20, r.x, r.w); return r; }();   // thread-safe init
+    const std::vector<double>& gx = rule.x;
+    const std::vector<double>& gw = rule.w;
+    const int N = ax.N;
+    const double width = 0.25 * std::min(1.0, std::sqrt(T));
+    const double top = std::max(us, 0.0) + 40.0 * std::sqrt(T);
+    const int panels = (int)std::ceil(top / width);
+    const double norm = 1.0 / std::sqrt(2.0 * kPi * T);
+    for (int l = 0; l <= N; ++l) G[l] = 0.0;
+    for (int pnl = 0; pnl < panels; ++pnl) {
+        const double a = pnl * width;
+        for (int i = 0; i < 20; ++i) {
+            const double p = a + 0.5 * width * (1.0 + gx[i]);
+            const double d = p - us;
+            const double wt = 0.5 * width * gw[i] * norm * std::exp(-d * d / (2.0 * T));
+            double hm = 0.0, h = ax.h0[0];
+            G[0] += wt * h;
+            for (int l = 0; l < N; ++l) {
+                const double hn = (ax.ra[l] * p + ax.rb[l]) * h + ax.rc[l] * hm;
+                hm = h;
+                h = hn;
+                G[l + 1] += wt * h;
+            }
+        }
+    }
+}
+
 void axis_equilibrium(const AxisTables& ax, double u, double T, double* g) {
     if (ax.count == 1 && !ax.half && ax.Q == 0) {
         g[0] = 1.0;
@@ -393,7 +439,17 @@ void axis_equilibrium(const AxisTables& ax, double u, double T, double* g) {
     }
     const int N = ax.N;
     double G[kMaxN + 2];
-    if (ax.half) {
+    if (ax.half && N > kStableRecurrenceN) {
+        const int Q = ax.Q;
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            half_range_projection_quadrature(ax, sgn ? -u : u, T, G);
+            for (int k = 0; k < Q; ++k) {
+                double acc = 0.0;
+                for (int l = 0; l <= N; ++l) acc += ax.T[k * (N + 1) + l] * G[l];
+                g[sgn * Q + k] = acc;
+            }
+        }
+    } else if (ax.half) {
         const int Q = ax.Q;
         const double om0 = ax.om0;
         const double g0 = std::exp(-u * u / (2.0 * T)) / std::sqrt(2.0 * kPi * T);

@@ -55,6 +55,19 @@ def channel_1d_stretched(Kn: float, precision: int = FP32) -> dict:
                 Kn=Kn, advection=WENO5, precision=precision, **gravity(0.5, 30.0))
 CHANNEL_1D_STRETCHED_KN = (0.01, 0.1, 1.0, 10.0)
 
+# The paper's ballistic runs (Sec. V): the HHLB(20;200) model (Qx = 200 per
+# half, 400 velocities, equilibrium order N = 20), N_x = 24 cells stretched with
+# A = 0.99, dt = 1e-4, WENO5, FP64, no collisions, gravity g towards the left
+# wall, wall temperatures T_+- = 1 -+ Delta T (T_+ = 1.4, T_- = 0.6 at
+# Delta T = -0.4).  The paper's figure sweeps g in {0.1, 1} x Delta T in
+# {0.6, 0.3, 0, -0.4}: eight independent instances.
+def hhlb_ballistic(g: float, dT: float, Qx: int = 200, Nx_eq: int = 20) -> dict:
+    return make(Qx=Qx, Nx_eq=Nx_eq, nx=24, stretch_A=0.99, Lx=1.0, advection=WENO5, precision=FP64,
+                dt=1e-4, Kn=math.inf, ax=-g, T_left=1.0 - dT, T_right=1.0 + dT)
+HHLB_BALLISTIC_G = (0.1, 1.0)
+HHLB_BALLISTIC_DT = (0.6, 0.3, 0.0, -0.4)
+HHLB_BALLISTIC_SET = [hhlb_ballistic(g, dT) for g in HHLB_BALLISTIC_G for dT in HHLB_BALLISTIC_DT]
+
 # 2D box 256 x 256, Qx = 16 per half x Qy = 16 (512 velocities).
 BOX_2D = make(Qx=16, Qy=16, nx=256, ny=256, Lx=1.0, Ly=1.0, T_left=1.0,
               T_right=1.2, Kn=0.05, advection=WENO5, precision=FP32,

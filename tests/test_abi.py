@@ -33,7 +33,7 @@ def test_version(hlb_lib):
     assert "sm_103a" in hlb.version()
 
 
-@pytest.mark.parametrize("field,value", [("Qx", 0), ("Qx", 33), ("Qy", 3), ("Qz", -2), ("nx", 5),
+@pytest.mark.parametrize("field,value", [("Qx", 0), ("Qx", 33), ("Qx", 201), ("Qy", 3), ("Qz", -2), ("nx", 5),
                                           ("ny", 2), ("Kn", 0.0), ("T_left", -1.0), ("stretch_A", 1.0),
                                           ("advection", 7), ("precision", 3), ("Nx_eq", 4), ("Lx", 0.0),
                                           ("x_basis", 3),
@@ -104,14 +104,74 @@ def test_full_range_axis_matches_oracle(hlb_lib, Q):
 
 
 @pytest.mark.parametrize("Q,u,T,tol", [(4, 0.3, 1.4, 1e-13), (8, -0.4, 0.6, 1e-11), (8, 0.1, 2.0, 1e-11),
-                                       (16, 0.25, 1.3, 1e-7)])
+                                       (16, 0.25, 1.3, 1e-12)])
 def test_equilibrium_recurrence_matches_oracle(hlb_lib, Q, u, T, tol):
-    # The library's orthonormal-basis recurrence (the per-node route of the
-    # kernels) against the oracle's term-by-term Eq. "eq:hh_gk".
+    # The library's host equilibrium against the oracle's term-by-term Eq.
+    # "eq:hh_gk": up to N = 12 the orthonormal-basis recurrence (the per-node
+    # route of the kernels), above it the quadrature projection (Q = 16: N = 15).
     from oracle.model import hh_equilibrium
     g = hlb.equilibrium_x(Q, u, T)
     ref = hh_equilibrium(Q, Q - 1, u, T, tol=0.0)
     np.testing.assert_allclose(g, ref, atol=tol * np.abs(ref).max())
+
+
+# --- the HHLB(20;200) order (Sec. V) ---------------------------------------------
+def _colwise_error(K, ref):
+    return (np.abs(K - ref) / np.abs(ref).max(axis=0)[None, :]).max()
+
+
+def test_order_200_axis_matches_the_stored_oracle_tables(hlb_lib):
+    # Library: discretised Stieltjes in FP64 (60 Gauss-Legendre nodes per
+    # panel beyond 34 terms), Sturm bisection, Christoffel weights.  Oracle:
+    # the 560-digit Hankel/Golub-Welsch tables, stored to 40 digits, and K^h
+    # from them.  K^h spans 110 orders of magnitude within a row, so it is
+    # compared per column and through its action on equilibria.
+    from oracle.model import VelocitySet
+    Q = 200
+    p, w, K = hlb.axis(Q, True)
+    vs = VelocitySet(Q, Nx=20)
+    np.testing.assert_allclose(p, vs.px, rtol=5e-12)
+    np.testing.assert_allclose(w, vs.wx, rtol=5e-12)
+    assert _colwise_error(K, vs.Kx) < 5e-12
+    for u, T in ((0.0, 1.0), (0.2, 0.6), (-0.3, 1.4)):
+        f = vs.g_x(np.array(u), np.array(T))
+        assert np.abs(K @ f - vs.Kx @ f).max() < 2e-10 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("Q", [64, 100])
+def test_high_order_axis_matches_oracle(hlb_lib, Q):
+    pytest.importorskip("mpmath")
+    from oracle.model import VelocitySet
+    p, w, K = hlb.axis(Q, True)
+    vs = VelocitySet(Q, Nx=20)
+    np.testing.assert_allclose(p, vs.px, rtol=1e-12)
+    np.testing.assert_allclose(w, vs.wx, rtol=2e-12)
+    assert _colwise_error(K, vs.Kx) < 5e-12
+
+
+@pytest.mark.parametrize("N", [20, 31])
+@pytest.mark.parametrize("u,T", [(0.0, 1.0), (0.0, 0.6), (0.3, 0.8), (-1.2, 2.0)])
+def test_order_200_equilibrium_matches_oracle(hlb_lib, N, u, T):
+    # N = 20 is the paper's HHLB(20;200); the recurrence route would be off by
+    # 5e-7 (N = 20) and 1e-1 (N = 31) of max g here, the quadrature projection
+    # is not.
+    from oracle.model import hh_equilibrium
+    g = hlb.equilibrium_x(200, u, T, N)
+    ref = hh_equilibrium(200, N, u, T)
+    np.testing.assert_allclose(g, ref, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("kw", [dict(Qx=40, Nx_eq=20, precision=W.FP32),          # weights below FP32
+                                dict(Qx=40, Nx_eq=-1, precision=W.FP64),          # N = 39 > 31
+                                dict(Qx=40, Nx_eq=20, precision=W.FP64, x_basis=W.X_FULL),
+                                dict(Qx=40, Nx_eq=10, precision=W.FP64, x_basis=W.X_LAGUERRE)])
+def test_high_order_config_rules(hlb_lib, kw):
+    cfg = W.make(nx=24, Kn=1.0, **kw)
+    with pytest.raises(hlb.HlbError) as e:
+        hlb.Handle(cfg)
+    assert e.value.status == hlb.HLB_EINVAL
+    with pytest.raises(hlb.HlbError):
+        hlb.equilibrium_x(40, 0.0, 1.0)                  # Nx_eq -1 -> 39 > 31
 
 
 def test_invalid_axis_and_equilibrium_arguments(hlb_lib):

@@ -161,6 +161,41 @@ def test_fp64_q16():
     _check_fp64(got, refs, 5e-8)
 
 
+# --- the HHLB(20;200) model of the ballistic runs (Sec. V) -----------------------
+# 400 velocities, K^h read from global memory (400 x 400 FP64), each node's
+# velocities split over several CTAs; the oracle takes the stored 40-digit
+# order-200 tables.  Tolerance: the library's K^h differs from the oracle's
+# by 1.5e-12 of each column's largest entry, which moves (K f)_k by up to
+# 7e-11 of max f at the slowest velocity; times g dt per stage.
+@pytest.mark.parametrize("g,dT", [(1.0, -0.4), (0.1, 0.6)])
+def test_fp64_hhlb_20_200_ballistic(g, dT):
+    cfg = W.hhlb_ballistic(g, dT)
+    got, mom, N, refs = run_pair(cfg, 40)
+    _check_fp64(got, refs, 1e-11)
+    assert N[0] == pytest.approx(refs[0].total_number(), rel=1e-12)
+    errs = moment_errors(mom, _oracle_moments(refs))
+    assert max(errs.values()) < 1e-11, errs
+
+
+def test_fp64_hhlb_20_200_paper_set_in_one_handle():
+    # the eight (g, Delta T) cases of the paper's figure as instances of one
+    # group: 192 nodes x 400 velocities in one launch per stage
+    got, mom, N, refs = run_pair(W.HHLB_BALLISTIC_SET, 12)
+    _check_fp64(got, refs, 1e-11)
+
+
+@pytest.mark.parametrize("Qx,Qy,Nx_eq,adv", [(200, 4, 12, W.WENO5), (200, 0, 12, W.UPWIND2)])
+def test_fp64_high_order_collisional(Qx, Qy, Nx_eq, adv):
+    # BGK at the order-200 set (the oracle's stored tables; no mpmath on
+    # every machine), also with a p_y axis (1600 velocities, 19 CTAs per
+    # node).  The per-node equilibrium recurrence on the device is accurate
+    # to ~3^N eps: N = 12 keeps it below 1e-10.
+    cfg = W.make(Qx=Qx, Qy=Qy, Nx_eq=Nx_eq, nx=16, stretch_A=0.8, advection=adv, precision=W.FP64,
+                 T_left=0.8, T_right=1.3, Kn=0.3, dt=2e-4, **W.gravity(0.5, 30.0))
+    got, mom, N, refs = run_pair(cfg, 10, init=(1.0, 0.05, 0.0, 1.0))
+    _check_fp64(got, refs, 1e-9)
+
+
 # --- FP32 ------------------------------------------------------------------------
 @pytest.mark.parametrize("Kn", W.CHANNEL_1D_STRETCHED_KN)
 def test_fp32_stretched_channel(Kn):
