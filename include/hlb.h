@@ -11,7 +11,8 @@
  * p_0 = 1 (momenta equal velocities); a = F/m.
  *
  *  - momentum set (App. A): p_x on the half-range Gauss-Hermite quadrature
- *    of order Qx per half (2 Qx values, Sec. IV.B.1, Eq. "eq:hh_pk"; or, by
+ *    of order Qx per half (2 Qx values, Sec. IV.B.1, Eq. "eq:hh_pk"; up to
+ *    the Qx = 200 of the paper's HHLB(20;200) model in FP64; or, by
  *    hlb_config.x_basis, the half-range Gauss-Laguerre quadrature or the
  *    full-range Gauss-Hermite one of the HLB models); p_y and p_z on
  *    full-range Gauss-Hermite quadratures of even order Qy, Qz (Sec. IV.A.1;
@@ -278,8 +279,11 @@ hlb_status hlb_tables(const hlb_handle* h, int inst, double* px, double* py, dou
 hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K);
 
 /* Equilibrium g_x(u, T) (2Qx values) of a velocity set, computed on the host
- * by the same per-node routine the kernels use (FP64).  No handle needed.
- * Nx_eq (-1: Qx - 1) must be at most 31; HLB_EINVAL otherwise. */
+ * in FP64 as the library's wall Maxwellians and hlb_init_equilibrium are:
+ * for Nx_eq <= 12 by the per-node recurrence the kernels use, above by
+ * quadrature of the projection integrals (the recurrence's rounding grows
+ * about threefold per order).  No handle needed.  Nx_eq (-1: Qx - 1) must be
+ * at most 31; HLB_EINVAL otherwise. */
 hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g);
 
 /* Enable (1) / disable (0) CUDA-graph replay in hlb_step, and per-launch

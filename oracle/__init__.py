@@ -19,7 +19,9 @@ model       the discrete force matrices K^h (Eq. "eq:hh_Kk_hh") and K^H
             "eq:H_gk") and the direct-product velocity set (App. A).
 highorder   the half-range quadrature and K^h at orders up to 200 (the
             HHLB(20;200) model of Sec. V) by the Golub-Welsch recurrence of the
-            Cholesky-factorised Hankel matrix in mpmath (2.5 Q + 60 digits).
+            Cholesky-factorised Hankel matrix in mpmath (2.5 Q + 60 digits);
+            order 200 stored to 40 digits (tests/golden), so that the oracle
+            needs no mpmath for it; K^h from the stored recurrence in FP64.
 ballistic   the free-streaming reference profiles of Sec. V and eps_max.
 solver      grid (Eqs. "eq:x_eta", "eq:etai"), WENO-5 without epsilon
             (Sec. IV.C.2, Tab. "weno"), 2nd-order upwind, diffuse-reflection

@@ -1,8 +1,9 @@
 """The C ABI on the host: the library loads, exports every declared symbol,
 rejects bad configurations with HLB_EINVAL, and its host-built tables (an
 independent construction: discretised Stieltjes, Sturm bisection, Christoffel
-weights, the equilibrium recurrence in the orthonormal basis) agree with the
-oracle's 80-digit tables.  No GPU compute is called here."""
+weights, the equilibrium recurrence in the orthonormal basis or, above order
+12, the quadrature projection) agree with the oracle's 80-digit tables and,
+up to order 200, with its high-precision ones.  No GPU compute is called here."""
 import math
 import os
 import re
