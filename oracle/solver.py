@@ -116,19 +116,31 @@ def weno5_weights(s1, s2, s3):
     If any sigma_q is exactly zero, the weights are delta_q renormalised over
     the set of zero sigmas (the limits of delta_q/sigma_q^2 as those sigmas
     vanish); otherwise w_q = (delta_q/sigma_q^2) / sum_r (delta_r/sigma_r^2).
-    The quotients are formed in numpy's long double (exponent range to
-    1e4932 on x86 and Arm): a nonzero sigma below 1e-154 would overflow
-    delta_q/sigma_q^2 in FP64.
+    Where a nonzero sigma is so small (below ~1e-154) that these quotients
+    overflow FP64, they are formed again in numpy's long double (exponent
+    range to 1e4932 on x86 and Arm; only those entries, since long double is
+    a software type on Arm).
     """
     s = (np.asarray(s1, float), np.asarray(s2, float), np.asarray(s3, float))
     z = [si == 0.0 for si in s]
     anyz = z[0] | z[1] | z[2]
-    with np.errstate(divide="ignore", invalid="ignore"):
-        wt = [np.where(anyz, np.where(z[q], _DELTA[q], 0.0),
-                       np.longdouble(_DELTA[q]) / (s[q].astype(np.longdouble) ** 2))
-              for q in range(3)]
-    tot = wt[0] + wt[1] + wt[2]
-    return tuple((wt[q] / tot).astype(np.float64) for q in range(3))
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        wt = [np.where(anyz, np.where(z[q], _DELTA[q], 0.0), _DELTA[q] / (s[q] * s[q])) for q in range(3)]
+        tot = wt[0] + wt[1] + wt[2]
+        out = [wt[q] / tot for q in range(3)]
+    wide = ~np.isfinite(tot)
+    if np.any(wide):
+        sw = [np.asarray(np.broadcast_to(si, wide.shape)[wide], dtype=np.longdouble) for si in s]
+        zw = [si == 0 for si in sw]
+        anyw = zw[0] | zw[1] | zw[2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ww = [np.where(anyw, np.where(zw[q], _DELTA[q], 0.0), np.longdouble(_DELTA[q]) / (sw[q] * sw[q]))
+                  for q in range(3)]
+        totw = ww[0] + ww[1] + ww[2]
+        out = [np.array(np.broadcast_to(o, wide.shape), dtype=np.float64) for o in out]
+        for q in range(3):
+            out[q][wide] = (ww[q] / totw).astype(np.float64)
+    return tuple(out)
 
 
 def weno5_face(a, b, c, d, e):
