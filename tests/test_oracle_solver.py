@@ -126,6 +126,26 @@ def test_homogeneous_force_and_bgk_closed_form(Qx, Qy, Qz, ax, ay, az):
     np.testing.assert_allclose(T, T0, rtol=1e-12)
 
 
+def test_homogeneous_force_and_bgk_closed_form_order_200():
+    # The same closed form with the HHLB(20;200) set of Sec. V (stored tables):
+    # K^h of order 200 and the order-20 projected equilibrium keep n and T and
+    # move u by a t exactly, with 400 velocities whose weights reach 5e-221.
+    s = Solver(Config(Qx=200, Nx_eq=20, nx=3, ax=-0.3, Kn=0.3, dt=0.001))
+    s.init_equilibrium(1.2, 0.1, -0.05, 0.9)
+    rng = np.random.default_rng(3)
+    s.f = s.f * (1 + 0.1 * rng.uniform(-1, 1, s.f.shape))
+    n0, u0, T0, _ = s.moments()
+    for _ in range(20):
+        f = s.f
+        f1 = f + s.dt * s.source(f)
+        f2 = 0.75 * f + 0.25 * f1 + 0.25 * s.dt * s.source(f1)
+        s.f = f / 3 + 2 / 3 * f2 + 2 / 3 * s.dt * s.source(f2)
+    n, u, T, _ = s.moments()
+    np.testing.assert_allclose(n, n0, rtol=1e-13)
+    np.testing.assert_allclose(u, u0 + np.array([-0.3, 0.0, 0.0]) * 20 * s.dt, atol=1e-13)
+    np.testing.assert_allclose(T, T0, rtol=1e-12)
+
+
 @pytest.mark.parametrize("Qx,Qy,Qz", [(4, 0, 0), (8, 4, 0), (6, 4, 4)])
 def test_homogeneous_force_closed_form_full_range_x(Qx, Qy, Qz):
     # The same closed form for the HLB set along p_x (K^H, no jump term).
