@@ -313,6 +313,14 @@ hlb_status hlb_launch_count(hlb_handle* h, long long* launches, int reset);
  * are unaffected.  Synchronises if a CUDA graph has to be re-captured. */
 hlb_status hlb_set_wait_test(hlb_handle* h, int withhold_copies, double wait_limit_s);
 
+/* Test hook of the out-of-memory paths (no counterpart in the paper; process
+ * wide, no handle).  nth > 0 arms it: the nth device or page-locked
+ * allocation the library makes from then on fails as if memory were
+ * exhausted (the call that made it returns HLB_ENOMEM and frees what it had
+ * allocated; a failed hlb_create leaves nothing behind), and the hook
+ * disarms.  nth == 0 disarms it.  Errors: HLB_EINVAL (nth < 0). */
+hlb_status hlb_set_alloc_fail_test(long long nth);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char* hlb_last_error(void);
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -22,6 +23,35 @@ thread_local std::string g_last_error;
 hlb_status fail(hlb_status s, const std::string& msg) {
     g_last_error = msg;
     return s;
+}
+
+// Allocation-failure injection (hlb_set_alloc_fail_test): when armed with
+// n > 0, the n-th device or page-locked allocation from then on fails as if
+// memory were exhausted, and the injection disarms.
+std::atomic<long long> g_alloc_countdown{0};
+
+bool injected_alloc_failure() {
+    long long c = g_alloc_countdown.load();
+    while (c > 0) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc(void** p, size_t bytes) {
+    if (injected_alloc_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
 }
 
 #define HLB_CUDA(expr)                                                                 \
@@ -164,7 +194,7 @@ template <typename T>
 hlb_status upload(DevBuf& b, const std::vector<T>& v) {
     if (b.p) { cudaFree(b.p); b.p = nullptr; }
     size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
-    if (cudaMalloc(&b.p, bytes) != cudaSuccess) return fail(HLB_ENOMEM, "cudaMalloc of tables failed");
+    if (dev_malloc((void**)&b.p, bytes) != cudaSuccess) return fail(HLB_ENOMEM, "cudaMalloc of tables failed");
     if (!v.empty()) HLB_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
     return HLB_OK;
 }
@@ -415,20 +445,20 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     // state buffers
     const size_t bytes = (size_t)G.nvalues * G.esize;
     for (auto& b : G.buf) {
-        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        if (dev_malloc((void**)&b.p, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(HLB_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes for the state failed");
         }
         HLB_CUDA(cudaMemset(b.p, 0, bytes));
     }
-    if (cudaMalloc(&G.d_mom.p, std::max<size_t>((size_t)G.nnodes * 6 * sizeof(double), 16)) != cudaSuccess) {
+    if (dev_malloc((void**)&G.d_mom.p, std::max<size_t>((size_t)G.nnodes * 6 * sizeof(double), 16)) != cudaSuccess) {
         cudaGetLastError();
         return fail(HLB_ENOMEM, "cudaMalloc of moment scratch failed");
     }
     {
         const int ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
-        if (cudaMalloc(&G.d_coef.p, std::max<size_t>((size_t)G.nnodes * ncp * G.esize, 16)) != cudaSuccess ||
-            cudaMalloc(&G.d_sums.p, std::max<size_t>((size_t)G.nnodes * 16 * G.esize, 16)) != cudaSuccess) {
+        if (dev_malloc((void**)&G.d_coef.p, std::max<size_t>((size_t)G.nnodes * ncp * G.esize, 16)) != cudaSuccess ||
+            dev_malloc((void**)&G.d_sums.p, std::max<size_t>((size_t)G.nnodes * 16 * G.esize, 16)) != cudaSuccess) {
             cudaGetLastError();
             return fail(HLB_ENOMEM, "cudaMalloc of the equilibrium factor lines failed");
         }
@@ -637,6 +667,14 @@ extern "C" {
 const char* hlb_last_error(void) { return g_last_error.c_str(); }
 const char* hlb_version(void) { return "libhlb 0.1 (sm_103a)"; }
 
+// Teardown of a handle whose creation failed: the caller's error message is
+// the creation's, not whatever the teardown runs into.
+static void destroy_keeping_error(hlb_handle* h) {
+    const std::string keep = g_last_error;
+    hlb_destroy(h);
+    g_last_error = keep;
+}
+
 hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_handle** out) {
     g_last_error.clear();
     if (!out) return fail(HLB_EINVAL, "out is NULL");
@@ -647,7 +685,9 @@ hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_h
         if (!e.empty()) return fail(HLB_EINVAL, e);
         if (cfg[i].precision != cfg[0].precision) return fail(HLB_EINVAL, "all instances must share precision");
     }
-    std::unique_ptr<hlb_handle> h(new hlb_handle());
+    // a handle that fails half-built is torn down like a finished one
+    // (streams and events included), not only freed
+    std::unique_ptr<hlb_handle, void (*)(hlb_handle*)> h(new hlb_handle(), destroy_keeping_error);
     h->cfg.assign(cfg, cfg + ninst);
     h->precision = cfg[0].precision;
     h->esize = h->precision == HLB_FP64 ? 8 : 4;
@@ -785,7 +825,7 @@ hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const 
     HLB_CUDA(cudaStreamSynchronize(h->stream));
     for (cudaStream_t s2 : h->group_stream) HLB_CUDA(cudaStreamSynchronize(s2));
     if (on && !G->d_afield.p) {
-        if (cudaMalloc(&G->d_afield.p, (size_t)G->nnodes * 3 * sizeof(double)) != cudaSuccess) {
+        if (dev_malloc((void**)&G->d_afield.p, (size_t)G->nnodes * 3 * sizeof(double)) != cudaSuccess) {
             G->d_afield.p = nullptr;
             return fail(HLB_ENOMEM, "cudaMalloc of the acceleration field failed");
         }
@@ -933,7 +973,7 @@ hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
         if (!G.h_mom.p) {
-            if (cudaMallocHost(&G.h_mom.p, 16) != cudaSuccess) {
+            if (host_malloc((void**)&G.h_mom.p, 16) != cudaSuccess) {
                 cudaGetLastError();
                 G.h_mom.p = nullptr;
                 return fail(HLB_ENOMEM, "cudaMallocHost of the moments flag failed");
@@ -982,7 +1022,7 @@ hlb_status hlb_moments_async(hlb_handle* h, double* n, double* u, double* T, dou
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
         if (!G.h_mom.p) {
-            if (cudaMallocHost(&G.h_mom.p, 16) != cudaSuccess) {
+            if (host_malloc((void**)&G.h_mom.p, 16) != cudaSuccess) {
                 cudaGetLastError();
                 G.h_mom.p = nullptr;
                 return fail(HLB_ENOMEM, "cudaMallocHost of the moments flag failed");
@@ -1100,7 +1140,7 @@ hlb_status hlb_prefetch_state(hlb_handle* h, const void* host_f, size_t bytes) {
         HLB_CUDA(cudaEventCreateWithFlags(&h->stage_free, cudaEventDisableTiming));
         HLB_CUDA(cudaEventCreateWithFlags(&h->stage_filled, cudaEventDisableTiming));
     }
-    if (!h->stage_buf && cudaMalloc(&h->stage_buf, total) != cudaSuccess) {
+    if (!h->stage_buf && dev_malloc((void**)&h->stage_buf, total) != cudaSuccess) {
         h->stage_buf = nullptr;
         return fail(HLB_ENOMEM, "cudaMalloc of the staging buffer failed");
     }
@@ -1322,6 +1362,12 @@ hlb_status hlb_launch_count(hlb_handle* h, long long* launches, int reset) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (launches) *launches = h->launches;
     if (reset) h->launches = 0;
+    return HLB_OK;
+}
+
+hlb_status hlb_set_alloc_fail_test(long long nth) {
+    if (nth < 0) return fail(HLB_EINVAL, "nth must be >= 0");
+    g_alloc_countdown.store(nth);
     return HLB_OK;
 }
 

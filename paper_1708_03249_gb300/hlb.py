@@ -78,6 +78,7 @@ SIGNATURES = {
     "hlb_kernel_times": (C.c_int, [_P, _D, _LL, _D, _LL, C.c_int]),
     "hlb_launch_count": (C.c_int, [_P, _LL, C.c_int]),
     "hlb_set_wait_test": (C.c_int, [_P, C.c_int, C.c_double]),
+    "hlb_set_alloc_fail_test": (C.c_int, [C.c_longlong]),
     "hlb_last_error": (C.c_char_p, []),
     "hlb_version": (C.c_char_p, []),
 }
@@ -281,6 +282,11 @@ class Handle:
 
     def set_wait_test(self, withhold_copies: bool, wait_limit_s: float = 0.0):
         _check(lib().hlb_set_wait_test(self._h, int(bool(withhold_copies)), float(wait_limit_s)))
+
+
+def set_alloc_fail_test(nth: int) -> None:
+    """hlb_set_alloc_fail_test: the nth library allocation from now on fails (0 disarms)."""
+    _check(lib().hlb_set_alloc_fail_test(int(nth)))
 
 
 def equilibrium_x(Qx: int, u: float, T: float, Nx_eq: int = -1) -> np.ndarray:
