@@ -150,15 +150,15 @@ def test_high_order_axis_matches_oracle(hlb_lib, Q):
     assert _colwise_error(K, vs.Kx) < 5e-12
 
 
-@pytest.mark.parametrize("N", [20, 31])
-@pytest.mark.parametrize("u,T", [(0.0, 1.0), (0.0, 0.6), (0.3, 0.8), (-1.2, 2.0)])
-def test_order_200_equilibrium_matches_oracle(hlb_lib, N, u, T):
-    # N = 20 is the paper's HHLB(20;200); the recurrence route would be off by
-    # 5e-7 (N = 20) and 1e-1 (N = 31) of max g here, the quadrature projection
-    # is not.
+@pytest.mark.parametrize("Q,N", [(200, 20), (200, 31), (32, 25)])
+@pytest.mark.parametrize("u,T", [(0.0, 1.0), (0.0, 0.6), (0.3, 0.8), (-1.2, 2.0), (0.0, 0.2), (0.5, 9.0)])
+def test_high_order_equilibrium_matches_oracle(hlb_lib, Q, N, u, T):
+    # N = 20 at Q = 200 is the paper's HHLB(20;200); the recurrence route would
+    # be off by 5e-7 (N = 20) and 1e-1 (N = 31) of max g, the quadrature
+    # projection is not, from T = 0.2 to T = 9.
     from oracle.model import hh_equilibrium
-    g = hlb.equilibrium_x(200, u, T, N)
-    ref = hh_equilibrium(200, N, u, T)
+    g = hlb.equilibrium_x(Q, u, T, N)
+    ref = hh_equilibrium(Q, N, u, T)
     np.testing.assert_allclose(g, ref, atol=1e-12 * np.abs(ref).max())
 
 
