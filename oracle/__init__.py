@@ -23,6 +23,8 @@ highorder   the half-range quadrature and K^h at orders up to 200 (the
             order 200 stored to 40 digits (tests/golden), so that the oracle
             needs no mpmath for it; K^h from the stored recurrence in FP64.
 ballistic   the free-streaming reference profiles of Sec. V and eps_max.
+hydrodynamic  the Navier-Stokes (Chapman-Enskog) profiles of Sec. V
+            (Eqs. "eq:NS_temp", "eq:NS_n", "eq:NS_q").
 solver      grid (Eqs. "eq:x_eta", "eq:etai"), WENO-5 without epsilon
             (Sec. IV.C.2, Tab. "weno"), 2nd-order upwind, diffuse-reflection
             walls (Sec. IV.C.3), BGK with tau = Kn/n (Eq. "eq:tau"), the TVD

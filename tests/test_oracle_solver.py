@@ -475,3 +475,53 @@ def test_weno_face_is_homogeneous_down_to_tiny_populations():
     # so the third candidate takes the whole weight
     F3 = st[2] / 3.0 + 5.0 * st[3] / 6.0 - st[4] / 6.0
     assert np.isfinite(got) and got == pytest.approx(F3, rel=1e-12)
+
+
+# --- the Navier-Stokes regime (Sec. V, oracle/hydrodynamic.py) -------------------
+@pytest.mark.parametrize("g,TL,TR", [(0.5, 0.8, 1.2), (1.0, 1.4, 0.6), (0.1, 1.0, 1.0), (0.0, 0.8, 1.2)])
+def test_navier_stokes_profiles_closed_forms(g, TL, TR):
+    # Eqs. "eq:NS_temp", "eq:NS_n": N particles, the wall temperatures at the
+    # walls, T^2 linear (constant heat flux with kappa ~ T), hydrostatic
+    # balance d(nT)/dx = -g n, and the barometric Eq. "eq:iso_n" at equal
+    # wall temperatures; g -> 0 is continuous.
+    from scipy.integrate import quad
+    from oracle.hydrodynamic import ns_profiles
+    N = quad(lambda s: ns_profiles(s, 1.0, g, TL, TR, N=0.7)[0], 0.0, 1.0, epsabs=1e-14, epsrel=1e-13)[0]
+    assert N == pytest.approx(0.7, rel=1e-12)
+    _, Tw = ns_profiles(np.array([0.0, 1.0]), 1.0, g, TL, TR)
+    np.testing.assert_allclose(Tw, [TL, TR], rtol=1e-14)
+    x = np.linspace(0.05, 0.95, 19)
+    n, T = ns_profiles(x, 1.0, g, TL, TR)
+    np.testing.assert_allclose(np.diff(T ** 2) / np.diff(x), TR ** 2 - TL ** 2, rtol=1e-9, atol=1e-12)
+    h = 1e-5
+    (n1, T1), (n0, T0) = ns_profiles(x + h, 1.0, g, TL, TR), ns_profiles(x - h, 1.0, g, TL, TR)
+    np.testing.assert_allclose((n1 * T1 - n0 * T0) / (2 * h), -g * n, rtol=1e-7, atol=1e-9)
+    if TL == TR:
+        Tw = TL
+        iso = g * np.exp(-g * (x - 0.5) / Tw) / (2 * Tw * math.sinh(g / (2 * Tw)))
+        np.testing.assert_allclose(n, iso, rtol=1e-13)
+    if g == 0.0:
+        np.testing.assert_allclose(n, ns_profiles(x, 1.0, 1e-7, TL, TR)[0], rtol=1e-6)
+
+
+@pytest.mark.slow
+def test_oracle_approaches_the_navier_stokes_profiles():
+    # HHLB(3;4), 24 cells, WENO5, g = 0.5, walls at 0.8 and 1.2, Kn = 0.02:
+    # the stationary n and T lie within O(Kn) of Eqs. "eq:NS_n", "eq:NS_temp"
+    # (measured eps = 2.8 % and 5.4 % here; 1.5 % and 2.7 % at Kn = 0.01,
+    # 0.7 % and 1.3 % at Kn = 0.005: first order in Kn, the temperature jump and
+    # Knudsen layers at the walls), and the heat flux approaches Eq. "eq:NS_q".
+    from oracle.ballistic import epsilon
+    from oracle.hydrodynamic import ns_heat_flux, ns_profiles
+    g, TL, TR, Kn = 0.5, 0.8, 1.2, 0.02
+    s = Solver(Config(Qx=4, nx=24, advection="weno5", T_left=TL, T_right=TR, ax=-g, Kn=Kn, cfl=0.5))
+    s.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+    s.step(6000)
+    n, u, T, q = (a.ravel() for a in s.moments())
+    _, xc, dx = grid_x(24, 1.0, 0.0)
+    rn, rT = ns_profiles(xc, 1.0, g, TL, TR, N=float((n * dx).sum()))
+    assert epsilon(n, rn) < 0.04
+    assert epsilon(T, rT) < 0.07
+    assert 0.03 < epsilon(T, rT)                       # not converged past the O(Kn) error
+    q_ns = ns_heat_flux(1.0, Kn, TL, TR)
+    assert np.abs(q[6:-6] - q_ns).max() < 0.25 * abs(q_ns)
