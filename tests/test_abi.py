@@ -125,7 +125,7 @@ def test_order_200_axis_matches_the_stored_oracle_tables(hlb_lib):
     # Library: discretised Stieltjes in FP64 (60 Gauss-Legendre nodes per
     # panel beyond 34 terms), Sturm bisection, Christoffel weights.  Oracle:
     # the 560-digit Hankel/Golub-Welsch tables, stored to 40 digits, and K^h
-    # from them.  K^h spans 110 orders of magnitude within a row, so it is
+    # from them.  K^h spans 112 orders of magnitude within a row, so it is
     # compared per column and through its action on equilibria.
     from oracle.model import VelocitySet
     Q = 200
