@@ -11,7 +11,12 @@
 //                 (Eqs. "eq:hh_Kk_hh", "eq:H_Kk"), BGK with tau = Kn/n,
 //                 WENO-5 / upwind2 fluxes along x (walls: Eq.
 //                 "eq:weno_populate" ghosts) and y (periodic), and the RK-3
-//                 combination; writes the stage output.
+//                 combination; writes the stage output.  It serves the
+//                 shapes the marching kernels do not, among them the
+//                 half-range sets beyond Qx = 32 (the HHLB(20;200) model of
+//                 Sec. V): there K_x stays in global memory, its cross-half
+//                 blocks enter as their rank-one factor, and a node's
+//                 velocities are split over several CTAs.
 #include <cuda_runtime.h>
 
 #include <cmath>
