@@ -183,9 +183,10 @@ hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* 
  * Limits and behaviour:
  *  - each velocity-set group of the handle may have at most 262144 nodes;
  *    larger handles get HLB_EINVAL and nothing is launched;
- *  - the first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress) once; make that first call before any stream
- *    capture on that device;
+ *  - every call looks the array's device address up (cudaGetSymbolAddress,
+ *    which allocates nothing); the first lookup on a device loads the
+ *    library's device code there, so make the first call on a device before
+ *    any stream capture on that device;
  *  - every call shares the one array: calls that overlap on the GPU (other
  *    streams, other handles, other threads) race on it.  The array keeps the
  *    last call's contents; each call overwrites all entries it later reads.

@@ -96,10 +96,6 @@ def hh_force_matrix(Q: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
-# full-range Hermite: K^H  (Eq. "eq:H_Kk")
-# ----------------------------------------------------------------------------
-@lru_cache(maxsize=None)
-# ----------------------------------------------------------------------------
 # half-range Gauss-Laguerre: K^L  (Eq. "eq:hh_Kk_L")
 # ----------------------------------------------------------------------------
 @lru_cache(maxsize=None)
@@ -160,6 +156,10 @@ def hl_equilibrium(Q: int, N: int, u, T) -> np.ndarray:
     return out
 
 
+# ----------------------------------------------------------------------------
+# full-range Hermite: K^H  (Eq. "eq:H_Kk")
+# ----------------------------------------------------------------------------
+@lru_cache(maxsize=None)
 def h_force_matrix(Q: int) -> np.ndarray:
     d = gauss_hermite(Q)
     z, w, He = d["z"], d["w"], d["He"]

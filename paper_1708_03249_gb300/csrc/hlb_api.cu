@@ -8,7 +8,6 @@
 #include <cstring>
 #include <map>
 #include <memory>
-#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1408,23 +1407,16 @@ constexpr long long kNoAllocMaxNodes = 1LL << 18;          // per group: 12 MiB 
 // Shared by every call on a device, kept for the life of the process.
 static __device__ __align__(256) double g_noalloc_scratch[6 * kNoAllocMaxNodes];
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch on the current device (looked up once per
-// device; the host-side name of the array is only a stand-in).
+// Device address of the scratch in the current device's context.  The
+// host-side name of the array is only a stand-in, so the address is looked up
+// on every call: the lookup allocates nothing, and a cached address would go
+// stale if the primary context were reset and the module loaded again.  The
+// first lookup in a context loads the module (lazy loading), which is why the
+// first call on a device must come before any stream capture.
 hlb_status noalloc_scratch(double** out) {
-    int dev = 0;
-    HLB_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(HLB_EUNSUPPORTED, "device ordinal too large");
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        HLB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    HLB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = static_cast<double*>(p);
     return HLB_OK;
 }
 

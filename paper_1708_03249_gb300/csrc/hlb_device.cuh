@@ -529,12 +529,20 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
     return true;
 }
 
-// After a wait ran out: wait, again at most wait_ns, for the phase of the
-// given parity (the bulk copies it tracks) to complete; records nothing.
+// After a wait ran out: wait for the phase of the given parity (the bulk
+// copies it tracks) to complete before the CTA exits, so that no copy the CTA
+// issued lands in shared memory after the CTA is gone.  Callers drain only
+// phases whose byte count was registered (not the ones the test hook
+// withholds); a copy that was issued always completes, normally within
+// microseconds, so the bound here is generous (wait_ns + 1 s) and is only
+// reached if a phase was registered but some of its copies were never issued
+// (a warp that left the loop early), by which time the issued ones have long
+// landed.  Records nothing.
 __device__ __forceinline__ void mbar_drain(unsigned long long* bar, uint32_t parity, unsigned long long wait_ns) {
     const unsigned long long t0 = global_ns();
+    const unsigned long long bound = wait_ns + 1000000000ull;
     while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > wait_ns) return;
+        if (global_ns() - t0 > bound) return;
     }
 }
 

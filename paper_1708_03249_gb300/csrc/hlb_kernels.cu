@@ -169,14 +169,16 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
         // Collisionless instances (Kn = +inf) have no BGK term at all: no
         // moments and no equilibrium are formed for them.
         const bool collide = I.inv_Kn != 0.0;
-        // 1. node values and moment partial sums
-        R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+        // 1. node values and moment partial sums, accumulated in FP64 for
+        // either state precision (T = (E - n|u|^2)/(D n) cancels digits, and
+        // the FP32 state's sums are not compensated here)
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
         for (int v = tid; v < V; v += bs) {
-            const R val = frow[(size_t)x * V + v];
-            sF[v] = val;
+            const R val_r = frow[(size_t)x * V + v];
+            sF[v] = val_r;
             if (!collide) continue;
             const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
-            const R px = sPx[ix], py = sPy[jy], pz = sPz[kz];
+            const double px = sPx[ix], py = sPy[jy], pz = sPz[kz], val = val_r;
             a0 += val;
             a1 += px * val;
             a2 += py * val;

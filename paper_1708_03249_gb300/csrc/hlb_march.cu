@@ -274,9 +274,10 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
         }
     }
     if (*sAbort && t == 0) {
-        // a wait ran out at step xab: let the copies issued since land before the CTA exits
+        // a wait ran out at step xab: let the copies issued since (less a step
+        // the test hook withheld) land before the CTA exits
         for (int s2 = xab - xa; s2 < xb - xa && s2 < xab - xa + kDepth - 1; ++s2)
-            mbar_drain(&bars[s2 % kDepth], (s2 / kDepth) & 1, g.wait_ns);
+            if (!(g.inject_stall && s2 == 1)) mbar_drain(&bars[s2 % kDepth], (s2 / kDepth) & 1, g.wait_ns);
     }
 }
 

@@ -18,10 +18,14 @@ torch = pytest.importorskip("torch")
 
 
 def _dev_moments(h, fn):
-    n = torch.zeros(h.nodes, dtype=torch.float64, device="cuda")
-    u = torch.zeros(3 * h.nodes, dtype=torch.float64, device="cuda")
-    T = torch.zeros(h.nodes, dtype=torch.float64, device="cuda")
-    q = torch.zeros(h.nodes, dtype=torch.float64, device="cuda")
+    # NaN-filled outputs on torch's current stream, which is also the
+    # handle's stream (see below), so the fill is ordered before the copies
+    # and an output that the call failed to write would show as NaN
+    n = torch.full((h.nodes,), float("nan"), dtype=torch.float64, device="cuda")
+    u = torch.full((3 * h.nodes,), float("nan"), dtype=torch.float64, device="cuda")
+    T = torch.full((h.nodes,), float("nan"), dtype=torch.float64, device="cuda")
+    q = torch.full((h.nodes,), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.current_stream().synchronize()
     fn(n.data_ptr(), u.data_ptr(), T.data_ptr(), q.data_ptr())
     torch.cuda.synchronize()
     return [a.cpu().numpy() for a in (n, u, T, q)]
@@ -33,7 +37,7 @@ def test_moments_noalloc_matches_moments_dev_twice():
     cfgs = [W.make(Qx=4, Qy=4, nx=24, Kn=0.3, ax=-0.2, precision=W.FP32),
             W.make(Qx=8, Qy=8, nx=16, Kn=1.0, T_right=1.5, precision=W.FP32),
             W.make(Qx=4, Qy=4, nx=40, Kn=0.1, precision=W.FP32)]
-    with hlb.Handle(cfgs) as h:
+    with hlb.Handle(cfgs, stream=torch.cuda.current_stream().cuda_stream) as h:
         h.init_equilibrium(1.0, 0.1, 0.0, 1.1)
         f = h.get_state().astype(np.float64) * W.perturbation(h.values, seed=4)
         h.set_state(f)
@@ -42,6 +46,7 @@ def test_moments_noalloc_matches_moments_dev_twice():
             ref = _dev_moments(h, h.moments_dev)
             got = _dev_moments(h, h.moments_noalloc)
             for a, b in zip(got, ref):
+                assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
                 np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
             h.step(1)
 
