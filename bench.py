@@ -36,6 +36,19 @@ BYTES_PER_NV_STAGE = 32.0 / 3.0      # FP32: stage 1 reads f^n, writes f1 (8 B);
 SMS, FP32_LANES_PER_SM, MAX_SM_MHZ = 152, 128, 2070.0
 
 
+FORCE_FORMS = {0: "fma", 1: "tf32x3 tensor cores", 2: "split-bf16 tensor cores"}
+PRECISIONS = {"fp32": W.FP32, "tf32x3": W.FP32_TF32X3, "bf16split": W.FP32_BF16SPLIT}
+
+
+def with_precision(cfg, name: str):
+    """The FP32 workload cfg (or list) with the force-term form `name`; FP64 ones unchanged."""
+    if isinstance(cfg, list):
+        return [with_precision(c, name) for c in cfg]
+    if cfg["precision"] == W.FP64:
+        return cfg
+    return dict(cfg, precision=PRECISIONS[name])
+
+
 def flops_per_nv_stage(cfg) -> float:
     """Algorithmic flops of one node-velocity in one RK-3 stage: the K_x and
     K_y contractions (2 flop per term), WENO-5 at ~60 flop per spatial axis
@@ -60,7 +73,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("hlb_pair.cu", "hlb_device.cuh", "hlb_internal.h"):
+    for name in ("hlb_pair.cuh", "hlb_pair.cu", "hlb_device.cuh", "hlb_internal.h"):
         with open(os.path.join(ROOT, "paper_1708_03249_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -163,6 +176,93 @@ def oracle_sample(steps: int = 1, nx: int = 32, ny: int = 32, keep: bool = False
     return out
 
 
+_POOL_SOLVER = None
+
+
+def _pool_init(nx, ny, seed):
+    """Worker set-up (untimed): the oracle's tables and one window's initial state."""
+    global _POOL_SOLVER
+    from oracle.solver import Solver, config_from
+    s = Solver(config_from(window_config(nx, ny)))
+    s.init_equilibrium(1.0, 0.05, -0.02, 1.2)
+    s.f *= W.perturbation(s.f.shape, seed=seed, amplitude=0.02)
+    _POOL_SOLVER = s
+
+
+def _pool_steps(steps):
+    t0, c0 = time.perf_counter(), time.process_time()
+    _POOL_SOLVER.step(steps)
+    return time.perf_counter() - t0, time.process_time() - c0
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: one spawned process per core, each
+    advancing its own nx x ny window of the workload (same velocity set,
+    physics and dt; its own seeded perturbation), all at once.  The oracle's
+    arithmetic is unchanged: the windows are independent problems, so the
+    host's throughput is their node-velocity updates over the slowest one's
+    wall time.  BLAS threads are pinned to one per process."""
+
+    def __init__(self, workers: int = 0, nx: int = 32, ny: int = 32):
+        import multiprocessing as mp
+        self.workers = workers or (os.cpu_count() or 1)
+        self.nx, self.ny = nx, ny
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        ctx = mp.get_context("spawn")
+        self.pools = [ctx.Pool(1, initializer=_pool_init, initargs=(nx, ny, 100 + r)) for r in range(self.workers)]
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        for p in self.pools:                 # wait for every worker's set-up
+            p.apply(time.sleep, (0,))
+        self.V = None
+
+    def run(self, steps: int):
+        """(node-velocity updates/s over all workers, wall seconds, CPU seconds)."""
+        t0 = time.perf_counter()
+        res = [p.apply_async(_pool_steps, (steps,)) for p in self.pools]
+        out = [r.get() for r in res]
+        wall = time.perf_counter() - t0
+        if self.V is None:
+            from oracle.model import VelocitySet
+            c = W.LARGE_2D
+            self.V = VelocitySet(c["Qx"], c["Qy"], c["Qz"]).V
+        nv = self.workers * self.nx * self.ny * self.V * steps
+        return nv / wall, wall, sum(o[1] for o in out)
+
+    def describe(self, steps: int) -> str:
+        return (f"{self.workers} independent {self.nx}x{self.ny}-node windows of the workload's velocity set "
+                f"(one spawned process per host core, os.cpu_count() = {os.cpu_count()}, CPU: {cpu_model()}) "
+                f"x {steps} RK-3 step(s) each, FP64 numpy oracle")
+
+    def close(self):
+        for p in self.pools:
+            p.terminate()
+
+
 def moment_errors(mom, ref) -> dict:
     """L-infinity error of each moment against the FP64 oracle, relative to
     max(max |M_ref|, s_M) with s_n = max n, s_u = sqrt(max T), s_T = max T,
@@ -183,13 +283,15 @@ def run_reference(args):
     if rank != 0:
         return
     total_nv, total_t = 0.0, 0.0
-    desc = ""
-    cores = 1
+    pool = OraclePool()
+    desc = pool.describe(1) + " per timed step"
+    cores = pool.workers
     for i in range(args.warmup + args.steps):
-        rate, secs, desc, cores = oracle_sample(steps=1)
+        rate, secs, _ = pool.run(1)
         if i >= args.warmup:
             total_nv += rate * secs
             total_t += secs
+    pool.close()
     value = total_nv / total_t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "node-velocity updates/s",
@@ -198,7 +300,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": desc},
         "cpu_baseline": {"value": value, "unit": "node-velocity updates/s", "cores": cores,
-                         "kind": "oracle", "sample": desc},
+                         "kind": "oracle", "sample": desc, "cpu_model": cpu_model(),
+                         "os_cpu_count": os.cpu_count()},
         "e2e": {"value": value, "unit": "node-velocity updates/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -253,6 +356,8 @@ def run_gpu(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the oracle's host-core pool (rank 0 at N = 1 only), spawned before any CUDA call
+    pool = OraclePool() if rank == 0 and world == 1 else None
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -264,8 +369,8 @@ def run_gpu(args):
         if dist is not None:
             dist.barrier()
     stream = torch.cuda.Stream()
-    cfg = W.LARGE_2D
-    workload = WORKLOAD
+    cfg = with_precision(W.LARGE_2D, args.precision)
+    workload = WORKLOAD if args.precision == "fp32" else f"{WORKLOAD}_{args.precision}"
     if args.nx or args.ny:        # a smaller grid of the same workload (profiling captures)
         nx = args.nx or cfg["nx"]
         ny = args.ny or cfg["ny"]
@@ -273,6 +378,7 @@ def run_gpu(args):
         workload = f"{WORKLOAD}_grid{nx}x{ny}"
     h = hlb.Handle(cfg, stream=stream.cuda_stream)
     nodes, values, state_bytes = h.nodes, h.values, h.state_bytes
+    force_form = h.force_form(0)
     V = values // nodes
     h.init_equilibrium(1.0, 0.0, 0.0, 1.0)
     segments = h.autotune()              # marching-kernel segment length, timed per group (untimed here)
@@ -371,8 +477,15 @@ def run_gpu(args):
             traffic = prof.get("dram_bytes_per_launch")
     # the same window on the GPU from the oracle's own initial state: the L-inf
     # moment errors of the timed kernels against the FP64 oracle
-    cpu_rate, cpu_secs, cpu_desc, cpu_cores, f0_win, mom_ref = oracle_sample(steps=3, keep=True)
-    with hlb.Handle(window_config(), stream=stream.cuda_stream) as hw:
+    _, _, _, _, f0_win, mom_ref = oracle_sample(steps=3, keep=True)
+    cpu_baseline = None
+    if pool is not None:
+        cpu_rate, _, cpu_sec = pool.run(3)
+        cpu_baseline = {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": pool.workers,
+                        "kind": "oracle", "sample": pool.describe(3), "cpu_model": cpu_model(),
+                        "os_cpu_count": os.cpu_count(), "cpu_seconds": cpu_sec}
+        pool.close()
+    with hlb.Handle(with_precision(window_config(), args.precision), stream=stream.cuda_stream) as hw:
         hw.set_state(f0_win.reshape(-1).astype(np.float32))
         hw.step(3)
         errs = moment_errors(hw.moments(), mom_ref)
@@ -385,11 +498,11 @@ def run_gpu(args):
                    "nodes": nodes, "values_per_copy": values, "precision": "fp32",
                    "advection": "weno5", "parallelism": f"replicas{world}",
                    "l2": f"state ({state_bytes / 1e9:.2f} GB per copy) larger than L2; no flush needed",
-                   "moments_finite": finite, "segment_cells": segments},
+                   "moments_finite": finite, "segment_cells": segments,
+                   "force_term": FORCE_FORMS[force_form]},
         "roofline": roofline_of(achieved, peak, peak_kind, alu_achieved, alu_peak, sm_mhz, traffic,
                                 stage_avg_ms, kt, flop_nv),
-        "cpu_baseline": {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": cpu_cores,
-                         "kind": "oracle", "sample": cpu_desc},
+        "cpu_baseline": cpu_baseline,
         "accuracy": {"moment_linf_rel_err": errs, "bound": 1e-5, "within_bound": max(errs.values()) <= 1e-5,
                      "case": "the cpu_baseline window (32x32 nodes, 3 RK-3 steps) from the oracle's initial "
                              "state, FP32 kernels vs the FP64 oracle"},
@@ -425,7 +538,7 @@ def run_batched(args):
     torch.cuda.set_device(0)
     if not os.path.exists(hlb.LIB_PATH):
         hbuild.build()
-    insts = W.batched_instances(args.ninst)
+    insts = with_precision(W.batched_instances(args.ninst), args.precision)
     stream = torch.cuda.Stream()
     h = hlb.Handle(insts, stream=stream.cuda_stream)
     h.init_equilibrium()
@@ -508,12 +621,13 @@ def run_other(args):
     if not os.path.exists(hlb.LIB_PATH):
         hbuild.build()
     desc, make_cfg = OTHER_WORKLOADS[args.workload]
-    cfgs = make_cfg()
+    cfgs = with_precision(make_cfg(), args.precision)
     cfg = cfgs[0] if isinstance(cfgs, list) else cfgs
     stream = torch.cuda.Stream()
     with hlb.Handle(cfgs, stream=stream.cuda_stream) as h:
         h.init_equilibrium()
         segments = h.autotune()
+        force_form = h.force_form(0)
         h.set_options(use_graphs=True, time_kernels=False)
         h.step(max(args.warmup, 30))
         torch.cuda.synchronize()
@@ -548,6 +662,7 @@ def run_other(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if cfg["precision"] == W.FP64 else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "values_per_copy": nv, "segment_cells": segments,
+                       "force_term": FORCE_FORMS[force_form],
                        "moments_finite": bool(np.isfinite(n).all() and np.isfinite(T).all())},
             "stage_kernel": stage}
     print(json.dumps(line), flush=True)
@@ -566,6 +681,9 @@ def main():
     ap.add_argument("--nx", type=int, default=0, help="profiling: the large 2D workload on a smaller grid")
     ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--fp64-sample", type=int, default=64)
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
+                    help="FP32 workloads: the force term's form (fp32: the library's choice; tf32x3, bf16split: "
+                         "on the tensor cores)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

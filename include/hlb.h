@@ -74,7 +74,23 @@ typedef enum {
 } hlb_status;
 
 enum { HLB_UPWIND2 = 0, HLB_WENO5 = 1 };
-enum { HLB_FP64 = 0, HLB_FP32 = 1 };
+/* Arithmetic (hlb_config.precision).  HLB_FP64: FP64 state and arithmetic.
+ * The other three keep an FP32 state with FP32 bulk arithmetic (advection,
+ * collision, RK-3), compensated FP32 moment sums and an FP64 wall balance;
+ * they differ in the force term a . K f of App. A (Eqs. "eq:hh_Kk_hh",
+ * "eq:H_Kk"), a small dense contraction along p_x and p_y:
+ *  - HLB_FP32: the library picks the form per velocity set and scheme, the
+ *    one measured faster on GB300 (FP32 FMAs; 3xTF32 for the 1D kernel's
+ *    32 x 16 slabs and for the 2D kernel's 16 x 8 slabs with upwind2);
+ *  - HLB_FP32_TF32X3: on the tensor cores as three TF32 products (hi/lo split
+ *    of both operands) with FP32 accumulation;
+ *  - HLB_FP32_BF16SPLIT: on the tensor cores with every operand split into
+ *    three bf16 terms and the six leading products accumulated in FP32.
+ * The tensor-core forms apply to the marching kernels' slabs with 2 Qx and
+ * Qy multiples of 8 (16 x 8 and 32 x 16 values of (p_x, p_y)); other velocity
+ * sets keep the FMA form (hlb_force_form reports the form in use).  All
+ * three keep the moments within 1e-5 of the FP64 solution. */
+enum { HLB_FP64 = 0, HLB_FP32 = 1, HLB_FP32_TF32X3 = 2, HLB_FP32_BF16SPLIT = 3 };
 /* Quadrature along p_x: the half-range Hermite of Sec. IV.B (HHLB models,
  * 2 Qx values), the full-range Gauss-Hermite of Sec. IV.A (HLB models, Qx
  * values, Qx even), the model the paper compares against in Sec. V, or the
@@ -94,7 +110,7 @@ typedef struct {
     double Lx, Ly;       /* channel width (walls at x = 0, Lx) and periodic length in y   */
     double stretch_A;    /* 0: uniform; 0 < A < 1: tanh stretching, Eqs. "eq:x_eta","eq:etai" */
     int advection;       /* HLB_UPWIND2 or HLB_WENO5                                      */
-    int precision;       /* HLB_FP64 or HLB_FP32 (state and bulk arithmetic)              */
+    int precision;       /* HLB_FP64, HLB_FP32, HLB_FP32_TF32X3 or HLB_FP32_BF16SPLIT      */
     double cfl;          /* dt = cfl / (max|p_x|/min dx + [ny>1] max|p_y|/dy) if dt <= 0   */
     double dt;           /* explicit time step if > 0                                     */
     double T_left, T_right;  /* wall temperatures (> 0) at x = 0 and x = Lx               */
@@ -212,6 +228,12 @@ hlb_status hlb_moments_wait(hlb_handle* h);
 /* Number of nodes and of values in the state (all instances), and the bytes
  * of one state copy.  Any output pointer may be NULL. */
 hlb_status hlb_sizes(const hlb_handle* h, long long* nodes, long long* values, long long* bytes);
+
+/* Form of the force term in the stage kernel of instance `inst`'s velocity
+ * set: 0 FP32 (or FP64) FMAs, 1 3xTF32 tensor-core products, 2 split-BF16
+ * tensor-core products (see HLB_FP32_TF32X3 and HLB_FP32_BF16SPLIT).
+ * Errors: HLB_EINVAL. */
+hlb_status hlb_force_form(const hlb_handle* h, int inst, int* form);
 
 /* Time step and step counter of instance `inst`. */
 hlb_status hlb_get_dt(const hlb_handle* h, int inst, double* dt);

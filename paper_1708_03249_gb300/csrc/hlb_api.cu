@@ -1,6 +1,7 @@
 // C ABI of libhlb: handle management, tables upload, RK-3 stepping (eager or
 // replayed from a captured CUDA graph), moments, state I/O and diagnostics.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -72,7 +73,9 @@ struct PinnedBuf {                           // page-locked host memory
 };
 
 struct Group {
-    int precision = HLB_FP32, adv = HLB_WENO5;
+    int precision = HLB_FP32, adv = HLB_WENO5;   // precision: HLB_FP64 or HLB_FP32 (the state's type)
+    int force_request = 0;                   // 0: the library's choice; 1: 3xTF32; 2: split-BF16 (FP32 state)
+    int force_form = 0;                      // resolved: 0 FMA, 1 3xTF32, 2 split-BF16
     int Qx = 0, Qy = 0, Qz = 0, Nx = 0, Ny = 0, Nz = 0;
     bool x_full = false;                     // p_x on the full-range Gauss-Hermite axis
     hlb::AxisTables tx, ty, tz;
@@ -104,6 +107,14 @@ struct Group {
     std::vector<char> field_on;
     bool has_field = false;
     const void* mom_buf = nullptr;           // state buffer read by a pending hlb_moments_async
+};
+
+// Host-side NVTX range (the library's calls and the RK-3 stages they enqueue,
+// for profilers; free when no tool is attached).  Ranges opened while a CUDA
+// graph is captured mark the capture, not the replays.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
 };
 
 struct KernelTimer {
@@ -173,7 +184,9 @@ std::string check_config(const hlb_config& c, int i) {
     if (c.Qy && (c.Ny_eq >= c.Qy || c.Ny_eq < -1)) return bad("Ny_eq must be -1 or in [0, Qy - 1]");
     if (c.Qz && (c.Nz_eq >= c.Qz || c.Nz_eq < -1)) return bad("Nz_eq must be -1 or in [0, Qz - 1]");
     if (c.advection != HLB_WENO5 && c.advection != HLB_UPWIND2) return bad("advection must be HLB_UPWIND2 or HLB_WENO5");
-    if (c.precision != HLB_FP32 && c.precision != HLB_FP64) return bad("precision must be HLB_FP64 or HLB_FP32");
+    if (c.precision != HLB_FP32 && c.precision != HLB_FP64 && c.precision != HLB_FP32_TF32X3 &&
+        c.precision != HLB_FP32_BF16SPLIT)
+        return bad("precision must be HLB_FP64, HLB_FP32, HLB_FP32_TF32X3 or HLB_FP32_BF16SPLIT");
     if (c.nx < (c.advection == HLB_WENO5 ? 6 : 3)) return bad("nx must be >= 6 (WENO5) or >= 3 (upwind2)");
     if (c.ny < 1 || c.ny == 2) return bad("ny must be 1 or >= 3");
     if ((long long)c.nx * c.ny > (1LL << 30)) return bad("nx * ny too large");
@@ -288,6 +301,7 @@ void fill_dev(Group& G) {
     d.use_df = (G.precision == HLB_FP32 && G.Nx <= 15) ? 1 : 0;
     d.wait_ns = kDefaultWaitNs;
     d.inject_stall = 0;
+    d.force_form = G.force_form;
 }
 
 // The marching kernel's work list: one CTA per (p_z slab, instance, strip of
@@ -311,7 +325,8 @@ hlb_status set_segments(hlb_handle* h, Group& G, int SX) {
 
 hlb_status build_group(hlb_handle* h, Group& G) {
     const hlb_config& c0 = h->cfg[G.members[0]];
-    G.precision = c0.precision;
+    G.precision = c0.precision == HLB_FP64 ? HLB_FP64 : HLB_FP32;
+    G.force_request = c0.precision == HLB_FP32_TF32X3 ? 1 : (c0.precision == HLB_FP32_BF16SPLIT ? 2 : 0);
     G.adv = c0.advection;
     G.Qx = c0.Qx; G.Qy = c0.Qy; G.Qz = c0.Qz;
     G.Nx = c0.Nx_eq < 0 ? c0.Qx - 1 : c0.Nx_eq;
@@ -491,7 +506,22 @@ hlb_status build_group(hlb_handle* h, Group& G) {
             long long sx = rows / (two_d ? 4096 : 1216);
             sx = std::max(24LL, std::min(512LL, (sx + 5) / 6 * 6));
             if ((s = set_segments(h, G, (int)sx)) != HLB_OK) return s;
-            HLB_CUDA(hlb::prepare_march(G.precision, G.adv, G.QX2, G.VY, G.TY));
+            // the force term's form: on the tensor cores where the caller
+            // asked for it and the slab tiles into 16 x 8 x 8 blocks; by
+            // default where 3xTF32 measured faster than the FMA loop on a
+            // GB300: the 1D kernel's 32 x 16 slabs (0.412 against 0.523 ms
+            // per stage, 131072 cells) and the 2D kernel's 16 x 8 slabs with
+            // upwind2 (2.06 against 2.39 ms, 1024 x 512 cells, 1024
+            // velocities); with WENO-5 the 2D kernel is issue-bound and the
+            // FMA loop is faster (3.43 against 3.64 ms; 32 x 16: 0.330
+            // against 0.347 ms)
+            G.force_form = 0;
+            if (G.precision == HLB_FP32 && hlb::force_tc_available(G.QX2, G.VY)) {
+                if (G.force_request) G.force_form = G.force_request;
+                else if (G.TY == 1 && G.QX2 * G.VY >= 512) G.force_form = 1;
+                else if (G.TY == 2 && G.adv == HLB_UPWIND2 && G.QX2 * G.VY == 128) G.force_form = 1;
+            }
+            HLB_CUDA(hlb::prepare_march(G.precision, G.adv, G.QX2, G.VY, G.TY, G.force_form));
             HLB_CUDA(hlb::prepare_node());
         }
     }
@@ -538,6 +568,7 @@ void wait_moments(hlb_handle* h, cudaStream_t s) {
 // One RK-3 step of one group on stream st: three (node pass, wall, stage)
 // triples; buffer roles rotate.
 void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
+    static const char* kStageNames[3] = {"RK-3 stage 1", "RK-3 stage 2", "RK-3 stage 3"};
     void* S = G.buf[G.cur].p;
     void* X = G.buf[(G.cur + 1) % 3].p;
     void* Y = G.buf[(G.cur + 2) % 3].p;
@@ -549,6 +580,7 @@ void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
             cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2);
             cudaEventRecord(e0, st_);
         }
+        NvtxRange range(kStageNames[st]);
         const bool march = G.march_ok && !group_has_z_force(h, G);
         if (march) hlb::launch_node(G.precision, G.dev, ins[st], st_);
         hlb::launch_wall(G.precision, G.adv, G.dev, ins[st], st_);
@@ -688,7 +720,7 @@ hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_h
     // (streams and events included), not only freed
     std::unique_ptr<hlb_handle, void (*)(hlb_handle*)> h(new hlb_handle(), destroy_keeping_error);
     h->cfg.assign(cfg, cfg + ninst);
-    h->precision = cfg[0].precision;
+    h->precision = cfg[0].precision == HLB_FP64 ? HLB_FP64 : HLB_FP32;
     h->esize = h->precision == HLB_FP64 ? 8 : 4;
     if (cuda_stream) {
         h->stream = (cudaStream_t)cuda_stream;
@@ -898,6 +930,7 @@ hlb_status hlb_init_equilibrium(hlb_handle* h, double n, double ux, double uy, d
 hlb_status hlb_step(hlb_handle* h, long nsteps) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(HLB_EINVAL, "nsteps < 0");
+    NvtxRange range("hlb_step");
     if (h->mom_pending && nsteps > 0) {
         // one step reads the state the pending moments read and writes the
         // other two buffers, so it need not wait; more steps reuse that buffer
@@ -960,6 +993,7 @@ hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* 
 
 hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    NvtxRange range("hlb_moments");
     wait_moments(h, h->stream);                         // the moments scratch is shared
     {
         hlb_status e = check_device_error(h);
@@ -1080,6 +1114,14 @@ hlb_status hlb_get_dt(const hlb_handle* h, int inst, double* dt) {
     if (inst < 0 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
     const Group* G = h->groups[h->inst_group[inst]].get();
     *dt = G->inst[h->inst_local[inst]].dt;
+    return HLB_OK;
+}
+
+hlb_status hlb_force_form(const hlb_handle* h, int inst, int* form) {
+    if (!h || !form) return fail(HLB_EINVAL, "handle or output is NULL");
+    if (inst < 0 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    const Group& G = *h->groups[h->inst_group[inst]];
+    *form = (G.march_ok && !group_has_z_force(h, G)) ? G.force_form : 0;
     return HLB_OK;
 }
 

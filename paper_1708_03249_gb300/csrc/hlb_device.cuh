@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "hlb_internal.h"
 
 namespace hlb {
@@ -223,6 +225,108 @@ struct ForceMMA {
         kyo[((jyo + 1) * SP + ix0 + 2) * 4 + ry] = dy[3];
     }
 };
+
+// ---------------------------------------------------------------------------
+// The same force term with split-BF16 products: every FP32 operand x is
+// written as three bf16 terms, x = h + m + l + r with |m| <= 2^-9 |h|,
+// |l| <= 2^-18 |x| and |r| <= 2^-27 |x| (each split step subtracts exactly in
+// FP32), and A B is formed from the six products whose order is at most
+// 2^-18 (h h, h m, m h, m m, h l, l h), smallest first, on mma.sync m16n8k8
+// with bf16 inputs and FP32 accumulation.  The dropped products (m l, l m,
+// l l) are below 2^-26 of |A| |B|, so the contraction keeps FP32 accuracy.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+    // D += A B, m16n8k8, A row-major 16 x 8 (two bf16 per register), B column-major 8 x 8
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// (x0, x1) -> bf16x2 words h, m, l (x0 in the low halves): x_k = h_k + m_k + l_k
+// up to 2^-27 |x_k|.  cvt.rn.bf16x2.f32 packs its first source in the high half.
+__device__ __forceinline__ void split_bf16x3(float x0, float x1, uint32_t& h, uint32_t& m, uint32_t& l) {
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
+    const float r0 = x0 - __uint_as_float(h << 16), r1 = x1 - __uint_as_float(h & 0xffff0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(m) : "f"(r1), "f"(r0));
+    const float s0 = r0 - __uint_as_float(m << 16), s1 = r1 - __uint_as_float(m & 0xffff0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(s1), "f"(s0));
+}
+
+__device__ __forceinline__ void mma_bf16x6(float (&d)[4], uint32_t ah0, uint32_t am0, uint32_t al0, uint32_t ah1,
+                                           uint32_t am1, uint32_t al1, uint32_t bh, uint32_t bm, uint32_t bl) {
+    mma_bf16(d, am0, am1, bm);
+    mma_bf16(d, ah0, ah1, bl);
+    mma_bf16(d, al0, al1, bh);
+    mma_bf16(d, ah0, ah1, bm);
+    mma_bf16(d, am0, am1, bh);
+    mma_bf16(d, ah0, ah1, bh);
+}
+
+// Same tiles, layout and interface as ForceMMA; fragments of m16n8k8 bf16:
+// A rows g and g+8, columns 2t and 2t+1; B rows (k) 2t and 2t+1, column g.
+template <int QX2, int VY>
+struct ForceMMABF16 {
+    static constexpr int XS = QX2 / 8, YS = VY / 8, SP = QX2 + 1;
+    static constexpr int XA = XS > 0 ? XS : 1, YA = YS > 0 ? YS : 1;
+    uint32_t bx[XA][3], by[YA][3];       // (h, m, l) of each B fragment
+    int mX, nX, mY, nY, gq, tq;
+
+    __device__ __forceinline__ void load(const float* K, float axf, float ayf, int warp, int lane) {
+        mX = warp / XS; nX = warp % XS; mY = warp / YS; nY = warp % YS;
+        gq = lane >> 2; tq = lane & 3;
+#pragma unroll
+        for (int ks = 0; ks < XS; ++ks) {    // B[k][n] = a_x K_x[8 nX + n][8 ks + k]
+            const float* r = K + (8 * nX + gq) * QX2 + 8 * ks + 2 * tq;
+            split_bf16x3(axf * r[0], axf * r[1], bx[ks][0], bx[ks][1], bx[ks][2]);
+        }
+#pragma unroll
+        for (int ks = 0; ks < YS; ++ks) {    // B[k][n] = a_y K_y[8 nY + n][8 ks + k]
+            const float* r = K + QX2 * QX2 + (8 * nY + gq) * VY + 8 * ks + 2 * tq;
+            split_bf16x3(ayf * r[0], ayf * r[1], by[ks][0], by[ks][1], by[ks][2]);
+        }
+    }
+
+    __device__ __forceinline__ void run(const float4* fr, float4* sKx, float4* sKy) const {
+        const float* ff = reinterpret_cast<const float*>(fr);
+        float* kxo = reinterpret_cast<float*>(sKx);
+        float* kyo = reinterpret_cast<float*>(sKy);
+        const int R0 = 16 * mX + gq, jy0 = R0 >> 2, rx = R0 & 3;       // X rows: (j_y, c)
+        float dx[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < XS; ++ks) {
+            const int i0 = 8 * ks + 2 * tq;
+            uint32_t h0, m0, l0, h1, m1, l1;
+            split_bf16x3(ff[(jy0 * SP + i0) * 4 + rx], ff[(jy0 * SP + i0 + 1) * 4 + rx], h0, m0, l0);
+            split_bf16x3(ff[((jy0 + 2) * SP + i0) * 4 + rx], ff[((jy0 + 2) * SP + i0 + 1) * 4 + rx], h1, m1, l1);
+            mma_bf16x6(dx, h0, m0, l0, h1, m1, l1, bx[ks][0], bx[ks][1], bx[ks][2]);
+        }
+        const int ixo = 8 * nX + 2 * tq;
+        kxo[(jy0 * SP + ixo) * 4 + rx] = dx[0];
+        kxo[(jy0 * SP + ixo + 1) * 4 + rx] = dx[1];
+        kxo[((jy0 + 2) * SP + ixo) * 4 + rx] = dx[2];
+        kxo[((jy0 + 2) * SP + ixo + 1) * 4 + rx] = dx[3];
+        const int Q0 = 16 * mY + gq, ix0 = Q0 >> 2, ry = Q0 & 3;       // Y rows: (i_x, c)
+        float dy[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < YS; ++ks) {
+            const int j0 = 8 * ks + 2 * tq;
+            uint32_t h0, m0, l0, h1, m1, l1;
+            split_bf16x3(ff[(j0 * SP + ix0) * 4 + ry], ff[((j0 + 1) * SP + ix0) * 4 + ry], h0, m0, l0);
+            split_bf16x3(ff[(j0 * SP + ix0 + 2) * 4 + ry], ff[((j0 + 1) * SP + ix0 + 2) * 4 + ry], h1, m1, l1);
+            mma_bf16x6(dy, h0, m0, l0, h1, m1, l1, by[ks][0], by[ks][1], by[ks][2]);
+        }
+        const int jyo = 8 * nY + 2 * tq;
+        kyo[(jyo * SP + ix0) * 4 + ry] = dy[0];
+        kyo[((jyo + 1) * SP + ix0) * 4 + ry] = dy[1];
+        kyo[(jyo * SP + ix0 + 2) * 4 + ry] = dy[2];
+        kyo[((jyo + 1) * SP + ix0 + 2) * 4 + ry] = dy[3];
+    }
+};
+
+// Force-term forms of the FP32 marching kernels (template parameter FM).
+constexpr int kForceFMA = 0, kForceTF32x3 = 1, kForceBF16x6 = 2;
+template <int FM, int QX2, int VY>
+using ForceTC = typename std::conditional<FM == kForceBF16x6, ForceMMABF16<QX2, VY>, ForceMMA<QX2, VY>>::type;
 
 // 1/x on the special-function unit (x >= 1e-30 here; beyond 1e38 it flushes to 0).
 __device__ __forceinline__ float rcp_approx(float x) {

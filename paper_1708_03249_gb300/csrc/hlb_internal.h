@@ -121,6 +121,8 @@ struct GroupDev {
     int* nonfinite;          // set by the moments kernel when a node's n or T is not finite
     unsigned long long wait_ns;   // bound of every pipeline wait in the marching kernels
     int inject_stall;        // test hook: nonzero withholds the copies of a marching CTA's second step
+    int force_form;          // FP32 marching kernels: force term by FMA (0), 3xTF32 (1) or split-BF16 (2)
+                             // tensor-core products
 };
 
 }  // namespace hlb
@@ -138,19 +140,28 @@ void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t 
 cudaError_t prepare_node();
 // Marching stage kernel for (QX2, VY, TY); returns false if no instantiation exists.
 bool march_available(int precision, int adv, int QX2, int VY, int TY);
-cudaError_t prepare_march(int precision, int adv, int QX2, int VY, int TY);
+cudaError_t prepare_march(int precision, int adv, int QX2, int VY, int TY, int form);
 void launch_march(int precision, int adv, int QX2, int VY, int TY, const GroupDev& g, const Work* works,
                   int nworks, const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
 // FP32 marching kernels of hlb_pair.cu (2D strips of two rows) and
 // hlb_line.cu (1D rows).
+// `form` is the force-term form (GroupDev::force_form); forms 1 and 2 exist for
+// the slabs force_tc_available accepts (instantiated in hlb_tc.cu).
 bool line_available(int QX2, int VY);
-cudaError_t prepare_line(int adv, int QX2, int VY);
-void launch_line(int adv, int QX2, int VY, const GroupDev& g, const Work* works, int nworks, const void* fs,
-                 const void* fn, void* fo, int stage, cudaStream_t st);
+cudaError_t prepare_line(int adv, int QX2, int VY, int form);
+void launch_line(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, int nworks,
+                 const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
 bool pair_available(int QX2, int VY);
-cudaError_t prepare_pair(int adv, int QX2, int VY);
-void launch_pair(int adv, int QX2, int VY, const GroupDev& g, const Work* works, int nworks, const void* fs,
-                 const void* fn, void* fo, int stage, cudaStream_t st);
+cudaError_t prepare_pair(int adv, int QX2, int VY, int form);
+void launch_pair(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, int nworks,
+                 const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
+bool force_tc_available(int QX2, int VY);
+cudaError_t prepare_pair_tc(int adv, int QX2, int VY, int form);
+cudaError_t prepare_line_tc(int adv, int QX2, int VY, int form);
+void launch_pair_tc(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, int nworks,
+                    const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
+void launch_line_tc(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, int nworks,
+                    const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
 void launch_broadcast(int precision, void* f, const void* gvec, long long nvalues, int V, cudaStream_t st);
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
                     double* q, int node_base, cudaStream_t st);

@@ -315,10 +315,10 @@ bool march_available(int precision, int adv, int QX2, int VY, int TY) {
     return false;
 }
 
-cudaError_t prepare_march(int precision, int adv, int QX2, int VY, int TY) {
+cudaError_t prepare_march(int precision, int adv, int QX2, int VY, int TY, int form) {
     const bool dbl = precision == HLB_FP64_;
-    if (!dbl && TY == 2) return prepare_pair(adv, QX2, VY);
-    if (!dbl && TY == 1 && line_available(QX2, VY)) return prepare_line(adv, QX2, VY);
+    if (!dbl && TY == 2) return prepare_pair(adv, QX2, VY, form);
+    if (!dbl && TY == 1 && line_available(QX2, VY)) return prepare_line(adv, QX2, VY, form);
 #define HLB_PREP(RT, A, B, C)                                                        \
     if ((sizeof(RT) == 8) == dbl && QX2 == A && VY == B && TY == C)                  \
         return adv == HLB_WENO5_ ? prepare_one<RT, HLB_WENO5_, A, B, C>()          \
@@ -332,11 +332,11 @@ void launch_march(int precision, int adv, int QX2, int VY, int TY, const GroupDe
                   int nworks, const void* fs, const void* fn, void* fo, int stage, cudaStream_t st) {
     const bool dbl = precision == HLB_FP64_;
     if (!dbl && TY == 2) {
-        launch_pair(adv, QX2, VY, g, works, nworks, fs, fn, fo, stage, st);
+        launch_pair(adv, QX2, VY, g.force_form, g, works, nworks, fs, fn, fo, stage, st);
         return;
     }
     if (!dbl && TY == 1 && line_available(QX2, VY)) {
-        launch_line(adv, QX2, VY, g, works, nworks, fs, fn, fo, stage, st);
+        launch_line(adv, QX2, VY, g.force_form, g, works, nworks, fs, fn, fo, stage, st);
         return;
     }
 #define HLB_LAUNCH(RT, A, B, C)                                                                      \

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhlb.so")
 
 HLB_OK, HLB_EINVAL, HLB_ENOMEM, HLB_ECUDA, HLB_ETIMEOUT, HLB_ENONFINITE, HLB_EUNSUPPORTED = range(7)
 HLB_UPWIND2, HLB_WENO5 = 0, 1
-HLB_FP64, HLB_FP32 = 0, 1
+HLB_FP64, HLB_FP32, HLB_FP32_TF32X3, HLB_FP32_BF16SPLIT = 0, 1, 2, 3
 STATUS_NAMES = {0: "HLB_OK", 1: "HLB_EINVAL", 2: "HLB_ENOMEM", 3: "HLB_ECUDA",
                 4: "HLB_ETIMEOUT", 5: "HLB_ENONFINITE", 6: "HLB_EUNSUPPORTED"}
 
@@ -59,6 +59,7 @@ SIGNATURES = {
     "hlb_moments_noalloc": (C.c_int, [_P, _P, _P, _P, _P]),
     "hlb_sizes": (C.c_int, [_P, _LL, _LL, _LL]),
     "hlb_get_dt": (C.c_int, [_P, C.c_int, _D]),
+    "hlb_force_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "hlb_get_nsteps": (C.c_int, [_P, _LL]),
     "hlb_get_state": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_set_state": (C.c_int, [_P, _P, C.c_size_t]),
@@ -184,6 +185,12 @@ class Handle:
 
     def step(self, nsteps=1):
         _check(lib().hlb_step(self._h, int(nsteps)))
+
+    def force_form(self, inst=0) -> int:
+        """0: FMA force term; 1: 3xTF32 tensor cores; 2: split-BF16 tensor cores."""
+        f = C.c_int(-1)
+        _check(lib().hlb_force_form(self._h, inst, C.byref(f)))
+        return f.value
 
     def dt(self, inst=0) -> float:
         d = C.c_double()

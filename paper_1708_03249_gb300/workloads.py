@@ -18,7 +18,7 @@ import math
 import numpy as np
 
 UPWIND2, WENO5 = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_TF32X3, FP32_BF16SPLIT = 0, 1, 2, 3   # FP32 state; force term on the tensor cores
 X_HALF, X_FULL, X_LAGUERRE = 0, 1, 2   # along p_x: half-range Hermite (HHLB), Gauss-Hermite (HLB),
                                        # half-range Gauss-Laguerre
 

@@ -36,7 +36,7 @@ def test_version(hlb_lib):
 
 @pytest.mark.parametrize("field,value", [("Qx", 0), ("Qx", 33), ("Qx", 201), ("Qy", 3), ("Qz", -2), ("nx", 5),
                                           ("ny", 2), ("Kn", 0.0), ("T_left", -1.0), ("stretch_A", 1.0),
-                                          ("advection", 7), ("precision", 3), ("Nx_eq", 4), ("Lx", 0.0),
+                                          ("advection", 7), ("precision", 4), ("precision", -1), ("Nx_eq", 4), ("Lx", 0.0),
                                           ("x_basis", 3),
                                           ("ax", math.nan)])
 def test_invalid_config_is_rejected(hlb_lib, field, value):
@@ -194,17 +194,3 @@ def test_null_handle_is_rejected(hlb_lib):
     assert L.hlb_set_wait_test(None, 1, 0.01) == hlb.HLB_EINVAL
     assert L.hlb_get_dt(None, 0, C.byref(D)) == hlb.HLB_EINVAL
     L.hlb_destroy(None)                      # a no-op
-
-
-def test_tensor_core_force_variant_compiles(tmp_path):
-    # The optional tensor-core force term of the pair kernel (compile-time
-    # switch HLB_PAIR_MMA) must keep building for sm_103a.
-    import shutil
-    import subprocess
-    from paper_1708_03249_gb300 import build as B
-    if shutil.which(B.nvcc()) is None and not os.path.exists(B.nvcc()):
-        pytest.skip("nvcc not available")
-    cmd = [B.nvcc(), "-c", os.path.join(B.CSRC, "hlb_pair.cu"), "-o", str(tmp_path / "m.o"),
-           "-DHLB_PAIR_MMA=1"] + B._flags()
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    assert res.returncode == 0, res.stderr[-2000:]

@@ -268,6 +268,68 @@ def test_fp32_1d_q16_tensor_core_force(adv):
     _check_fp32(got, mom, refs)
 
 
+# The force term a . K f on the tensor cores, as a runtime option: three TF32
+# products (HLB_FP32_TF32X3) or the six leading products of a three-term bf16
+# split (HLB_FP32_BF16SPLIT), FP32 accumulation, in the 2D pair kernel and the
+# 1D line kernel, for both slab shapes that tile into 16 x 8 x 8 blocks; a
+# strong oblique force so that K carries the update.
+_TC_CASES = {
+    "pair_16x8": lambda p: W.make(Qx=8, Qy=8, nx=27, ny=6, Ly=0.3, precision=p, T_left=1.0, T_right=2.0,
+                                  Kn=0.5, **W.gravity(0.9, 40.0)),
+    "pair_32x16": lambda p: W.make(Qx=16, Qy=16, nx=14, ny=6, Ly=6 / 14, precision=p, T_left=1.0, T_right=1.2,
+                                   Kn=0.05, **W.gravity(0.9, 45.0)),
+    "line_16x8": lambda p: W.make(Qx=8, Qy=8, nx=43, precision=p, T_left=0.7, T_right=1.4, Kn=0.3,
+                                  **W.gravity(0.9, 30.0)),
+    "line_32x16": lambda p: W.make(Qx=16, Qy=16, nx=42, precision=p, T_left=0.8, T_right=1.6, Kn=0.3,
+                                   **W.gravity(0.9, 35.0)),
+}
+
+
+@pytest.mark.parametrize("prec", [W.FP32_TF32X3, W.FP32_BF16SPLIT])
+@pytest.mark.parametrize("case", sorted(_TC_CASES))
+@pytest.mark.parametrize("adv", [W.WENO5, W.UPWIND2])
+def test_fp32_tensor_core_force_forms(case, prec, adv):
+    from paper_1708_03249_gb300 import hlb
+    cfg = dict(_TC_CASES[case](prec), advection=adv)
+    with hlb.Handle(cfg, stream=_stream()) as h:
+        assert h.force_form(0) == (1 if prec == W.FP32_TF32X3 else 2)
+    got, mom, N, refs = run_pair(cfg, 6, init=(1.0, 0.1, 0.05, 1.1))
+    _check_fp32(got, mom, refs)
+
+
+def test_fp32_force_forms_agree():
+    # The three FP32 forms of the force term on one state: they differ only
+    # by FP32 rounding of the contraction (all within a few ulps of the state).
+    from paper_1708_03249_gb300 import hlb
+    outs = []
+    for prec in (W.FP32, W.FP32_TF32X3, W.FP32_BF16SPLIT):
+        cfg = _TC_CASES["pair_32x16"](prec)
+        with hlb.Handle(cfg, stream=_stream()) as h:
+            h.init_equilibrium(1.0, 0.1, 0.05, 1.1)
+            f = h.get_state().astype(np.float64) * W.perturbation(h.values, seed=21)
+            h.set_state(f)
+            h.step(5)
+            outs.append(h.get_state().astype(np.float64))
+    scale = np.abs(outs[0]).max()
+    for o in outs[1:]:
+        assert np.abs(o - outs[0]).max() < 2e-6 * scale
+
+
+def test_default_force_forms():
+    # HLB_FP32 leaves the choice to the library (the measured faster form):
+    # the tensor cores for the 1D kernel's 32 x 16 slabs and the 2D kernel's
+    # 16 x 8 slabs with upwind2, FMAs elsewhere; FP64 and slabs that do not
+    # tile use FMAs whatever was asked.
+    from paper_1708_03249_gb300 import hlb
+    cases = [(_TC_CASES["line_32x16"](W.FP32), 1), (_TC_CASES["pair_16x8"](W.FP32), 0),
+             (dict(_TC_CASES["pair_16x8"](W.FP32), advection=W.UPWIND2), 1),
+             (_TC_CASES["line_16x8"](W.FP32), 0), (W.make(Qx=4, Qy=4, nx=16, precision=W.FP32_TF32X3), 0),
+             (W.make(Qx=8, Qy=8, nx=16, precision=W.FP64), 0)]
+    for cfg, form in cases:
+        with hlb.Handle(cfg, stream=_stream()) as h:
+            assert h.force_form(0) == form, cfg
+
+
 @pytest.mark.parametrize("Qx,Qy,ny,prec,adv", [(16, 8, 1, W.FP32, W.WENO5), (8, 4, 5, W.FP32, W.WENO5),
                                                 (32, 16, 1, W.FP32, W.UPWIND2), (8, 4, 1, W.FP64, W.UPWIND2)])
 def test_full_range_x_models(Qx, Qy, ny, prec, adv):

@@ -138,3 +138,31 @@ def test_async_moments_match_and_overlap_the_next_steps():
         a.moments_wait()
         np.testing.assert_array_equal(a.get_state(), b.get_state())
         np.testing.assert_array_equal(outs[0][0].numpy(), np.asarray(ref[0]).reshape(-1))
+
+
+@pytest.mark.parametrize("prec", [W.FP32, W.FP64])
+def test_checkpoint_resume_is_bit_exact(prec):
+    # run(2n) == run(n), checkpoint (hlb_get_state), restore into a fresh
+    # handle (hlb_set_state), run(n): the same bits.  Two velocity sets and a
+    # 2D instance (group streams, pair and line kernels); n = 37 crosses the
+    # captured graph's 30-step boundary.
+    from paper_1708_03249_gb300 import hlb
+    cfgs = [dict(c, precision=prec) for c in _cfgs("groups")] + \
+           [W.make(Qx=8, Qy=8, nx=20, ny=6, Ly=0.3, Kn=0.4, ax=-0.3, ay=-0.1, precision=prec)]
+    n = 37
+    with hlb.Handle(cfgs) as a:
+        a.init_equilibrium(1.0, 0.05, 0.0, 1.1)
+        f0 = a.get_state().astype(np.float64) * W.perturbation(a.values, seed=17, amplitude=0.05)
+        a.set_state(f0)
+        a.step(2 * n)
+        whole = a.get_state()
+    with hlb.Handle(cfgs) as b:
+        b.set_state(f0)
+        b.step(n)
+        ckpt = b.get_state().copy()
+    with hlb.Handle(cfgs) as c:
+        c.set_state(ckpt)
+        c.step(n)
+        resumed = c.get_state()
+    assert resumed.dtype == whole.dtype
+    assert np.array_equal(resumed.view(np.uint8), whole.view(np.uint8))
