@@ -251,7 +251,9 @@ hlb_status hlb_set_state_dev(hlb_handle* h, const void* f_dev, size_t bytes);
  * group that runs them, times the three stage launches of one step for x-
  * segment lengths from a quarter to four times the built-in heuristic's (CUDA
  * events on the handle's stream, one untimed round, three timed) and keeps the
- * fastest.  The state is only read (the launches write the two scratch
+ * fastest; for groups on the persistent kernel, whole persistent steps for
+ * segment lengths (cells per work item) of 24 to 264 cells times one or half
+ * the resident CTAs per SM.  The state is only read (the launches write the two scratch
  * buffers), so the call may come at any time between steps; it synchronises
  * the handle's streams and drops the captured graph.  The results do not
  * depend on the segment length (every cell's update is computed the same way),
@@ -308,6 +310,32 @@ hlb_status hlb_axis(int Q, int half, double* p, double* w, double* K);
  * about threefold per order).  No handle needed.  Nx_eq (-1: Qx - 1) must be
  * at most 31; HLB_EINVAL otherwise. */
 hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g);
+
+/* Persistent batched kernel on (1, the default) or off (0).  Velocity-set
+ * groups of 1D FP32 instances without a p_z axis (2 Qx x Qy slabs of 8 x 4,
+ * 16 x 8, 32 x 16 with the default force-term form, or 32 x 1; equilibrium
+ * orders up to 15) step with one persistent launch per RK-3 step: the CTAs
+ * take work items from a queue in stage-major order, per instance first its
+ * node chunks (moment sums, equilibrium factors, the emitted densities of the
+ * walls they hold), then its x-segments (the marching update), and each item
+ * waits on per-instance counters for what it reads (bounded: a wait that
+ * runs out records HLB_ETIMEOUT and ends the launch).  Off, or with per-launch timing, or for a group with
+ * a force field, those groups launch the node pass, the wall kernel and the
+ * stage kernel per stage.  The results agree to FP32 rounding (the moment
+ * sums are formed in another order).  Drops a captured graph (synchronises).
+ * No counterpart in the paper.  Errors: HLB_EINVAL. */
+hlb_status hlb_set_persistent(hlb_handle* h, int on);
+
+/* How instance `inst`'s velocity-set group steps: persistent (1: the
+ * persistent kernel, 0: per-stage launches), segment_cells (cells per work
+ * item or CTA of the marching kernels; 0 if the group does not march), ctas
+ * (the persistent grid, or the stage kernel's CTAs per launch) and
+ * tuned_ms[2] (the RK-3 step times hlb_autotune measured for the group with
+ * the persistent kernel and with the per-stage launches, each with its best
+ * shape; 0 where it did not time them).  Any output may be NULL.
+ * Errors: HLB_EINVAL. */
+hlb_status hlb_step_form(const hlb_handle* h, int inst, int* persistent, int* segment_cells, int* ctas,
+                         double* tuned_ms);
 
 /* Enable (1) / disable (0) CUDA-graph replay in hlb_step, and per-launch
  * CUDA-event timing (timing forces eager launches).  hlb_kernel_times

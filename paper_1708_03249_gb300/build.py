@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhlb.so")
 SOURCES = ["hlb_api.cu", "hlb_kernels.cu", "hlb_node.cu", "hlb_march.cu", "hlb_pair.cu", "hlb_line.cu",
-           "hlb_tc.cu", "hlb_tables.cpp"]
+           "hlb_tc.cu", "hlb_persist.cu", "hlb_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

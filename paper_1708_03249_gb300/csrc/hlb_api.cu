@@ -107,6 +107,16 @@ struct Group {
     std::vector<char> field_on;
     bool has_field = false;
     const void* mom_buf = nullptr;           // state buffer read by a pending hlb_moments_async
+    // persistent batched kernel (1D FP32 groups without a p_z axis): one
+    // launch per step; control words [head, abort, pad, pad, node counters
+    // [ninst], segment counters [ninst]] zeroed before each launch; the work
+    // items of a stage (per instance its node chunks, then its segments),
+    // node chunks and segments per instance, resident CTAs
+    bool persist_ok = false;
+    bool persist_use = true;                 // the autotuner's pick: persistent or per-stage launches
+    float tuned_ms_persist = 0.0f, tuned_ms_stages = 0.0f;   // its best step times (0: not timed)
+    int persist_per_sm = 0, persist_grid = 0, persist_nitems = 0;
+    DevBuf d_pctl, d_nseg, d_nchunk, d_pitems;
 };
 
 // Host-side NVTX range (the library's calls and the RK-3 stages they enqueue,
@@ -162,6 +172,7 @@ struct hlb_handle {
     std::vector<cudaEvent_t> group_done;
     cudaEvent_t step_fork = nullptr;
     bool once_field_prepared = false;
+    bool persistent = true;                  // eligible groups step with the persistent kernel
 };
 
 namespace {
@@ -320,7 +331,31 @@ hlb_status set_segments(hlb_handle* h, Group& G, int SX) {
                 }
         }
     G.nworks = (int)works.size();
-    return upload(G.d_works, works);
+    hlb_status st = upload(G.d_works, works);
+    if (st != HLB_OK || !G.persist_ok) return st;
+    // the persistent kernel's items of one stage: the node chunks (one cell
+    // per thread) of every instance, then the segments of every instance (in
+    // the work list's order: instance, then x).  A segment then rarely finds
+    // its instance's node chunks unfinished (they were taken long before),
+    // and a node chunk of the next stage its instance's segments.
+    const int chunk = std::min(G.V, hlb::kPersistNodeChunk);
+    std::vector<int> nseg(G.members.size(), 0), nchunk(G.members.size(), 0);
+    std::vector<hlb::PersistItem> items;
+    for (size_t m = 0; m < G.members.size(); ++m) {
+        const int nx = h->cfg[G.members[m]].nx;
+        for (int a = 0; a < nx; a += chunk) {
+            items.push_back(hlb::PersistItem{0, (int)m, a, std::min(nx, a + chunk)});
+            ++nchunk[m];
+        }
+    }
+    for (size_t j = 0; j < works.size(); ++j) {
+        items.push_back(hlb::PersistItem{1, works[j].inst, (int)j, 0});
+        ++nseg[works[j].inst];
+    }
+    G.persist_nitems = (int)items.size();
+    if ((st = upload(G.d_pitems, items)) != HLB_OK) return st;
+    if ((st = upload(G.d_nchunk, nchunk)) != HLB_OK) return st;
+    return upload(G.d_nseg, nseg);
 }
 
 hlb_status build_group(hlb_handle* h, Group& G) {
@@ -505,22 +540,41 @@ hlb_status build_group(hlb_handle* h, Group& G) {
             const long long rows = xwork / std::max(1LL, (long long)G.TY);
             long long sx = rows / (two_d ? 4096 : 1216);
             sx = std::max(24LL, std::min(512LL, (sx + 5) / 6 * 6));
-            if ((s = set_segments(h, G, (int)sx)) != HLB_OK) return s;
-            // the force term's form: on the tensor cores where the caller
-            // asked for it and the slab tiles into 16 x 8 x 8 blocks; by
-            // default where 3xTF32 measured faster than the FMA loop on a
-            // GB300: the 1D kernel's 32 x 16 slabs (0.412 against 0.523 ms
-            // per stage, 131072 cells) and the 2D kernel's 16 x 8 slabs with
-            // upwind2 (2.06 against 2.39 ms, 1024 x 512 cells, 1024
-            // velocities); with WENO-5 the 2D kernel is issue-bound and the
-            // FMA loop is faster (3.43 against 3.64 ms; 32 x 16: 0.330
-            // against 0.347 ms)
+            // the force term's form (below) decides the persistent kernel's
+            // eligibility, and that the segment bound: resolve the form first
             G.force_form = 0;
             if (G.precision == HLB_FP32 && hlb::force_tc_available(G.QX2, G.VY)) {
                 if (G.force_request) G.force_form = G.force_request;
                 else if (G.TY == 1 && G.QX2 * G.VY >= 512) G.force_form = 1;
                 else if (G.TY == 2 && G.adv == HLB_UPWIND2 && G.QX2 * G.VY == 128) G.force_form = 1;
             }
+            // persistent batched kernel: 1D FP32 groups without a p_z axis,
+            // equilibrium in double-float, the line kernel's slabs
+            if (G.precision == HLB_FP32 && G.TY == 1 && G.VZ == 1 && !G.x_full && G.Nx <= 15 &&
+                hlb::persist_available(G.QX2, G.VY, G.force_form, std::max(G.Nx, G.Ny))) {
+                int per = 0;
+                if (hlb::prepare_persist(G.adv, G.QX2, G.VY, G.force_form, &per) == cudaSuccess && per > 0) {
+                    int dev = 0, nsm = 1;
+                    HLB_CUDA(cudaGetDevice(&dev));
+                    HLB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+                    G.persist_ok = true;
+                    G.persist_per_sm = per;
+                    G.persist_grid = nsm * per;
+                    if ((s = upload(G.d_pctl, std::vector<int>(4 + 2 * G.members.size(), 0))) != HLB_OK) return s;
+                } else {
+                    cudaGetLastError();
+                }
+            }
+            if ((s = set_segments(h, G, (int)sx)) != HLB_OK) return s;
+            // the force term's form (set above): on the tensor cores where the
+            // caller asked for it and the slab tiles into 16 x 8 x 8 blocks;
+            // by default where 3xTF32 measured faster than the FMA loop on a
+            // GB300: the 1D kernel's 32 x 16 slabs (0.412 against 0.523 ms
+            // per stage, 131072 cells) and the 2D kernel's 16 x 8 slabs with
+            // upwind2 (2.06 against 2.39 ms, 1024 x 512 cells, 1024
+            // velocities); with WENO-5 the 2D kernel is issue-bound and the
+            // FMA loop is faster (3.43 against 3.64 ms; 32 x 16: 0.330
+            // against 0.347 ms)
             HLB_CUDA(hlb::prepare_march(G.precision, G.adv, G.QX2, G.VY, G.TY, G.force_form));
             HLB_CUDA(hlb::prepare_node());
         }
@@ -567,8 +621,42 @@ void wait_moments(hlb_handle* h, cudaStream_t s) {
 
 // One RK-3 step of one group on stream st: three (node pass, wall, stage)
 // triples; buffer roles rotate.
+// Whether group G steps with the persistent kernel: eligible, enabled, not
+// timed per stage, no per-node force field (that adds a pass per stage).
+bool persist_on(const hlb_handle* h, const Group& G) {
+    return G.persist_ok && G.persist_use && G.march_ok && h->persistent && !h->time_kernels && !G.has_field;
+}
+
+// One RK-3 step of group G by one launch of the persistent kernel (its
+// control words zeroed first).
+void enqueue_persist_step(Group& G, cudaStream_t st) {
+    NvtxRange range("RK-3 step (persistent)");
+    hlb::PersistArgs a{};
+    for (int k = 0; k < 3; ++k) a.buf[k] = static_cast<float*>(G.buf[k].p);
+    a.cur = G.cur;
+    a.nitems = G.persist_nitems;
+    a.items = static_cast<const hlb::PersistItem*>(G.d_pitems.p);
+    const size_t ninst = G.members.size();
+    int* ctl = static_cast<int*>(G.d_pctl.p);
+    a.head = ctl;
+    a.abort = ctl + 1;
+    a.prog_node = reinterpret_cast<unsigned*>(ctl + 4);
+    a.prog_march = reinterpret_cast<unsigned*>(ctl + 4 + ninst);
+    a.nchunk = static_cast<const int*>(G.d_nchunk.p);
+    a.nseg = static_cast<const int*>(G.d_nseg.p);
+    cudaMemsetAsync(ctl, 0, (4 + 2 * ninst) * sizeof(int), st);
+    hlb::launch_persist(G.adv, G.QX2, G.VY, G.force_form, G.dev, (const hlb::Work*)G.d_works.p, a,
+                        std::min(G.persist_grid, 3 * G.persist_nitems), st);
+}
+
 void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
     static const char* kStageNames[3] = {"RK-3 stage 1", "RK-3 stage 2", "RK-3 stage 3"};
+    if (persist_on(h, G)) {
+        enqueue_persist_step(G, st_);
+        G.prev = G.cur;
+        G.cur = (G.cur + 1) % 3;
+        return;
+    }
     void* S = G.buf[G.cur].p;
     void* X = G.buf[(G.cur + 1) % 3].p;
     void* Y = G.buf[(G.cur + 2) % 3].p;
@@ -623,7 +711,8 @@ void enqueue_step(hlb_handle* h) {
 // lines) when the marching kernel runs, the wall kernel and the stage kernel.
 long long kernels_per_step(hlb_handle* h) {
     long long n = 0;
-    for (auto& G : h->groups) n += 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2) + (G->has_field ? 3 : 0);
+    for (auto& G : h->groups)
+        n += persist_on(h, *G) ? 1 : 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2) + (G->has_field ? 3 : 0);
     return n;
 }
 
@@ -1314,7 +1403,98 @@ struct EventPair {
     }
 };
 
+// Persistent groups: the segment length (cells per work item) and the CTAs
+// resident per SM, timed over whole persistent steps (one untimed, three
+// timed).  A step reads the state buffer and writes the two scratch buffers
+// (stage 1 S -> X, stage 2 X -> Y, stage 3 Y -> X), so the state is kept.
+hlb_status tune_persist(hlb_handle* h, Group& G, EventPair& ev, int* chosen, float* step_ms) {
+    int dev = 0, nsm = 1;
+    HLB_CUDA(cudaGetDevice(&dev));
+    HLB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int base_sx = G.SX, base_grid = G.persist_grid;
+    std::vector<int> per_sm = {G.persist_per_sm};
+    if (G.persist_per_sm >= 2) per_sm.push_back(G.persist_per_sm / 2);
+    int best_sx = base_sx, best_grid = base_grid;
+    float best_ms = -1.0f;
+    hlb_status s = HLB_OK;
+    for (int sx : {24, 36, 48, 72, 96, 132, 192, 264}) {
+        if ((s = set_segments(h, G, sx)) != HLB_OK) break;
+        for (int per : per_sm) {
+            G.persist_grid = nsm * per;
+            for (int round = 0; round < 4; ++round) {
+                if (round == 1) cudaEventRecord(ev.e0, h->stream);
+                enqueue_persist_step(G, h->stream);
+            }
+            cudaEventRecord(ev.e1, h->stream);
+            float ms = 0.0f;
+            cudaError_t e = cudaEventSynchronize(ev.e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+            if (e != cudaSuccess) { s = fail(HLB_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(e)); break; }
+            if (best_ms < 0.0f || ms < best_ms) { best_ms = ms; best_sx = sx; best_grid = G.persist_grid; }
+        }
+        if (s != HLB_OK) break;
+    }
+    G.persist_grid = s == HLB_OK ? best_grid : base_grid;
+    const hlb_status s2 = set_segments(h, G, s == HLB_OK ? best_sx : base_sx);
+    if (s2 != HLB_OK) G.march_ok = false;
+    *chosen = G.march_ok ? G.SX : 0;
+    *step_ms = best_ms / 3.0f;
+    return s != HLB_OK ? s : s2;
+}
+
+// One RK-3 step of the per-stage launches (node pass, wall, stage kernel per
+// stage), timed over three steps after an untimed one.  The steps read the
+// state buffer and write the two scratch buffers; the buffer roles are put
+// back, so the state is kept.
+hlb_status time_per_stage_step(hlb_handle* h, Group& G, EventPair& ev, float* step_ms) {
+    const int cur = G.cur, prev = G.prev;
+    const bool use = G.persist_use;
+    G.persist_use = false;
+    for (int round = 0; round < 4; ++round) {
+        if (round == 1) cudaEventRecord(ev.e0, h->stream);
+        enqueue_group_step(h, G, h->stream);
+        G.cur = cur;
+        G.prev = prev;
+    }
+    cudaEventRecord(ev.e1, h->stream);
+    G.persist_use = use;
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(ev.e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+    if (e != cudaSuccess) return fail(HLB_ECUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+    *step_ms = ms / 3.0f;
+    return HLB_OK;
+}
+
+hlb_status tune_group_stages(hlb_handle* h, Group& G, EventPair& ev, int* chosen);
+
+// A group the persistent kernel can step: the per-stage launches with their
+// best segment length against the persistent kernel with its best segment
+// length and grid, whole steps timed; the faster is kept (the results agree
+// to FP32 rounding either way).
 hlb_status tune_group(hlb_handle* h, Group& G, EventPair& ev, int* chosen) {
+    G.persist_use = true;
+    if (!persist_on(h, G)) return tune_group_stages(h, G, ev, chosen);
+    G.persist_use = false;
+    hlb_status s = tune_group_stages(h, G, ev, chosen);
+    if (s != HLB_OK) { G.persist_use = true; return s; }
+    const int sx_stages = G.SX;
+    float ms_stages = 0.0f, ms_persist = 0.0f;
+    if ((s = time_per_stage_step(h, G, ev, &ms_stages)) != HLB_OK) { G.persist_use = true; return s; }
+    G.persist_use = true;
+    if ((s = tune_persist(h, G, ev, chosen, &ms_persist)) != HLB_OK) return s;
+    G.tuned_ms_stages = ms_stages;
+    G.tuned_ms_persist = ms_persist;
+    if (ms_stages < ms_persist) {
+        G.persist_use = false;
+        s = set_segments(h, G, sx_stages);
+        if (s != HLB_OK) G.march_ok = false;
+        *chosen = G.march_ok ? G.SX : 0;
+    }
+    return s;
+}
+
+hlb_status tune_group_stages(hlb_handle* h, Group& G, EventPair& ev, int* chosen) {
     // candidates around the heuristic's segment length, multiples of 6 cells
     const int base = G.SX;
     std::vector<int> cand;
@@ -1379,9 +1559,41 @@ hlb_status hlb_autotune(hlb_handle* h, int* segments_out) {
     return check_device_error(h);
 }
 
+hlb_status hlb_set_persistent(hlb_handle* h, int on) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (h->persistent != (on != 0) && h->graph) {     // the captured steps change: re-capture
+        HLB_CUDA(cudaStreamSynchronize(h->stream));
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->persistent = on != 0;
+    return HLB_OK;
+}
+
+hlb_status hlb_step_form(const hlb_handle* h, int inst, int* persistent, int* segment_cells, int* ctas,
+                         double* tuned_ms) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (inst < 0 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
+    const Group& G = *h->groups[h->inst_group[inst]];
+    const bool p = persist_on(h, G);
+    if (persistent) *persistent = p ? 1 : 0;
+    if (segment_cells) *segment_cells = G.march_ok ? G.SX : 0;
+    if (ctas) *ctas = p ? std::min(G.persist_grid, 3 * G.persist_nitems) : (G.march_ok ? G.nworks : G.grid);
+    if (tuned_ms) {
+        tuned_ms[0] = G.tuned_ms_persist;
+        tuned_ms[1] = G.tuned_ms_stages;
+    }
+    return HLB_OK;
+}
+
 hlb_status hlb_set_options(hlb_handle* h, int use_graphs, int time_kernels) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     h->use_graphs = use_graphs != 0;
+    if (h->time_kernels != (time_kernels != 0) && h->graph) {   // timed steps launch per stage: re-capture later
+        HLB_CUDA(cudaStreamSynchronize(h->stream));
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     h->time_kernels = time_kernels != 0;
     return HLB_OK;
 }

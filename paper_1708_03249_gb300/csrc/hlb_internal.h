@@ -162,6 +162,34 @@ void launch_pair_tc(int adv, int QX2, int VY, int form, const GroupDev& g, const
                     const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
 void launch_line_tc(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, int nworks,
                     const void* fs, const void* fn, void* fo, int stage, cudaStream_t st);
+// Persistent batched kernel (hlb_persist.cu): 1D FP32 groups without a p_z
+// axis, one launch per RK-3 step.  The work items of one stage: node chunks
+// (kind 0: cells [a, b) of instance inst -> moment sums, factor lines, the
+// wall densities of the walls they hold) and x-segments (kind 1: a = index
+// into the group's work list), the node chunks of an instance before its
+// segments.  The control words (head, abort, progress counters) are zeroed
+// before every launch.
+constexpr int kPersistNodeChunk = 512;   // cells per node item at most (one thread per cell)
+struct PersistItem {
+    int kind, inst, a, b;
+};
+struct PersistArgs {
+    float* buf[3];            // the group's three state buffers
+    int cur;                  // index of the current state buffer (S) at the step's start
+    int nitems;               // work items per stage
+    const PersistItem* items; // [nitems]
+    int* head;                // work-queue counter
+    int* abort;               // nonzero: a wait ran out; every CTA leaves
+    unsigned* prog_node;      // [ninst] node items of the step completed per instance
+    unsigned* prog_march;     // [ninst] segments of the step completed per instance
+    const int* nchunk;        // [ninst] node items per instance and stage
+    const int* nseg;          // [ninst] segments per instance and stage
+};
+bool persist_available(int QX2, int VY, int form, int Nmax);
+cudaError_t prepare_persist(int adv, int QX2, int VY, int form, int* blocks_per_sm);
+size_t persist_smem_bytes(int QX2, int VY, int form);
+void launch_persist(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, const PersistArgs& a,
+                    int grid, cudaStream_t st);
 void launch_broadcast(int precision, void* f, const void* gvec, long long nvalues, int V, cudaStream_t st);
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
                     double* q, int node_base, cudaStream_t st);

@@ -60,6 +60,8 @@ SIGNATURES = {
     "hlb_sizes": (C.c_int, [_P, _LL, _LL, _LL]),
     "hlb_get_dt": (C.c_int, [_P, C.c_int, _D]),
     "hlb_force_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "hlb_set_persistent": (C.c_int, [_P, C.c_int]),
+    "hlb_step_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _D]),
     "hlb_get_nsteps": (C.c_int, [_P, _LL]),
     "hlb_get_state": (C.c_int, [_P, _P, C.c_size_t]),
     "hlb_set_state": (C.c_int, [_P, _P, C.c_size_t]),
@@ -185,6 +187,18 @@ class Handle:
 
     def step(self, nsteps=1):
         _check(lib().hlb_step(self._h, int(nsteps)))
+
+    def set_persistent(self, on: bool = True):
+        _check(lib().hlb_set_persistent(self._h, 1 if on else 0))
+
+    def step_form(self, inst=0) -> dict:
+        """{"persistent": bool, "segment_cells": int, "ctas": int, "tuned_ms": (persistent, per-stage)}
+        of instance inst's group."""
+        p, sx, c = C.c_int(), C.c_int(), C.c_int()
+        ms = (C.c_double * 2)()
+        _check(lib().hlb_step_form(self._h, inst, C.byref(p), C.byref(sx), C.byref(c), ms))
+        return {"persistent": bool(p.value), "segment_cells": sx.value, "ctas": c.value,
+                "tuned_ms": (ms[0], ms[1])}
 
     def force_form(self, inst=0) -> int:
         """0: FMA force term; 1: 3xTF32 tensor cores; 2: split-BF16 tensor cores."""

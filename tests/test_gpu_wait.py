@@ -4,8 +4,12 @@ The marching stage kernels wait on their bulk-copy pipeline with a time
 limit.  The test hook of the C ABI withholds the copies of one pipeline step
 in every marching CTA, so that those waits run out: no fault and no trap, the
 waits give up, record HLB_ETIMEOUT in the device error word and the CTAs
-leave at their next barrier.  The context must stay usable, and once the
-hook is cleared the handle must step exactly as a fresh one does."""
+leave at their next barrier.  In the persistent batched kernel the same hook
+withholds one work item's count on its instance's progress counter, so that
+the items of the next stage of that instance wait on it until their bound runs
+out (a per-instance device barrier that never opens); the launch's abort flag
+then ends every CTA.  The context must stay usable, and once the hook is
+cleared the handle must step exactly as a fresh one does."""
 import numpy as np
 import pytest
 
@@ -21,20 +25,27 @@ CASES = {
                            T_left=1.0, T_right=1.5, ax=-0.2, ay=0.1, Kn=0.3),
     # 1D FP64: the scalar marching kernel
     "scalar_fp64_1d": W.scaled(W.CHANNEL_1D_FP64, nx=40),
-    # 1D FP32: the line kernel (two cells per iteration)
+    # 1D FP32: the persistent batched kernel (two instances of one velocity
+    # set, per-instance progress counters), and the per-stage line kernel
+    "persistent_fp32_1d": [W.make(Qx=8, Qy=8, nx=60, advection=W.WENO5, precision=W.FP32, T_left=1.0,
+                                  T_right=1.4, Kn=0.3, **W.gravity(0.3, 20.0)),
+                           W.make(Qx=8, Qy=8, nx=150, advection=W.WENO5, precision=W.FP32, T_left=1.0,
+                                  T_right=0.7, Kn=0.1, ax=-0.4)],
     "line_fp32_1d": W.make(Qx=8, Qy=8, nx=60, advection=W.WENO5, precision=W.FP32, T_left=1.0, T_right=1.4,
                            Kn=0.3, **W.gravity(0.3, 20.0)),
 }
+PER_STAGE = {"line_fp32_1d"}
 
 
 def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def _run(cfg, steps, hook, graphs):
+def _run(cfg, steps, hook, graphs, persistent=True):
     from paper_1708_03249_gb300 import hlb
     with hlb.Handle(cfg, stream=_stream()) as h:
         h.set_options(use_graphs=graphs)
+        h.set_persistent(persistent)
         if hook:
             h.init_equilibrium()
             h.set_wait_test(True, 0.002)
@@ -58,8 +69,9 @@ def _run(cfg, steps, hook, graphs):
 @pytest.mark.parametrize("graphs,steps", [(False, 1), (True, 30)])
 def test_wait_runs_out_and_handle_recovers(name, graphs, steps):
     cfg = CASES[name]
-    got = _run(cfg, steps, hook=True, graphs=graphs)
-    ref = _run(cfg, steps, hook=False, graphs=graphs)
+    persistent = name not in PER_STAGE
+    got = _run(cfg, steps, hook=True, graphs=graphs, persistent=persistent)
+    ref = _run(cfg, steps, hook=False, graphs=graphs, persistent=persistent)
     np.testing.assert_array_equal(got, ref)
 
 
@@ -90,3 +102,11 @@ def test_launch_count(graphs):
         h.launch_count(reset=True)
         h.step(30)
         assert h.launch_count() == 30 * 6
+    # persistent batched kernel: one launch per step per group
+    with hlb.Handle(CASES["persistent_fp32_1d"], stream=_stream()) as h:
+        h.set_options(use_graphs=graphs)
+        h.init_equilibrium()
+        assert h.step_form(0)["persistent"]
+        h.launch_count(reset=True)
+        h.step(30)
+        assert h.launch_count() == 30
