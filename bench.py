@@ -179,11 +179,11 @@ def oracle_sample(steps: int = 1, nx: int = 32, ny: int = 32, keep: bool = False
 _POOL_SOLVER = None
 
 
-def _pool_init(nx, ny, seed):
-    """Worker set-up (untimed): the oracle's tables and one window's initial state."""
+def _pool_init(cfg, seed):
+    """Worker set-up (untimed): the oracle's tables and one problem's initial state."""
     global _POOL_SOLVER
     from oracle.solver import Solver, config_from
-    s = Solver(config_from(window_config(nx, ny)))
+    s = Solver(config_from(cfg))
     s.init_equilibrium(1.0, 0.05, -0.02, 1.2)
     s.f *= W.perturbation(s.f.shape, seed=seed, amplitude=0.02)
     _POOL_SOLVER = s
@@ -216,21 +216,25 @@ def cpu_model() -> str:
 
 class OraclePool:
     """The FP64 oracle on every host core: one spawned process per core, each
-    advancing its own nx x ny window of the workload (same velocity set,
-    physics and dt; its own seeded perturbation), all at once.  The oracle's
-    arithmetic is unchanged: the windows are independent problems, so the
-    host's throughput is their node-velocity updates over the slowest one's
-    wall time.  BLAS threads are pinned to one per process."""
+    advancing its own problem (by default an nx x ny window of the large
+    channel: same velocity set, physics and dt, its own seeded perturbation;
+    or the given configs, one per core), all at once.  The oracle's
+    arithmetic is unchanged: the problems are independent, so the host's
+    throughput is their node-velocity updates over the slowest one's wall
+    time.  BLAS threads are pinned to one per process."""
 
-    def __init__(self, workers: int = 0, nx: int = 32, ny: int = 32):
+    def __init__(self, workers: int = 0, nx: int = 32, ny: int = 32, cfgs=None, what: str = ""):
         import multiprocessing as mp
         self.workers = workers or (os.cpu_count() or 1)
         self.nx, self.ny = nx, ny
+        self.cfgs = list(cfgs[: self.workers]) if cfgs else [window_config(nx, ny)] * self.workers
+        self.workers = len(self.cfgs)
+        self.what = what or f"independent {nx}x{ny}-node windows of the workload's velocity set"
         saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
         for k in saved:
             os.environ[k] = "1"
         ctx = mp.get_context("spawn")
-        self.pools = [ctx.Pool(1, initializer=_pool_init, initargs=(nx, ny, 100 + r)) for r in range(self.workers)]
+        self.pools = [ctx.Pool(1, initializer=_pool_init, initargs=(c, 100 + r)) for r, c in enumerate(self.cfgs)]
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
@@ -248,15 +252,13 @@ class OraclePool:
         wall = time.perf_counter() - t0
         if self.V is None:
             from oracle.model import VelocitySet
-            c = W.LARGE_2D
-            self.V = VelocitySet(c["Qx"], c["Qy"], c["Qz"]).V
-        nv = self.workers * self.nx * self.ny * self.V * steps
+            self.V = sum(c["nx"] * c["ny"] * VelocitySet(c["Qx"], c["Qy"], c["Qz"]).V for c in self.cfgs)
+        nv = self.V * steps
         return nv / wall, wall, sum(o[1] for o in out)
 
     def describe(self, steps: int) -> str:
-        return (f"{self.workers} independent {self.nx}x{self.ny}-node windows of the workload's velocity set "
-                f"(one spawned process per host core, os.cpu_count() = {os.cpu_count()}, CPU: {cpu_model()}) "
-                f"x {steps} RK-3 step(s) each, FP64 numpy oracle")
+        return (f"{self.workers} {self.what} (one spawned process per host core, os.cpu_count() = "
+                f"{os.cpu_count()}, CPU: {cpu_model()}) x {steps} RK-3 step(s) each, FP64 numpy oracle")
 
     def close(self):
         for p in self.pools:
@@ -527,37 +529,112 @@ def run_gpu(args):
 # ------------------------------------------------------------------------------
 def run_batched(args):
     """4096 independent 1D channels (SplitMix64 draws) advanced together in
-    FP32, against the plain per-instance FP64 solve on the same GPU (a sample
-    of instances, each its own FP64 handle stepped on its own)."""
+    FP32 (one handle; each velocity-set group on the persistent kernel or the
+    per-stage launches, whichever hlb_autotune measured faster), against the
+    plain per-instance FP64 solve on the same GPU (a sample of instances, each
+    its own FP64 handle stepped on its own)."""
+    import ctypes
+
     import numpy as np
     import torch
 
     from paper_1708_03249_gb300 import build as hbuild
     from paper_1708_03249_gb300 import hlb
 
+    insts = with_precision(W.batched_instances(args.ninst), args.precision)
+    # the oracle's host-core pool (spawned before any CUDA call): the first
+    # seeded instances of the batch, one per core
+    pool = OraclePool(cfgs=insts, what="seeded batched channel instances (the batch's first ones)")
     torch.cuda.set_device(0)
     if not os.path.exists(hlb.LIB_PATH):
         hbuild.build()
-    insts = with_precision(W.batched_instances(args.ninst), args.precision)
     stream = torch.cuda.Stream()
     h = hlb.Handle(insts, stream=stream.cuda_stream)
     h.init_equilibrium()
     segments = h.autotune()
+    groups = {}
+    for i, c in enumerate(insts):
+        key = (c["Qx"], c["Qy"])
+        if key not in groups:
+            f = h.step_form(i)
+            groups[key] = {"velocities": 2 * c["Qx"] * max(c["Qy"], 1), "instances": 0, "values": 0,
+                           "persistent": f["persistent"], "segment_cells": f["segment_cells"], "ctas": f["ctas"],
+                           "tuned_step_ms": {"persistent": f["tuned_ms"][0], "per_stage": f["tuned_ms"][1]}}
+        groups[key]["instances"] += 1
+        groups[key]["values"] += c["nx"] * c["ny"] * groups[key]["velocities"]
     h.set_options(use_graphs=True, time_kernels=False)
     h.step(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    h.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    h.launch_count(reset=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        h.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    launches = h.launch_count(reset=True)
     nv = h.values
+    nodes, state_bytes = h.nodes, h.state_bytes
     rate32 = nv * args.steps / (ms * 1e-3)
     n, u, T, q = h.moments()
     finite = bool(np.isfinite(n).all() and np.isfinite(T).all())
+    # the stage kernels alone: per-stage launches with CUDA events (3 steps)
+    h.set_options(use_graphs=False, time_kernels=True)
+    h.kernel_times(reset=True)
+    h.step(3)
+    torch.cuda.synchronize()
+    kt = h.kernel_times(reset=True)
+    h.set_options(use_graphs=True, time_kernels=False)
+    stage_ms_per_step = kt["stage_ms"] / 3.0
+    # end to end through the C ABI with host buffers: per step the state from
+    # pinned memory (staged during the previous step), one step, the moments
+    # read back into pinned arrays while the next step runs
+    pinned = torch.empty(nv, dtype=torch.float32, pin_memory=True)
+    h.get_state(pinned.numpy())
+    moms = [torch.empty(k * nodes, dtype=torch.float64, pin_memory=True).numpy() for k in (1, 3, 1, 1)]
+    ptrs = [m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for m in moms]
+    lib = hlb.lib()
+    e2e_iters = max(2, min(args.steps, 20))
+
+    def e2e(iters):
+        h.prefetch_state(pinned.data_ptr(), state_bytes)
+        for it in range(iters):
+            h.commit_state()
+            if it + 1 < iters:
+                h.prefetch_state(pinned.data_ptr(), state_bytes)
+            h.step(1)
+            hlb._check(lib.hlb_moments_async(h._h, *ptrs))
+        hlb._check(lib.hlb_moments_wait(h._h))
+
+    e2e(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e(e2e_iters)
+    e2e_value = nv * e2e_iters / (time.perf_counter() - t0)
     h.close()
-    # per-instance FP64 solves of a sample (every 64th instance)
+    # accuracy: eight short seeded instances of the batch (all three velocity
+    # sets) on the FP32 path against the FP64 oracle from the same state
+    from oracle.solver import Solver, config_from
+    acc_cfgs = [c for c in insts[:64] if c["nx"] <= 120][:8]
+    with hlb.Handle(acc_cfgs, stream=stream.cuda_stream) as ha:
+        ha.init_equilibrium(1.0, 0.05, 0.0, 1.1)
+        f0 = ha.get_state().astype(np.float64) * W.perturbation(ha.values, seed=51, amplitude=0.05)
+        ha.set_state(f0)
+        f0 = ha.get_state().astype(np.float64)
+        acc_steps = 20
+        ha.step(acc_steps)
+        mom = ha.moments()
+    refs, off = [], 0
+    for c in acc_cfgs:
+        sv = Solver(config_from(c))
+        sv.f = f0[off:off + sv.f.size].reshape(sv.f.shape).copy()
+        off += sv.f.size
+        sv.step(acc_steps)
+        refs.append(sv.moments())
+    ref = tuple(np.concatenate([r[k].reshape(-1, 3) if k == 1 else r[k].reshape(-1) for r in refs]) for k in range(4))
+    errs = moment_errors(mom, ref)
+    # per-instance FP64 solves of a sample (every ninst/fp64_sample-th instance)
     sample = insts[:: max(1, len(insts) // args.fp64_sample)][: args.fp64_sample]
     total_nv, total_ms = 0, 0.0
     for c in sample:
@@ -574,12 +651,47 @@ def run_batched(args):
         total_nv += hh.values * args.steps
         hh.close()
     rate64 = total_nv / (total_ms * 1e-3)
+    # roofline of the stage kernels (per-stage launches: the FP32 marching
+    # kernels of every group, timed per launch)
+    peak, peak_kind = measured_peaks()
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_max_mhz") or MAX_SM_MHZ
+    hbm_ach = nv * BYTES_PER_NV_STAGE * 3 / (stage_ms_per_step * 1e-3) / 1e9
+    flops = sum(g["values"] * flops_per_nv_stage(dict(Qx=qx, Qy=qy, ny=1, advection=W.WENO5, x_basis=W.X_HALF))
+                for (qx, qy), g in groups.items())
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_ach = flops * 3 / (stage_ms_per_step * 1e-3) / 1e12
+    hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": peak, "unit": "GB/s", "frac": hbm_ach / peak,
+           "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})", "per_unit": BYTES_PER_NV_STAGE}
+    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+           "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
+    roof = dict(alu if alu["frac"] >= hbm["frac"] else hbm)
+    roof.update({"traffic": None, "kernel": "the groups' FP32 marching kernels (march1_kernel), per-stage launches",
+                 "stage_ms_per_step": stage_ms_per_step, "hbm": hbm, "alu": alu})
+    cpu_rate, _, cpu_sec = pool.run(3)
+    cpu_baseline = {"value": cpu_rate, "unit": "node-velocity updates/s", "cores": pool.workers, "kind": "oracle",
+                    "sample": pool.describe(3), "cpu_model": cpu_model(), "os_cpu_count": os.cpu_count(),
+                    "cpu_seconds": cpu_sec}
+    pool.close()
     line = {"metric": METRIC, "value": rate32, "unit": "node-velocity updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"batched_{args.ninst}_channels_splitmix64_seed{W.BATCH_SEED}",
-                       "values_per_copy": nv, "moments_finite": finite, "segment_cells": segments},
+                       "values_per_copy": nv, "moments_finite": finite, "segment_cells": segments,
+                       "l2": f"state ({state_bytes / 1e9:.2f} GB per copy) larger than L2; no flush needed",
+                       "groups": {f"{qx * 2}x{qy}": g for (qx, qy), g in groups.items()}},
+            "roofline": roof,
+            "cpu_baseline": cpu_baseline,
+            "accuracy": {"moment_linf_rel_err": errs, "bound": 1e-5, "within_bound": max(errs.values()) <= 1e-5,
+                         "case": f"{len(acc_cfgs)} short seeded instances of the batch, {acc_steps} RK-3 steps, "
+                                 "FP32 kernels vs the FP64 oracle from the same state"},
+            "e2e": {"value": e2e_value, "unit": "node-velocity updates/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": 6 * 8 * nodes, "steps": e2e_iters,
+                    "form": "per step: the state from pinned memory (hlb_prefetch_state during the previous step, "
+                            "hlb_commit_state), one RK-3 step, the moments into pinned arrays (hlb_moments_async)"},
+            "gpu_launches": launches,
+            "clocks": clocks,
             "fp64_per_instance": {"value": rate64, "unit": "node-velocity updates/s",
                                   "instances": len(sample), "dtype": "f64",
                                   "desc": "each sampled instance its own FP64 handle, stepped alone"},

@@ -444,7 +444,14 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     for (int k = 0; k < G.VZ; ++k)
         for (int j = 0; j < G.VY; ++j)
             for (int i = 0; i < G.QX2; ++i)
-                wscale[(k * G.VY + j) * G.QX2 + i] = 1.0 / (G.tx.w[i] * G.ty.w[j] * G.tz.w[k]);
+                // the power of two nearest 1/(w_x w_y w_z): the WENO weights do
+                // not change under a common scale, and a power of two makes the
+                // FP32 kernels' scaled stencils exact, so that a centre value
+                // rebuilt from its scaled copy is the stored one (a rounded
+                // scale s fl(1/s) != 1 biases every evolving value each stage,
+                // about 5e-9 of the mass per step)
+                wscale[(k * G.VY + j) * G.QX2 + i] =
+                    std::exp2(std::round(std::log2(1.0 / (G.tx.w[i] * G.ty.w[j] * G.tz.w[k]))));
     if (G.precision == HLB_FP32)
         for (double ws : wscale)
             if (!(ws < 1e36))

@@ -90,7 +90,8 @@ struct GroupDev {
     void* sums;              // R: [node][16] = n, j_x, j_y, j_z, E of the stage input at [0..4],
                              //    their compensation terms at [8..12]
     const void* inv_dx;      // R: 1/dx, concatenated per instance (same offsets as dx)
-    const void* wscale;      // R: [V] 1/(w_x w_y w_z) per velocity (WENO smoothness scale)
+    const void* wscale;      // R: [V] the power of two nearest 1/(w_x w_y w_z) per velocity (WENO
+                             //    smoothness scale; exact to apply and to undo)
     int ninst, nnodes, nrows;
     const InstDev* inst;
     const int* node_start;   // [ninst + 1]

@@ -351,8 +351,10 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
                 out = f + dt * Lval;
             } else {
                 const R fnv = fn[row_off + (size_t)x * V + v];
-                if (stage == 1) out = R(0.75) * fnv + R(0.25) * f + R(0.25) * dt * Lval;
-                else out = fnv * R(1.0 / 3.0) + R(2.0 / 3.0) * f + R(2.0 / 3.0) * dt * Lval;
+                // c f^n + (1 - c) f' as f' + c (f^n - f'): the weights sum to
+                // 1 exactly whatever the rounding of c
+                const R fp = f + dt * Lval;
+                out = fp + (stage == 1 ? R(0.75) : R(1.0 / 3.0)) * (fnv - fp);
             }
             fo[row_off + (size_t)x * V + v] = out;
         }

@@ -309,10 +309,11 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
                 out = fsub2(fc, __fmul2_rn(dt2, L));
             } else {
                 const float2 fo_n = make_float2(B.fnr[2 * q][vl], B.fnr[2 * q + 1][vl]);
-                if (stage == 1)
-                    out = __ffma2_rn(f2(0.75f), fo_n, __fmul2_rn(f2(0.25f), fsub2(fc, __fmul2_rn(dt2, L))));
-                else
-                    out = __ffma2_rn(f2(1.0f / 3.0f), fo_n, __fmul2_rn(f2(2.0f / 3.0f), fsub2(fc, __fmul2_rn(dt2, L))));
+                // c f^n + (1 - c) f' as f' + c (f^n - f'): the weights sum
+                // to 1 exactly whatever the rounding of c (with 1/3 and 2/3
+                // each rounded, FP32 gains mass 2^-25 per step)
+                const float2 fp = fsub2(fc, __fmul2_rn(dt2, L));
+                out = __ffma2_rn(f2(stage == 1 ? 0.75f : 1.0f / 3.0f), fsub2(fo_n, fp), fp);
             }
             fov[roff + (x0 + 2 * q) * V] = out.x;
             if (2 * q + 1 < n4) fov[roff + (x0 + 2 * q + 1) * V] = out.y;

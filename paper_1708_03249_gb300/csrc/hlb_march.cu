@@ -267,8 +267,10 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
                 out = fc[r] + dt * L;
             } else {
                 const R fo_n = B.fnr[r][t];
-                out = stage == 1 ? R(0.75) * fo_n + R(0.25) * fc[r] + R(0.25) * dt * L
-                                 : fo_n * R(1.0 / 3.0) + R(2.0 / 3.0) * fc[r] + R(2.0 / 3.0) * dt * L;
+                // c f^n + (1 - c) f' as f' + c (f^n - f'): the weights sum to
+                // 1 exactly whatever the rounding of c
+                const R fp = fc[r] + dt * L;
+                out = fp + (stage == 1 ? R(0.75) : R(1.0 / 3.0)) * (fo_n - fp);
             }
             if (valid[r]) fov[roff[r] + x * V] = out;
         }

@@ -423,15 +423,21 @@ def test_fp32_batched_mixed_instances():
         assert N[i] == pytest.approx(s.total_number(), rel=2e-6)
 
 
-def test_fp32_particle_number_conserved():
+@pytest.mark.parametrize("persistent", [True, False])
+def test_fp32_particle_number_conserved(persistent):
+    # N = int n dx is conserved by the scheme (flux telescoping, wall balance,
+    # K column sums, BGK mass); in FP32 only rounding noise may move it.  Over
+    # 3000 steps a bias of one ulp-fraction per step (e.g. RK-3 weights that
+    # do not sum to 1 after rounding: 2^-25 per step, 9e-5 here) shows.
     from paper_1708_03249_gb300 import hlb
     cfg = W.scaled(W.channel_1d_stretched(0.1), nx=64)
     with hlb.Handle(cfg, stream=_stream()) as h:
+        h.set_persistent(persistent)
         h.init_equilibrium()
         N0 = h.diag()[0][0]
-        h.step(200)
+        h.step(3000)
         N1, r = h.diag()
-    assert N1[0] == pytest.approx(N0, rel=1e-5)
+    assert N1[0] == pytest.approx(N0, rel=2e-6)
     assert r[0] > 0
 
 

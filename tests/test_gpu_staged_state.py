@@ -88,6 +88,10 @@ def test_autotune_keeps_the_state_and_the_results():
             W.make(Qx=4, Qy=4, nx=90, ny=7, Ly=0.3, Kn=0.5, precision=W.FP32)]
     with hlb.Handle(cfgs) as a, hlb.Handle(cfgs) as b:
         for h in (a, b):
+            # the per-stage launches (the tuner may also move a group to the
+            # persistent kernel, which rounds the moment sums in another order;
+            # tests/test_gpu_persistent.py covers that)
+            h.set_persistent(False)
             h.init_equilibrium(1.0, 0.05, 0.0, 1.0)
             h.step(2)
         before = a.get_state()
