@@ -94,6 +94,10 @@ struct Group {
     PinnedBuf h_mom;                         // pinned word for the non-finite flag (hlb_moments), first use
     DevBuf d_Td, d_invdx, d_wscale, d_coef, d_works, d_err, d_recf, d_Tf, d_sums;
     DevBuf d_KxT, d_KxJ;                     // FP64 Kx transposed and its jump factors (kx_global groups only)
+    DevBuf d_gquad, d_glrule;                // G^{+-} by quadrature above the recurrence's stable order (FP64)
+    DevBuf d_wpart, d_wcount;                // wall kernel: per-chunk partial fluxes, row counters
+    int wchunks = 1;
+    bool quad_x = false;
     int vchunks = 1;                         // CTAs per node of the generic stage kernel
     hlb::GroupDev dev{};
     int block = 256, grid = 1;
@@ -313,6 +317,12 @@ void fill_dev(Group& G) {
     d.wait_ns = kDefaultWaitNs;
     d.inject_stall = 0;
     d.force_form = G.force_form;
+    d.quad_x = G.quad_x ? 1 : 0;
+    d.wchunks = G.wchunks;
+    d.wpart = static_cast<double*>(G.d_wpart.p);
+    d.wcount = static_cast<unsigned*>(G.d_wcount.p);
+    d.gquad = static_cast<double*>(G.d_gquad.p);
+    d.glrule = static_cast<const double*>(G.d_glrule.p);
 }
 
 // The marching kernel's work list: one CTA per (p_z slab, instance, strip of
@@ -487,6 +497,18 @@ hlb_status build_group(hlb_handle* h, Group& G) {
         if ((s = upload(G.d_KxJ, J)) != HLB_OK) return s;
     }
     if ((s = upload_real(G.d_p, p, G.precision)) != HLB_OK) return s;
+    // FP64 half-range Hermite groups above the recurrence's stable order: the
+    // coefficients G^{+-} of every collisional node by quadrature, once per
+    // node and stage (quad_coef_kernel)
+    if (G.precision == HLB_FP64 && G.tx.half && !G.x_full && c0.x_basis == HLB_X_HALF_RANGE &&
+        G.Nx > hlb::kStableRecurrenceN) {
+        std::vector<double> gx, gw;
+        hlb::gauss_legendre_rule(hlb::kQuadNodes, gx, gw);
+        gx.insert(gx.end(), gw.begin(), gw.end());
+        if ((s = upload(G.d_glrule, gx)) != HLB_OK) return s;
+        if ((s = upload(G.d_gquad, std::vector<double>((size_t)G.nnodes * 2 * (G.Nx + 1), 0.0))) != HLB_OK) return s;
+        G.quad_x = true;
+    }
     if ((s = upload(G.d_pd, p)) != HLB_OK) return s;
     if ((s = upload_real(G.d_T, T, G.precision)) != HLB_OK) return s;
     if ((s = upload(G.d_rec, rec)) != HLB_OK) return s;
@@ -496,6 +518,20 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     if ((s = upload(G.d_nw, std::vector<double>((size_t)G.nrows * 2, 0.0))) != HLB_OK) return s;
     if ((s = upload(G.d_resid, std::vector<double>(G.members.size() * 2, 0.0))) != HLB_OK) return s;
     if ((s = upload(G.d_err, std::vector<int>(4, 0))) != HLB_OK) return s;
+    {
+        // the wall kernel's rows over several CTAs when there are few rows of
+        // many velocities (one CTA per row ran the 400-velocity FP64 fluxes of
+        // the order-200 set on 8 SMs): chunks of about 64 velocities, up to
+        // two CTAs per SM in all
+        int dev = 0, nsm = 1;
+        HLB_CUDA(cudaGetDevice(&dev));
+        HLB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        G.wchunks = std::max(1, std::min((G.V + 63) / 64, (2 * nsm + G.nrows - 1) / G.nrows));
+        if (G.wchunks > 1) {
+            if ((s = upload(G.d_wpart, std::vector<double>((size_t)G.nrows * G.wchunks * 2, 0.0))) != HLB_OK) return s;
+            if ((s = upload(G.d_wcount, std::vector<unsigned>((size_t)G.nrows, 0u))) != HLB_OK) return s;
+        }
+    }
     if ((s = refresh_walls(h, G)) != HLB_OK) return s;
 
     // state buffers
@@ -590,19 +626,39 @@ hlb_status build_group(hlb_handle* h, Group& G) {
 
     // launch shape of the stage kernel.  With Kx in global memory each
     // velocity's force term is a 2Qx-term dot product (FP64), so the velocities
-    // of a node are split over several CTAs (about 64 each, enough CTAs for two
-    // per SM); the CTAs of one node form its moments redundantly.
+    // of a node are split over several CTAs (the balanced split below); the
+    // CTAs of one node form its moments redundantly.
     int per_sm = 1, dev = 0, nsm = 1;
     HLB_CUDA(cudaGetDevice(&dev));
     HLB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     G.vchunks = 1;
+    auto block_of = [&](int vc) { return std::min(256, std::max(32, ((G.V + vc - 1) / vc + 31) / 32 * 32)); };
     if (G.d_KxT.p) {
-        const int by_size = (G.V + 63) / 64;
-        const int by_fill = (2 * nsm + G.nnodes - 1) / G.nnodes;
-        G.vchunks = std::max(1, std::min(by_size, by_fill));
+        // the split that finishes soonest: rounds of the grid (ceil of the
+        // items over the resident CTAs) times the velocities per CTA, for
+        // splits from one CTA per node up to about 64 velocities per CTA (the
+        // last round of a ragged split runs with few CTAs busy)
+        const int by_size = std::max(1, (G.V + 63) / 64);
+        long long best = -1;
+        int best_vc = 1;
+        for (int vc = 1; vc <= by_size; ++vc) {
+            G.vchunks = vc;
+            fill_dev(G);
+            const int blk = block_of(vc);
+            const size_t sm = hlb::stage_smem_bytes(G.dev, G.precision, blk);
+            if (sm > 200 * 1024) continue;
+            HLB_CUDA(hlb::prepare_stage(G.precision, G.adv, sm));
+            int per = 1;
+            HLB_CUDA(hlb::stage_occupancy(G.precision, G.adv, blk, sm, &per));
+            const long long resident = (long long)nsm * std::max(1, per);
+            const long long rounds = ((long long)G.nnodes * vc + resident - 1) / resident;
+            const long long cost = rounds * blk;
+            if (best < 0 || cost < best) { best = cost; best_vc = vc; }
+        }
+        G.vchunks = best_vc;
     }
     fill_dev(G);
-    G.block = std::min(256, std::max(32, ((G.V + G.vchunks - 1) / G.vchunks + 31) / 32 * 32));
+    G.block = block_of(G.vchunks);
     G.smem = hlb::stage_smem_bytes(G.dev, G.precision, G.block);
     if (G.smem > 200 * 1024) return fail(HLB_EUNSUPPORTED, "velocity set too large for the stage kernel's shared memory");
     HLB_CUDA(hlb::prepare_stage(G.precision, G.adv, G.smem));
@@ -677,6 +733,7 @@ void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
         }
         NvtxRange range(kStageNames[st]);
         const bool march = G.march_ok && !group_has_z_force(h, G);
+        if (G.quad_x) hlb::launch_quad_coef(G.dev, ins[st], st_);
         if (march) hlb::launch_node(G.precision, G.dev, ins[st], st_);
         hlb::launch_wall(G.precision, G.adv, G.dev, ins[st], st_);
         if (h->time_kernels) cudaEventRecord(e1, st_);
@@ -719,7 +776,9 @@ void enqueue_step(hlb_handle* h) {
 long long kernels_per_step(hlb_handle* h) {
     long long n = 0;
     for (auto& G : h->groups)
-        n += persist_on(h, *G) ? 1 : 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2) + (G->has_field ? 3 : 0);
+        n += persist_on(h, *G) ? 1
+                               : 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2) + (G->has_field ? 3 : 0) +
+                                     (G->quad_x ? 3 : 0);
     return n;
 }
 

@@ -124,7 +124,20 @@ struct GroupDev {
     int inject_stall;        // test hook: nonzero withholds the copies of a marching CTA's second step
     int force_form;          // FP32 marching kernels: force term by FMA (0), 3xTF32 (1) or split-BF16 (2)
                              // tensor-core products
+    // FP64 half-range groups above the recurrence's stable order: the
+    // coefficients G^{+-}_l of every collisional node by quadrature of the
+    // projection integrals (quad_coef_kernel), read by the stage kernel
+    int quad_x;              // 1: G^{+-} come from gquad
+    double* gquad;           // [nnodes][2][Nx + 1]
+    const double* glrule;    // [2][kQuadNodes]: Gauss-Legendre nodes and weights on [-1, 1]
+    // wall kernel: each row's velocities over wchunks CTAs, their partial
+    // incident fluxes in wpart [nrows][wchunks][2], summed in chunk order by the
+    // row's last CTA (wcount [nrows], zero between launches)
+    int wchunks;
+    double* wpart;
+    unsigned* wcount;
 };
+constexpr int kQuadNodes = 20;   // points per panel of the projection quadrature
 
 }  // namespace hlb
 
@@ -137,6 +150,10 @@ cudaError_t stage_occupancy(int precision, int adv, int block, size_t smem, int*
 void launch_stage(int precision, int adv, const GroupDev& g, const void* fs, const void* fn, void* fo,
                   int stage, int grid, int block, size_t smem, cudaStream_t st);
 void launch_wall(int precision, int adv, const GroupDev& g, const void* fs, cudaStream_t st);
+// G^{+-}_l (l <= Nx) of every collisional node of an FP64 half-range group by
+// quadrature of the projection integrals (hlb_kernels.cu)
+void launch_quad_coef(const GroupDev& g, const void* fs, cudaStream_t st);
+void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w);
 void launch_node(int precision, const GroupDev& g, const void* fs, cudaStream_t st);
 cudaError_t prepare_node();
 // Marching stage kernel for (QX2, VY, TY); returns false if no instantiation exists.

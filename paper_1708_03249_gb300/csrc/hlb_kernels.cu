@@ -108,8 +108,14 @@ __device__ __forceinline__ void face_pair(const R* w, bool pos, R& Fp, R& Fm) {
 // ---------------------------------------------------------------------------
 // stage kernel
 // ---------------------------------------------------------------------------
+// CTAs per SM the generic stage kernel is compiled for (2: at most 128
+// registers per thread, so that two 256-thread CTAs fit an SM; on the order-200
+// set 0.0927 ms per stage launch against 0.0989 ms at 1, eight ballistic cases).
+#ifndef HLB_STAGE_MIN_BLOCKS
+#define HLB_STAGE_MIN_BLOCKS 2
+#endif
 template <typename R, int ADV>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, HLB_STAGE_MIN_BLOCKS)
 stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ fn,
              R* __restrict__ fo, int stage) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -203,7 +209,12 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
                 sScal[0] = n;
                 sScal[1] = n * I.inv_Kn;     // 1/tau
             }
-            node_coefficients(g, tid, ux, uy, uz, T, sRec, sCoef);
+            if (g.quad_x && tid < 2) {          // G^{+-} by quadrature (quad_coef_kernel)
+                const double* q = g.gquad + ((size_t)node * 2 + tid) * (g.Nx + 1);
+                for (int l = 0; l <= g.Nx; ++l) sCoef[tid * (g.Nx + 1) + l] = q[l];
+            } else {
+                node_coefficients(g, tid, ux, uy, uz, T, sRec, sCoef);
+            }
         }
         __syncthreads();
         // 2. equilibrium factors g_x (times n), g_y, g_z
@@ -369,7 +380,7 @@ template <typename R, int ADV>
 __global__ void __launch_bounds__(256)
 wall_kernel(const GroupDev g, const R* __restrict__ fs) {
     __shared__ double red[2][8];
-    const int row = blockIdx.x;
+    const int row = blockIdx.x / g.wchunks, chunk = blockIdx.x - row * g.wchunks;
     if (row >= g.nrows) return;
     const int ii = g.ninst > 1 ? find_slot(g.row_start, g.ninst, row) : 0;
     const InstDev I = g.inst[ii];
@@ -377,7 +388,8 @@ wall_kernel(const GroupDev g, const R* __restrict__ fs) {
     const int nx = I.nx, V = g.V, QX2 = g.QX2;
     const R* frow = fs + (size_t)I.f_off + (size_t)y * nx * V;
     double accL = 0.0, accR = 0.0;
-    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+    const int Vc = (V + g.wchunks - 1) / g.wchunks, v0 = chunk * Vc, v1 = min(V, v0 + Vc);
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
         const int ix = v % QX2;
         const double px = g.pd[ix];
         const size_t a = px < 0 ? 0 : (size_t)(nx - 1) * V, step = px < 0 ? (size_t)V : (size_t)0 - (size_t)V;
@@ -416,8 +428,122 @@ wall_kernel(const GroupDev g, const R* __restrict__ fs) {
     if (threadIdx.x == 0) {
         double sl = 0.0, sr = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sl += red[0][w]; sr += red[1][w]; }
+        if (g.wchunks > 1) {
+            // this chunk's partial sums; the row's last CTA adds them in chunk
+            // order (the same result whatever order the CTAs finish in)
+            double* part = g.wpart + (size_t)row * g.wchunks * 2;
+            part[2 * chunk] = sl;
+            part[2 * chunk + 1] = sr;
+            __threadfence();
+            if (atomicAdd(g.wcount + row, 1u) != (unsigned)(g.wchunks - 1)) return;
+            __threadfence();
+            sl = sr = 0.0;
+            for (int c = 0; c < g.wchunks; ++c) {
+                sl += __ldcg(part + 2 * c);
+                sr += __ldcg(part + 2 * c + 1);
+            }
+            atomicExch(g.wcount + row, 0u);
+        }
         g.nw[(size_t)row * 2 + 0] = -sl / I.den_left;
         g.nw[(size_t)row * 2 + 1] = -sr / I.den_right;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The half-range equilibrium coefficients of FP64 groups above the
+// recurrence's stable order: G^{+-}_l = int_0^inf g(+-p) h_l(p) dp (l <= Nx),
+// g the Gaussian of the node's u_x and T (Sec. IV.B, the projection of Eq.
+// "eq:hh_gk"), by composite Gauss-Legendre quadrature over [0, |u_x| +
+// 15 sqrt(T)] in panels of width sqrt(T) (kQuadNodes points each; 300-440
+// points; 1e-14 of max |G| against a 30-point rule on panels of 0.02
+// sqrt(T)), h_l(p) by the three-term recurrence of the orthonormal basis
+// (forward evaluation at a point is stable).  The integration-by-parts
+// recurrence of node_coefficients carries its rounding (and that of its erf
+// and exp start) along a solution that grows about threefold per order:
+// 5e-7 of max g at N = 20.  One CTA per node, both signs from the same h_l(p);
+// moments in FP64 as the stage kernel forms them.
+// ---------------------------------------------------------------------------
+template <int NMAX>
+__global__ void __launch_bounds__(256) quad_coef_kernel(const GroupDev g, const double* __restrict__ fs) {
+    __shared__ double red[8][2 * NMAX];
+    __shared__ double sMom[8];
+    const int node = blockIdx.x;
+    const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
+    const InstDev& I = g.inst[ii];
+    if (I.inv_Kn == 0.0) return;                // collisionless: no equilibrium is formed
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int V = g.V, QX2 = g.QX2, VY = g.VY, Nx = g.Nx;
+    const double* f = fs + I.f_off + (size_t)(node - I.node_off) * V;
+    // moments of the node
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
+    for (int v = tid; v < V; v += blockDim.x) {
+        const double val = f[v];
+        const double px = g.pd[v % QX2], py = g.pd[QX2 + (v / QX2) % VY], pz = g.pd[QX2 + VY + v / (QX2 * VY)];
+        a0 += val;
+        a1 += px * val;
+        a2 += py * val;
+        a3 += pz * val;
+        a4 += (px * px + py * py + pz * pz) * val;
+    }
+    a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2); a3 = warp_sum(a3); a4 = warp_sum(a4);
+    if (lane == 0) { red[warp][0] = a0; red[warp][1] = a1; red[warp][2] = a2; red[warp][3] = a3; red[warp][4] = a4; }
+    __syncthreads();
+    if (tid == 0) {
+        double m[5] = {0, 0, 0, 0, 0};
+        for (int w = 0; w < nw; ++w)
+            for (int k = 0; k < 5; ++k) m[k] += red[w][k];
+        const double n = m[0], ux = m[1] / n, uy = m[2] / n, uz = m[3] / n;
+        sMom[0] = ux;
+        sMom[1] = (m[4] - n * (ux * ux + uy * uy + uz * uz)) / (g.D * n);
+    }
+    __syncthreads();
+    const double ux = sMom[0], T = sMom[1];
+    const double sT = sqrt(T), width = sT;
+    const int panels = (int)ceil((fabs(ux) + 15.0 * sT) / width);
+    const int npts = panels * kQuadNodes;
+    const double norm = 1.0 / (kSqrt2Pi * sT), i2T = 0.5 / T;
+    const double* ra = g.rec;
+    const double* rb = g.rec + Nx;
+    const double* rc = g.rec + 2 * Nx;
+    const double h00 = g.rec[3 * Nx];
+    double Gp[NMAX], Gm[NMAX];
+#pragma unroll
+    for (int l = 0; l < NMAX; ++l) Gp[l] = Gm[l] = 0.0;
+    for (int k = tid; k < npts; k += blockDim.x) {
+        const int pnl = k / kQuadNodes, i = k - pnl * kQuadNodes;
+        const double p = (pnl + 0.5 * (1.0 + g.glrule[i])) * width;
+        const double w0 = 0.5 * width * g.glrule[kQuadNodes + i] * norm;
+        const double dp = p - ux, dm = p + ux;
+        const double wp = w0 * exp(-dp * dp * i2T), wm = w0 * exp(-dm * dm * i2T);
+        double hm = 0.0, h = h00;
+        Gp[0] += wp * h;
+        Gm[0] += wm * h;
+#pragma unroll
+        for (int l = 0; l < NMAX - 1; ++l) {
+            if (l < Nx) {
+                const double hn = (ra[l] * p + rb[l]) * h + rc[l] * hm;
+                hm = h;
+                h = hn;
+                Gp[l + 1] += wp * h;
+                Gm[l + 1] += wm * h;
+            }
+        }
+    }
+    __syncthreads();                            // red[] is reused below
+#pragma unroll
+    for (int l = 0; l < NMAX; ++l) {
+        if (l <= Nx) {
+            const double sp = warp_sum(Gp[l]), sm = warp_sum(Gm[l]);
+            if (lane == 0) { red[warp][l] = sp; red[warp][NMAX + l] = sm; }
+        }
+    }
+    __syncthreads();
+    double* out = g.gquad + (size_t)node * 2 * (Nx + 1);
+    for (int t = tid; t < 2 * (Nx + 1); t += blockDim.x) {
+        const int sg = t / (Nx + 1), l = t - sg * (Nx + 1);
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) acc += red[w][sg * NMAX + l];
+        out[t] = acc;
     }
 }
 
@@ -704,14 +830,19 @@ void launch_stage(int precision, int adv, const GroupDev& g, const void* fs, con
     }
 }
 
+void launch_quad_coef(const GroupDev& g, const void* fs, cudaStream_t st) {
+    if (g.Nx < 24) quad_coef_kernel<24><<<g.nnodes, 256, 0, st>>>(g, (const double*)fs);
+    else quad_coef_kernel<32><<<g.nnodes, 256, 0, st>>>(g, (const double*)fs);
+}
+
 void launch_wall(int precision, int adv, const GroupDev& g, const void* fs, cudaStream_t st) {
     const int block = 128;
     if (precision == HLB_FP64_) {
-        if (adv == HLB_WENO5_) wall_kernel<double, HLB_WENO5_><<<g.nrows, block, 0, st>>>(g, (const double*)fs);
-        else wall_kernel<double, HLB_UPWIND2_><<<g.nrows, block, 0, st>>>(g, (const double*)fs);
+        if (adv == HLB_WENO5_) wall_kernel<double, HLB_WENO5_><<<g.nrows * g.wchunks, block, 0, st>>>(g, (const double*)fs);
+        else wall_kernel<double, HLB_UPWIND2_><<<g.nrows * g.wchunks, block, 0, st>>>(g, (const double*)fs);
     } else {
-        if (adv == HLB_WENO5_) wall_kernel<float, HLB_WENO5_><<<g.nrows, block, 0, st>>>(g, (const float*)fs);
-        else wall_kernel<float, HLB_UPWIND2_><<<g.nrows, block, 0, st>>>(g, (const float*)fs);
+        if (adv == HLB_WENO5_) wall_kernel<float, HLB_WENO5_><<<g.nrows * g.wchunks, block, 0, st>>>(g, (const float*)fs);
+        else wall_kernel<float, HLB_UPWIND2_><<<g.nrows * g.wchunks, block, 0, st>>>(g, (const float*)fs);
     }
 }
 

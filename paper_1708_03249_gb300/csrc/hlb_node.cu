@@ -187,8 +187,14 @@ __global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __r
                     for (int role = 0; role < 4; ++role)
                         node_coefficients_df(g, role, sIn[lane], sRecF, sGF + lane * ncoef);
                 } else {
-                    for (int role = 0; role < 4; ++role)
-                        node_coefficients(g, role, ux, uy, uz, T, sRec, sG + lane * ncoef);
+                    for (int role = 0; role < 4; ++role) {
+                        if (g.quad_x && role < 2) {      // G^{+-} by quadrature (quad_coef_kernel)
+                            const double* q = g.gquad + ((size_t)node * 2 + role) * (Nx + 1);
+                            for (int l = 0; l <= Nx; ++l) sG[lane * ncoef + role * (Nx + 1) + l] = q[l];
+                        } else {
+                            node_coefficients(g, role, ux, uy, uz, T, sRec, sG + lane * ncoef);
+                        }
+                    }
                 }
             }
         }

@@ -506,4 +506,6 @@ void grid_widths(int nx, double L, double A, std::vector<double>& dx) {
     }
 }
 
+void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) { gauss_legendre(n, x, w); }
+
 }  // namespace hlb

@@ -184,12 +184,16 @@ def test_fp64_hhlb_20_200_paper_set_in_one_handle():
     _check_fp64(got, refs, 1e-11)
 
 
-@pytest.mark.parametrize("Qx,Qy,Nx_eq,adv", [(200, 4, 12, W.WENO5), (200, 0, 12, W.UPWIND2)])
+@pytest.mark.parametrize("Qx,Qy,Nx_eq,adv", [(200, 4, 12, W.WENO5), (200, 0, 12, W.UPWIND2),
+                                              (200, 0, 20, W.WENO5), (200, 4, 20, W.UPWIND2),
+                                              (16, 0, 15, W.WENO5)])
 def test_fp64_high_order_collisional(Qx, Qy, Nx_eq, adv):
     # BGK at the order-200 set (the oracle's stored tables; no mpmath on
     # every machine), also with a p_y axis (1600 velocities, 19 CTAs per
-    # node).  The per-node equilibrium recurrence on the device is accurate
-    # to ~3^N eps: N = 12 keeps it below 1e-10.
+    # node).  Up to N = 12 the per-node equilibrium recurrence on the device
+    # is accurate to ~3^N eps; above it (N = 20: the paper's HHLB(20;200), and
+    # N = 15 at Q = 16 on the marching path) the coefficients G^{+-} come from
+    # the quadrature kernel.
     cfg = W.make(Qx=Qx, Qy=Qy, Nx_eq=Nx_eq, nx=16, stretch_A=0.8, advection=adv, precision=W.FP64,
                  T_left=0.8, T_right=1.3, Kn=0.3, dt=2e-4, **W.gravity(0.5, 30.0))
     got, mom, N, refs = run_pair(cfg, 10, init=(1.0, 0.05, 0.0, 1.0))
