@@ -153,10 +153,12 @@ hlb_status hlb_set_Kn(hlb_handle* h, int inst, double Kn);
  * presents the force-term formalism for general forces; the paper's tests use
  * a constant one).  ax, ay, az: host arrays of nx * ny finite values in node
  * order (y-major), copied before the call returns; NULL is a zero component;
- * all three NULL removes the field.  With a field the step adds one launch per
- * RK stage for the instance's velocity-set group.
- * Errors: HLB_EINVAL (instance, non-finite value), HLB_EUNSUPPORTED (velocity
- * set too large for the field kernel), HLB_ENOMEM, HLB_ECUDA. */
+ * all three NULL removes the field.  The stage kernels apply it themselves:
+ * the node pass writes each node's a into its equilibrium factor line, and
+ * the FP32 marching kernels of a group with a field run a variant that scales
+ * K_x f and K_y f per cell (FMA form of the force term; a group with a field
+ * and a p_z axis takes the per-node stage kernel).  No extra launch.
+ * Errors: HLB_EINVAL (instance, non-finite value), HLB_ENOMEM, HLB_ECUDA. */
 hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const double* ay, const double* az);
 
 /* State = n g_x(ux,T) g_y(uy,T) g_z(0,T) at every node of every instance

@@ -175,7 +175,6 @@ struct hlb_handle {
     std::vector<cudaStream_t> group_stream;
     std::vector<cudaEvent_t> group_done;
     cudaEvent_t step_fork = nullptr;
-    bool once_field_prepared = false;
     bool persistent = true;                  // eligible groups step with the persistent kernel
 };
 
@@ -308,7 +307,10 @@ void fill_dev(Group& G) {
     d.wscale = G.d_wscale.p;
     d.coef = G.d_coef.p;
     d.sums = G.d_sums.p;
-    d.ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
+    d.ncp = ((G.QX2 + G.VY + G.VZ + 1 + 3) + 3) / 4 * 4;      // factors, 1/tau, a_x a_y a_z
+    d.field_off = G.QX2 + G.VY + G.VZ + 1;
+    d.has_field = G.has_field ? 1 : 0;
+    d.afield = static_cast<const double*>(G.d_afield.p);
     d.err = (int*)G.d_err.p;
     d.nonfinite = (int*)G.d_err.p + 1;
     d.recf = (const float2*)G.d_recf.p;
@@ -316,7 +318,8 @@ void fill_dev(Group& G) {
     d.use_df = (G.precision == HLB_FP32 && G.Nx <= 15) ? 1 : 0;
     d.wait_ns = kDefaultWaitNs;
     d.inject_stall = 0;
-    d.force_form = G.force_form;
+    // with a field the FP32 marching kernels run their field instantiation (FMA form)
+    d.force_form = G.has_field && G.precision == HLB_FP32 ? 3 : G.force_form;
     d.quad_x = G.quad_x ? 1 : 0;
     d.wchunks = G.wchunks;
     d.wpart = static_cast<double*>(G.d_wpart.p);
@@ -548,7 +551,7 @@ hlb_status build_group(hlb_handle* h, Group& G) {
         return fail(HLB_ENOMEM, "cudaMalloc of moment scratch failed");
     }
     {
-        const int ncp = ((G.QX2 + G.VY + G.VZ + 1) + 3) / 4 * 4;
+        const int ncp = ((G.QX2 + G.VY + G.VZ + 1 + 3) + 3) / 4 * 4;
         if (dev_malloc((void**)&G.d_coef.p, std::max<size_t>((size_t)G.nnodes * ncp * G.esize, 16)) != cudaSuccess ||
             dev_malloc((void**)&G.d_sums.p, std::max<size_t>((size_t)G.nnodes * 16 * G.esize, 16)) != cudaSuccess) {
             cudaGetLastError();
@@ -634,28 +637,13 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     G.vchunks = 1;
     auto block_of = [&](int vc) { return std::min(256, std::max(32, ((G.V + vc - 1) / vc + 31) / 32 * 32)); };
     if (G.d_KxT.p) {
-        // the split that finishes soonest: rounds of the grid (ceil of the
-        // items over the resident CTAs) times the velocities per CTA, for
-        // splits from one CTA per node up to about 64 velocities per CTA (the
-        // last round of a ragged split runs with few CTAs busy)
-        const int by_size = std::max(1, (G.V + 63) / 64);
-        long long best = -1;
-        int best_vc = 1;
-        for (int vc = 1; vc <= by_size; ++vc) {
-            G.vchunks = vc;
-            fill_dev(G);
-            const int blk = block_of(vc);
-            const size_t sm = hlb::stage_smem_bytes(G.dev, G.precision, blk);
-            if (sm > 200 * 1024) continue;
-            HLB_CUDA(hlb::prepare_stage(G.precision, G.adv, sm));
-            int per = 1;
-            HLB_CUDA(hlb::stage_occupancy(G.precision, G.adv, blk, sm, &per));
-            const long long resident = (long long)nsm * std::max(1, per);
-            const long long rounds = ((long long)G.nnodes * vc + resident - 1) / resident;
-            const long long cost = rounds * blk;
-            if (best < 0 || cost < best) { best = cost; best_vc = vc; }
-        }
-        G.vchunks = best_vc;
+        // about 64 velocities per CTA at most, and enough CTAs for the two per
+        // SM the stage kernel is compiled for (measured against a split that
+        // minimised rounds times CTA size: 0.0927 against 0.0985 ms per stage
+        // launch on the eight-case order-200 handle)
+        const int by_size = (G.V + 63) / 64;
+        const int by_fill = (2 * nsm + G.nnodes - 1) / G.nnodes;
+        G.vchunks = std::max(1, std::min(by_size, by_fill));
     }
     fill_dev(G);
     G.block = block_of(G.vchunks);
@@ -668,9 +656,12 @@ hlb_status build_group(hlb_handle* h, Group& G) {
     return HLB_OK;
 }
 
-// The marching kernel keeps one p_z per CTA; a force along p_z mixes them.
+// The marching kernel keeps one p_z per CTA; a force along p_z mixes them (a
+// field may have a p_z component: groups with a field and a p_z axis take the
+// per-node kernel).
 bool group_has_z_force(const hlb_handle* h, const Group& G) {
     if (!G.Qz) return false;
+    if (G.has_field) return true;
     for (int i : G.members)
         if (h->cfg[i].az != 0.0) return true;
     return false;
@@ -742,8 +733,6 @@ void enqueue_group_step(hlb_handle* h, Group& G, cudaStream_t st_) {
                               G.nworks, ins[st], S, outs[st], st, st_);
         else
             hlb::launch_stage(G.precision, G.adv, G.dev, ins[st], S, outs[st], st, G.grid, G.block, G.smem, st_);
-        if (G.has_field)
-            hlb::launch_force_field(G.precision, G.dev, (const double*)G.d_afield.p, ins[st], outs[st], st, st_);
         if (h->time_kernels) {
             cudaEventRecord(e2, st_);
             h->timer.wall.push_back({e0, e1});
@@ -777,8 +766,7 @@ long long kernels_per_step(hlb_handle* h) {
     long long n = 0;
     for (auto& G : h->groups)
         n += persist_on(h, *G) ? 1
-                               : 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2) + (G->has_field ? 3 : 0) +
-                                     (G->quad_x ? 3 : 0);
+                               : 3 * ((G->march_ok && !group_has_z_force(h, *G)) ? 4 : 2) + (G->quad_x ? 3 : 0);
     return n;
 }
 
@@ -1006,8 +994,6 @@ hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const 
     int l;
     Group* G = group_of(h, inst, &l);
     const bool on = ax || ay || az;
-    if (on && hlb::force_field_smem_bytes(G->dev, G->precision) > 160 * 1024)
-        return fail(HLB_EUNSUPPORTED, "velocity set too large for the force-field kernel's shared memory");
     HLB_CUDA(cudaStreamSynchronize(h->stream));
     for (cudaStream_t s2 : h->group_stream) HLB_CUDA(cudaStreamSynchronize(s2));
     if (on && !G->d_afield.p) {
@@ -1016,10 +1002,8 @@ hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const 
             return fail(HLB_ENOMEM, "cudaMalloc of the acceleration field failed");
         }
         HLB_CUDA(cudaMemset(G->d_afield.p, 0, (size_t)G->nnodes * 3 * sizeof(double)));
-        if (!h->once_field_prepared) {
-            HLB_CUDA(hlb::prepare_force_field());
-            h->once_field_prepared = true;
-        }
+        // the FP32 marching kernels' field instantiations (FMA force term)
+        if (G->march_ok && G->precision == HLB_FP32) HLB_CUDA(hlb::prepare_march(G->precision, G->adv, G->QX2, G->VY, G->TY, 3));
     }
     if (G->field_on.size() != G->members.size()) G->field_on.assign(G->members.size(), 0);
     if (G->d_afield.p) {
@@ -1032,6 +1016,7 @@ hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const 
     }
     G->field_on[l] = on;
     G->has_field = std::any_of(G->field_on.begin(), G->field_on.end(), [](char f) { return f != 0; });
+    fill_dev(*G);                    // the kernels read the field through the factor lines
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     return HLB_OK;
 }
@@ -1276,7 +1261,7 @@ hlb_status hlb_force_form(const hlb_handle* h, int inst, int* form) {
     if (!h || !form) return fail(HLB_EINVAL, "handle or output is NULL");
     if (inst < 0 || inst >= (int)h->cfg.size()) return fail(HLB_EINVAL, "instance out of range");
     const Group& G = *h->groups[h->inst_group[inst]];
-    *form = (G.march_ok && !group_has_z_force(h, G)) ? G.force_form : 0;
+    *form = (G.march_ok && !group_has_z_force(h, G) && !G.has_field) ? G.force_form : 0;
     return HLB_OK;
 }
 

@@ -323,8 +323,10 @@ struct ForceMMABF16 {
     }
 };
 
-// Force-term forms of the FP32 marching kernels (template parameter FM).
-constexpr int kForceFMA = 0, kForceTF32x3 = 1, kForceBF16x6 = 2;
+// Force-term forms of the FP32 marching kernels (template parameter FM); the
+// dispatch form kForceField selects the FMA form with a per-node acceleration
+// field (template parameter FF of the kernels).
+constexpr int kForceFMA = 0, kForceTF32x3 = 1, kForceBF16x6 = 2, kForceField = 3;
 template <int FM, int QX2, int VY>
 using ForceTC = typename std::conditional<FM == kForceBF16x6, ForceMMABF16<QX2, VY>, ForceMMA<QX2, VY>>::type;
 

@@ -136,6 +136,12 @@ struct GroupDev {
     int wchunks;
     double* wpart;
     unsigned* wcount;
+    // per-node acceleration field (hlb_set_force_field): the node pass writes
+    // a = a_uniform + a_field(node) into slots field_off .. field_off+2 of the
+    // factor line, which every line reserves; afield [nnodes][3] FP64
+    int has_field;
+    int field_off;
+    const double* afield;
 };
 constexpr int kQuadNodes = 20;   // points per panel of the projection quadrature
 
@@ -213,9 +219,4 @@ void launch_moments(int precision, const GroupDev& g, const void* fs, double* n,
                     double* q, int node_base, cudaStream_t st);
 void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out,
                      cudaStream_t st);
-// Per-node acceleration field: fo += c_stage dt (-a(node) . K f) (hlb_kernels.cu).
-size_t force_field_smem_bytes(const GroupDev& g, int precision);
-cudaError_t prepare_force_field();
-void launch_force_field(int precision, const GroupDev& g, const double* afield, const void* fs, void* fo, int stage,
-                        cudaStream_t st);
 }  // namespace hlb

@@ -1,14 +1,20 @@
 // Device kernels of libhlb (sm_103a).
 //
-// Per RK-3 stage (Eq. "eq:rk3") two kernels run:
-//   wall_kernel   one CTA per (instance, y-row): incident fluxes at both wall
-//                 faces from the quadratically extrapolated ghosts (Sec.
-//                 IV.C.3), summed in FP64, give the emitted densities
+// Per RK-3 stage (Eq. "eq:rk3") these kernels run (the marching kernels of
+// hlb_march.cu, hlb_pair.cuh, hlb_line.cuh take the stage kernel's place
+// where they apply):
+//   quad_coef_kernel  FP64 half-range groups above order 12: the half-range
+//                 equilibrium coefficients of every collisional node by
+//                 quadrature of the projection integrals (see below).
+//   wall_kernel   one or a few CTAs per (instance, y-row): incident fluxes at
+//                 both wall faces from the quadratically extrapolated ghosts
+//                 (Sec. IV.C.3), summed in FP64, give the emitted densities
 //                 n_w = -sum_inc F / sum_emit p_x g^w (Eq. "eq:nplus_def").
 //   stage_kernel  fused per node: moments (Eq. "eq:fmoms") by a block
 //                 reduction, the equilibrium factors g_x, g_y, g_z (FP64
 //                 recurrences, App. A), the force term sum_a a_a K_a f
-//                 (Eqs. "eq:hh_Kk_hh", "eq:H_Kk"), BGK with tau = Kn/n,
+//                 (Eqs. "eq:hh_Kk_hh", "eq:H_Kk"; a the uniform acceleration
+//                 plus the node's field value), BGK with tau = Kn/n,
 //                 WENO-5 / upwind2 fluxes along x (walls: Eq.
 //                 "eq:weno_populate" ghosts) and y (periodic), and the RK-3
 //                 combination; writes the stage output.  It serves the
@@ -273,7 +279,10 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
         const R dt = (R)I.dt;
         const R inv_dx = (R)(1.0 / g.dx[I.dx_off + x]);
         const R inv_dy = (R)I.inv_dy;
-        const R ax = (R)I.ax, ay = (R)I.ay, az = (R)I.az;
+        // the uniform acceleration plus the node's field value (hlb_set_force_field)
+        const double* af = g.has_field ? g.afield + 3 * (size_t)node : nullptr;
+        const R ax = (R)(I.ax + (af ? af[0] : 0.0)), ay = (R)(I.ay + (af ? af[1] : 0.0)),
+                az = (R)(I.az + (af ? af[2] : 0.0));
         const double nwl = g.nw[(size_t)(I.row_off + y) * 2 + 0];
         const double nwr = g.nw[(size_t)(I.row_off + y) * 2 + 1];
         const R* gwl = gw + I.gw_off;
@@ -866,74 +875,6 @@ void launch_moments(int precision, const GroupDev& g, const void* fs, double* n,
         if (table) moments_kernel<float, true><<<grid, block, (g.V + g.VY * g.VZ) * sizeof(float4), st>>>(g, (const float*)fs, n, u, T, q, node_base);
         else moments_kernel<float, false><<<grid, block, 0, st>>>(g, (const float*)fs, n, u, T, q, node_base);
     }
-}
-
-// ---------------------------------------------------------------------------
-// The force term of a per-node acceleration field (App. A, with a = a(node)):
-//   fo += c_s dt (-(a_x K_x f + a_y K_y f + a_z K_z f))   at every node,
-// f the stage input and c_s the weight of dt L in stage s of Eq. "eq:rk3"
-// (1, 1/4, 2/3).  The stage kernel has already written fo with the uniform
-// part of the force, so the two add up to the force of a_uniform + a(node).
-// One CTA takes nodes in turn: the node's values are staged in shared memory,
-// each thread forms the three contractions for its velocities.
-template <typename R>
-__global__ void __launch_bounds__(256) force_field_kernel(const GroupDev g, const double* __restrict__ afield,
-                                                          const R* __restrict__ fs, R* __restrict__ fo, int stage) {
-    extern __shared__ __align__(16) unsigned char ffsm[];
-    const int V = g.V, QX2 = g.QX2, VY = g.VY, VZ = g.VZ;
-    R* sK = reinterpret_cast<R*>(ffsm);                      // Kx [QX2^2], Ky [VY^2], Kz [VZ^2]
-    const int nK = QX2 * QX2 + VY * VY + VZ * VZ;
-    R* sf = sK + ((nK + 1) & ~1);                           // [V]: the node's values
-    const R* K = static_cast<const R*>(g.K);
-    for (int i = threadIdx.x; i < nK; i += blockDim.x) sK[i] = K[i];
-    const R* Kx = sK;
-    const R* Ky = Kx + QX2 * QX2;
-    const R* Kz = Ky + VY * VY;
-    const R cs = stage == 0 ? R(1) : (stage == 1 ? R(0.25) : R(2.0 / 3.0));
-    for (int node = blockIdx.x; node < g.nnodes; node += gridDim.x) {
-        const double* a = afield + 3 * (size_t)node;
-        const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
-        const InstDev& I = g.inst[ii];
-        const size_t off = (size_t)I.f_off + (size_t)(node - I.node_off) * V;
-        __syncthreads();                                     // sf of the previous node is consumed
-        for (int v = threadIdx.x; v < V; v += blockDim.x) sf[v] = fs[off + v];
-        __syncthreads();
-        const R ax = (R)a[0], ay = (R)a[1], az = (R)a[2];
-        const R w = cs * (R)I.dt;
-        for (int v = threadIdx.x; v < V; v += blockDim.x) {
-            const int ix = v % QX2, jy = (v / QX2) % VY, kz = v / (QX2 * VY);
-            const R* fib = sf + (size_t)(kz * VY + jy) * QX2;
-            R fx = R(0), fy = R(0), fz = R(0);
-            for (int i = 0; i < QX2; ++i) fx += Kx[ix * QX2 + i] * fib[i];
-            if (g.Qy)
-                for (int j = 0; j < VY; ++j) fy += Ky[jy * VY + j] * sf[(size_t)(kz * VY + j) * QX2 + ix];
-            if (g.Qz)
-                for (int k = 0; k < VZ; ++k) fz += Kz[kz * VZ + k] * sf[(size_t)(k * VY + jy) * QX2 + ix];
-            fo[off + v] -= w * (ax * fx + ay * fy + az * fz);
-        }
-    }
-}
-
-size_t force_field_smem_bytes(const GroupDev& g, int precision) {
-    const size_t es = precision == HLB_FP64_ ? 8 : 4;
-    const int nK = g.QX2 * g.QX2 + g.VY * g.VY + g.VZ * g.VZ;
-    return es * (((size_t)nK + 1) / 2 * 2 + (size_t)g.V);
-}
-
-cudaError_t prepare_force_field() {
-    cudaError_t e = cudaFuncSetAttribute(force_field_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(force_field_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-}
-
-void launch_force_field(int precision, const GroupDev& g, const double* afield, const void* fs, void* fo, int stage,
-                        cudaStream_t st) {
-    const size_t smem = force_field_smem_bytes(g, precision);
-    const int grid = g.nnodes < 152 * 16 ? g.nnodes : 152 * 16;
-    if (precision == HLB_FP64_)
-        force_field_kernel<double><<<grid, 256, smem, st>>>(g, afield, (const double*)fs, (double*)fo, stage);
-    else
-        force_field_kernel<float><<<grid, 256, smem, st>>>(g, afield, (const float*)fs, (float*)fo, stage);
 }
 
 void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out, cudaStream_t st) {

@@ -23,7 +23,7 @@ namespace {
 template <int QX2, int VY>
 struct LineBuf {
     static constexpr int S = QX2 * VY;
-    static constexpr int NCPMAX = (QX2 + VY + 32 + 1 + 3) / 4 * 4;
+    static constexpr int NCPMAX = (QX2 + VY + 32 + 1 + 3 + 3) / 4 * 4;   // p_z up to 32, 1/tau, a_x a_y a_z
     float head[4][S];           // cells x0+3 .. x0+6
     float fnr[4][S];            // f^n of cells x0 .. x0+3 (stages 2, 3)
     float coef[4 * NCPMAX];     // factor lines of cells x0 .. x0+3
@@ -46,7 +46,10 @@ constexpr size_t line_smem_bytes() {
            (line_uses_mma<QX2, VY, FM>() ? 0 : pair_kdup_pairs<QX2, VY>() * sizeof(float2)) + (kLineDepth + 3) * 8 + 16;
 }
 
-template <int ADV, int QX2, int VY, int FM>
+// FF = 1: the group has a per-node acceleration field; the a K rows are then
+// plain K rows, K_x f and K_y f are kept apart and scaled per cell by the a_x,
+// a_y of the factor lines (uniform plus field).
+template <int ADV, int QX2, int VY, int FM, int FF>
 __global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? 8 : (QX2 * VY <= 256 ? 4 : 2))))
 march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
               const float* __restrict__ fn, float* __restrict__ fo, int stage) {
@@ -57,6 +60,7 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     constexpr int KXR = QX2 + 2, KYR = VY + 2;
     using Buf = LineBuf<QX2, VY>;
     constexpr bool kMMA = line_uses_mma<QX2, VY, FM>();
+    static_assert(!FF || !kMMA, "force fields take the FMA form");
     extern __shared__ __align__(128) unsigned char msm[];
     Buf* buf = reinterpret_cast<Buf*>(msm);
     float4* sF = reinterpret_cast<float4*>(msm + kLineDepth * sizeof(Buf));    // [2][VY][SP]
@@ -99,7 +103,7 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     if constexpr (kMMA) {
         mma.load(K, (float)I.ax, (float)I.ay, t >> 5, t & 31);
     } else {
-        const float axf = (float)I.ax, ayf = (float)I.ay;
+        const float axf = FF ? 1.0f : (float)I.ax, ayf = FF ? 1.0f : (float)I.ay;
         for (int e = t; e < QX2 * QX2; e += S) sKd[(e / QX2) * KXR + e % QX2] = f2(axf * K[e]);
         for (int e = t; e < VY * VY; e += S) sKd[QX2 * KXR + (e / VY) * KYR + e % VY] = f2(ayf * K[QX2 * QX2 + e]);
     }
@@ -260,7 +264,7 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
         issue(p + kLineDepth - 1);
         // a_x K_x f + a_y K_y f at the four cells
         const float4* fr = sF + b * VY * SP;
-        float2 fk01 = f2(0.0f), fk23 = f2(0.0f);
+        float2 fk01 = f2(0.0f), fk23 = f2(0.0f), gy01 = f2(0.0f), gy23 = f2(0.0f);   // gy: K_y f apart (FF)
         if constexpr (kMMA) {
             // every warp's tiles, exchanged through xch2 (sKx, sKy are free
             // again: every warp passed xch[b] after reading them last time)
@@ -286,10 +290,12 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
 #pragma unroll
                 for (int j = 0; j < VY; j += 2) {
                     const float4 kk = kyr[j >> 1], fa = fr[j * SP + ix], fb = fr[(j + 1) * SP + ix];
-                    fk01 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), fk01);
-                    fk23 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), fk23);
-                    fk01 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), fk01);
-                    fk23 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), fk23);
+                    float2& y01 = FF ? gy01 : fk01;
+                    float2& y23 = FF ? gy23 : fk23;
+                    y01 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), y01);
+                    y23 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), y23);
+                    y01 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), y01);
+                    y23 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), y23);
                 }
             }
         }
@@ -303,7 +309,13 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
             const float2 itau = make_float2(c0[csrc_t], c1[csrc_t]);
             const float2 fc = q ? fc23 : fc01;
             // L = -div_x - (a_x K_x f + a_y K_y f) - (f - feq)/tau
-            const float2 L = __ffma2_rn(fsub2(fc, feq), itau, __fadd2_rn(q ? divx23 : divx01, q ? fk23 : fk01));
+            float2 fk = q ? fk23 : fk01;
+            if (FF) {      // a_x (K_x f) + a_y (K_y f) with the cells' a of the factor lines
+                const int fo = g.field_off;
+                fk = __ffma2_rn(make_float2(c0[fo + 1], c1[fo + 1]), q ? gy23 : gy01,
+                                __fmul2_rn(make_float2(c0[fo], c1[fo]), fk));
+            }
+            const float2 L = __ffma2_rn(fsub2(fc, feq), itau, __fadd2_rn(q ? divx23 : divx01, fk));
             float2 out;  // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
             if (stage == 0) {
                 out = fsub2(fc, __fmul2_rn(dt2, L));
@@ -328,16 +340,16 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     }
 }
 
-template <int ADV, int QX2, int VY, int FM>
+template <int ADV, int QX2, int VY, int FM, int FF = 0>
 void launch_line_t(const GroupDev& g, const Work* works, int nworks, const void* fs, const void* fn, void* fo,
                    int stage, cudaStream_t st) {
-    march1_kernel<ADV, QX2, VY, FM><<<nworks, QX2 * VY, line_smem_bytes<QX2, VY, FM>(), st>>>(
+    march1_kernel<ADV, QX2, VY, FM, FF><<<nworks, QX2 * VY, line_smem_bytes<QX2, VY, FM>(), st>>>(
         g, works, (const float*)fs, (const float*)fn, (float*)fo, stage);
 }
 
-template <int ADV, int QX2, int VY, int FM>
+template <int ADV, int QX2, int VY, int FM, int FF = 0>
 cudaError_t prepare_line_t() {
-    return cudaFuncSetAttribute(march1_kernel<ADV, QX2, VY, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(march1_kernel<ADV, QX2, VY, FM, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)line_smem_bytes<QX2, VY, FM>());
 }
 

@@ -52,7 +52,7 @@ template <typename R, int QX2, int VY, int TY>
 struct StepBuf {
     static constexpr int S = QX2 * VY;
     static constexpr int NH = TY > 1 ? 6 : 1;
-    static constexpr int NCPMAX = (QX2 + VY + 32 + 1 + 3) / 4 * 4;
+    static constexpr int NCPMAX = (QX2 + VY + 32 + 1 + 3 + 3) / 4 * 4;   // p_z up to 32, 1/tau, a_x a_y a_z
     R head[TY][S];
     R halo[NH][S];
     R fnr[TY][S];
@@ -259,9 +259,11 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
                 for (int j = 0; j < VY; ++j) kyf += ky[j] * fr[j * QX2 + ix];
             }
             const R* cr = B.coef[r];
+            // with a force field the node's a = a_uniform + a_field is in its factor line
+            const R axr = g.has_field ? cr[g.field_off] : ax, ayr = g.has_field ? cr[g.field_off + 1] : ay;
             const R feq = cr[ix] * cr[QX2 + jy] * cr[csrc_z];
             const R itau = cr[csrc_t];
-            const R L = -divx[r] - divy[r] - (ax * kxf + ay * kyf) - (fc[r] - feq) * itau;
+            const R L = -divx[r] - divy[r] - (axr * kxf + ayr * kyf) - (fc[r] - feq) * itau;
             R out;
             if (stage == 0) {
                 out = fc[r] + dt * L;

@@ -260,6 +260,14 @@ __global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __r
             }
         }
         if (lane < nb) coef[(size_t)(base + lane) * g.ncp + nf] = (R)sNT[2 * lane + 1];   // 1/tau
+        if (g.has_field && lane < nb) {              // a = a_uniform + a_field(node)
+            const int node = base + lane;
+            const InstDev& I = g.inst[g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0];
+            R* fl = coef + (size_t)node * g.ncp + g.field_off;
+            fl[0] = (R)(I.ax + g.afield[3 * (size_t)node]);
+            fl[1] = (R)(I.ay + g.afield[3 * (size_t)node + 1]);
+            fl[2] = (R)(I.az + g.afield[3 * (size_t)node + 2]);
+        }
         __syncwarp();
     }
 }
@@ -314,6 +322,12 @@ __global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const fl
         const double T = ((double)sm[4] + (double)sm[12] - n * (ux * ux + uy * uy + uz * uz)) * in *
                          (g.D == 3 ? 1.0 / 3.0 : (g.D == 2 ? 0.5 : 1.0));
         factor_line_df<NM>(g, n, ux, uy, uz, T, (double)n * inv_Kn, sPx, sPy, sPz, sRec, line);
+        if (g.has_field) {                           // a = a_uniform + a_field(node)
+            const InstDev& I = g.inst[ii];
+            line[g.field_off] = (float)(I.ax + g.afield[3 * (size_t)node]);
+            line[g.field_off + 1] = (float)(I.ay + g.afield[3 * (size_t)node + 1]);
+            line[g.field_off + 2] = (float)(I.az + g.afield[3 * (size_t)node + 2]);
+        }
     }
     __syncwarp();
     // the warp's lines are contiguous in the factor-line buffer

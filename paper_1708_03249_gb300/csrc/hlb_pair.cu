@@ -14,6 +14,15 @@ bool pair_available(int QX2, int VY) {
 }
 
 cudaError_t prepare_pair(int adv, int QX2, int VY, int form) {
+    if (form == kForceField) {
+#define HLB_PRF(A, B)                                                                         \
+        if (QX2 == A && VY == B)                                                              \
+            return adv == HLB_WENO5_ ? prepare_pair_t<HLB_WENO5_, A, B, kForceFMA, 1>()     \
+                                     : prepare_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1>();
+        HLB_PAIR_LIST(HLB_PRF)
+#undef HLB_PRF
+        return cudaErrorInvalidValue;
+    }
     if (form != kForceFMA) return prepare_pair_tc(adv, QX2, VY, form);
 #define HLB_PR(A, B)                                                                          \
     if (QX2 == A && VY == B)                                                                  \
@@ -26,6 +35,17 @@ cudaError_t prepare_pair(int adv, int QX2, int VY, int form) {
 
 void launch_pair(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, int nworks,
                  const void* fs, const void* fn, void* fo, int stage, cudaStream_t st) {
+    if (form == kForceField) {
+#define HLB_LAF(A, B)                                                                                         \
+        if (QX2 == A && VY == B) {                                                                            \
+            if (adv == HLB_WENO5_) launch_pair_t<HLB_WENO5_, A, B, kForceFMA, 1>(g, works, nworks, fs, fn, fo, stage, st); \
+            else launch_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1>(g, works, nworks, fs, fn, fo, stage, st);              \
+            return;                                                                                           \
+        }
+        HLB_PAIR_LIST(HLB_LAF)
+#undef HLB_LAF
+        return;
+    }
     if (form != kForceFMA) {
         launch_pair_tc(adv, QX2, VY, form, g, works, nworks, fs, fn, fo, stage, st);
         return;

@@ -24,7 +24,7 @@ namespace {
 template <int QX2, int VY>
 struct PairBuf {
     static constexpr int S = QX2 * VY;
-    static constexpr int NCPMAX = (QX2 + VY + 32 + 1 + 3) / 4 * 4;
+    static constexpr int NCPMAX = (QX2 + VY + 32 + 1 + 3 + 3) / 4 * 4;   // p_z up to 32, 1/tau, a_x a_y a_z
     float head[2][2][S];        // [cell x0+3+i][row]
     float halo[2][6][S];        // [cell x0+i][halo row y0-3, y0-2, y0-1, y0+2, y0+3, y0+4]
     float fnr[2][2][S];         // [cell x0+i][row]: f^n (stages 2, 3)
@@ -56,7 +56,10 @@ constexpr size_t pair_smem_bytes() {
            (pair_uses_mma<QX2, VY, FM>() ? 0 : pair_kdup_pairs<QX2, VY>() * sizeof(float2)) + (kPairDepth + 3) * 8 + 16;
 }
 
-template <int ADV, int QX2, int VY, int FM>
+// FF = 1: the group has a per-node acceleration field; the a K rows are then
+// plain K rows, K_x f and K_y f are kept apart and scaled per cell by the a_x,
+// a_y of the factor lines (uniform plus field).
+template <int ADV, int QX2, int VY, int FM, int FF>
 __global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? HLB_PAIR_MIN_BLOCKS : 2)))
 march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
                   const float* __restrict__ fn, float* __restrict__ fo, int stage) {
@@ -67,6 +70,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     extern __shared__ __align__(128) unsigned char msm[];
     Buf* buf = reinterpret_cast<Buf*>(msm);
     constexpr bool kMMA = pair_uses_mma<QX2, VY, FM>();
+    static_assert(!FF || !kMMA, "force fields take the FMA form");
     float4* sF = reinterpret_cast<float4*>(msm + kPairDepth * sizeof(Buf));   // [2][VY][SP]: (r0 x0, r1 x0, r0 x1, r1 x1)
     float4* sKx = sF + 2 * VY * SP;                   // [VY][SP]: a_x K_x f, same layout (tensor-core path)
     float4* sKy = sKx + VY * SP;                      // [VY][SP]: a_y K_y f
@@ -113,7 +117,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
     if constexpr (kMMA) {
         mma.load(K, (float)I.ax, (float)I.ay, warp, lane);
     } else {
-        const float axf = (float)I.ax, ayf = (float)I.ay;
+        const float axf = FF ? 1.0f : (float)I.ax, ayf = FF ? 1.0f : (float)I.ay;
         for (int e = t; e < QX2 * QX2; e += S) sKd[(e / QX2) * KXR + e % QX2] = f2(axf * K[e]);
         for (int e = t; e < VY * VY; e += S) sKd[QX2 * KXR + (e / VY) * KYR + e % VY] = f2(ayf * K[QX2 * QX2 + e]);
     }
@@ -340,7 +344,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
 #pragma unroll
         for (int j = 0; j < 6; ++j) w[j] = w[j + 2];
         // force term at both cells (rows packed): a_x K_x f + a_y K_y f
-        float2 fk0, fk1;
+        float2 fk0, fk1, gy0 = f2(0.0f), gy1 = f2(0.0f);     // gy: K_y f apart (FF)
         if constexpr (kMMA) {
             if (!mbar_wait(xch2, p & 1, g.err, g.wait_ns)) *sAbort = 1;
             const float4 ex = sKx[jy * SP + ix], ey = sKy[jy * SP + ix];
@@ -368,10 +372,12 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             for (int j = 0; j < VY; j += 2) {
                 const float4 kk = kyr[j >> 1];
                 const float4 fa = fr[j * SP + ix], fb = fr[(j + 1) * SP + ix];
-                fk0 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), fk0);
-                fk1 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), fk1);
-                fk0 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), fk0);
-                fk1 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), fk1);
+                float2& y0 = FF ? gy0 : fk0;
+                float2& y1 = FF ? gy1 : fk1;
+                y0 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.x, fa.y), y0);
+                y1 = __ffma2_rn(make_float2(kk.x, kk.y), make_float2(fa.z, fa.w), y1);
+                y0 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.x, fb.y), y0);
+                y1 = __ffma2_rn(make_float2(kk.z, kk.w), make_float2(fb.z, fb.w), y1);
             }
         }
 #pragma unroll
@@ -386,7 +392,13 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             const float2 divx = i ? divx1 : divx0;
             const float2 divy = i ? make_float2(dy0.y, dy1.y) : make_float2(dy0.x, dy1.x);
             // L = -div_x - div_y - (a_x K_x f + a_y K_y f) - (f - feq)/tau
-            float2 L = __fadd2_rn(__fadd2_rn(divx, divy), i ? fk1 : fk0);
+            float2 fk = i ? fk1 : fk0;
+            if (FF) {      // a_x (K_x f) + a_y (K_y f) with the cells' a of the factor lines
+                const int fo = g.field_off;
+                fk = __ffma2_rn(make_float2(c0[fo + 1], c1[fo + 1]), i ? gy1 : gy0,
+                                __fmul2_rn(make_float2(c0[fo], c1[fo]), fk));
+            }
+            float2 L = __fadd2_rn(__fadd2_rn(divx, divy), fk);
             L = __ffma2_rn(fsub2(fc, feq), itau, L);
             float2 out;      // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
             if (stage == 0) {
@@ -416,16 +428,16 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
 }
 
 
-template <int ADV, int QX2, int VY, int FM>
+template <int ADV, int QX2, int VY, int FM, int FF = 0>
 void launch_pair_t(const GroupDev& g, const Work* works, int nworks, const void* fs, const void* fn, void* fo,
                    int stage, cudaStream_t st) {
-    march_pair_kernel<ADV, QX2, VY, FM><<<nworks, QX2 * VY, pair_smem_bytes<QX2, VY, FM>(), st>>>(
+    march_pair_kernel<ADV, QX2, VY, FM, FF><<<nworks, QX2 * VY, pair_smem_bytes<QX2, VY, FM>(), st>>>(
         g, works, (const float*)fs, (const float*)fn, (float*)fo, stage);
 }
 
-template <int ADV, int QX2, int VY, int FM>
+template <int ADV, int QX2, int VY, int FM, int FF = 0>
 cudaError_t prepare_pair_t() {
-    return cudaFuncSetAttribute(march_pair_kernel<ADV, QX2, VY, FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(march_pair_kernel<ADV, QX2, VY, FM, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pair_smem_bytes<QX2, VY, FM>());
 }
 

@@ -57,7 +57,7 @@ constexpr int kPDepth = 2;          // iterations in flight (copy buffers)
 template <int QX2, int VY>
 struct PersistBuf {
     static constexpr int S = QX2 * VY;
-    static constexpr int NCP = (QX2 + VY + 2 + 3) / 4 * 4;     // factor line (VZ = 1)
+    static constexpr int NCP = (QX2 + VY + 2 + 3 + 3) / 4 * 4;     // factor line (VZ = 1; field slots)
     float head[4][S];               // cells x0+3 .. x0+6
     float fnr[4][S];                // f^n of cells x0 .. x0+3 (stages 2, 3)
     float coef[4 * NCP];            // factor lines of cells x0 .. x0+3
