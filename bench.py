@@ -79,6 +79,22 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+_FP32_PEAK = None
+
+
+def fp32_alu_peak(sm_mhz: float):
+    """The FP32 ALU roof: the FMA throughput measured on this GPU by the library
+    (scalar and packed f32x2 chains, the larger), with the nominal figure (152 SMs
+    x 128 FP32 lanes x 2 flop x the SM clock) beside it for context."""
+    global _FP32_PEAK
+    from paper_1708_03249_gb300 import hlb
+    if _FP32_PEAK is None:
+        _FP32_PEAK = (hlb.fp32_peak(False), hlb.fp32_peak(True))
+    nominal = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    return max(_FP32_PEAK), {"measured_scalar_tflops": _FP32_PEAK[0], "measured_packed_tflops": _FP32_PEAK[1],
+                              "nominal_tflops": nominal}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -334,9 +350,11 @@ def roofline_of(hbm_achieved, hbm_peak, peak_kind, alu_achieved, alu_peak, sm_mh
     hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
            "frac": hbm_achieved / hbm_peak, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
            "per_unit": BYTES_PER_NV_STAGE, "per_unit_desc": "algorithmic bytes per node-velocity per stage launch"}
-    alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
-           "frac": alu_achieved / alu_peak,
-           "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and clock)",
+    alu_meas, alu_ctx = fp32_alu_peak(sm_mhz)
+    alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_meas, "unit": "TFLOP/s",
+           "frac": alu_achieved / alu_meas,
+           "peak_source": "measured: FP32 FMA chains on every SM (hlb_fp32_peak, the larger of scalar and packed)",
+           "peak_context": alu_ctx, "frac_of_nominal": alu_achieved / alu_peak,
            "per_unit": flop_nv, "per_unit_desc": "algorithmic flops per node-velocity per stage launch"}
     top = dict(alu if alu["frac"] >= hbm["frac"] else hbm)
     top.update({"traffic": traffic, "kernel": "march_pair_kernel<WENO5, 16, 8>", "stage_avg_ms": stage_avg_ms,
@@ -401,10 +419,12 @@ def run_gpu(args):
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("bench_timed")       # profilers: --nvtx --nvtx-include bench_timed/
         e0.record(stream)
         h.step(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     barrier()
     ms = e0.elapsed_time(e1)
     kt = h.kernel_times(reset=True)
@@ -542,6 +562,8 @@ def run_batched(args):
     from paper_1708_03249_gb300 import hlb
 
     insts = with_precision(W.batched_instances(args.ninst), args.precision)
+    if args.qx:                       # one velocity-set group of the batch
+        insts = [c for c in insts if c["Qx"] == args.qx]
     # the oracle's host-core pool (spawned before any CUDA call): the first
     # seeded instances of the batch, one per core
     pool = OraclePool(cfgs=insts, what="seeded batched channel instances (the batch's first ones)")
@@ -551,7 +573,7 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     h = hlb.Handle(insts, stream=stream.cuda_stream)
     h.init_equilibrium()
-    segments = h.autotune()
+    segments = h.autotune() if args.tune else None     # untuned: the persistent kernel where eligible
     groups = {}
     for i, c in enumerate(insts):
         key = (c["Qx"], c["Qy"])
@@ -568,10 +590,12 @@ def run_batched(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     h.launch_count(reset=True)
     with ClockSampler(0) as clk:
+        torch.cuda.nvtx.range_push("bench_timed")
         e0.record(stream)
         h.step(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     launches = h.launch_count(reset=True)
     nv = h.values
@@ -659,12 +683,12 @@ def run_batched(args):
     hbm_ach = nv * BYTES_PER_NV_STAGE * 3 / (stage_ms_per_step * 1e-3) / 1e9
     flops = sum(g["values"] * flops_per_nv_stage(dict(Qx=qx, Qy=qy, ny=1, advection=W.WENO5, x_basis=W.X_HALF))
                 for (qx, qy), g in groups.items())
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak, alu_ctx = fp32_alu_peak(sm_mhz)
     alu_ach = flops * 3 / (stage_ms_per_step * 1e-3) / 1e12
     hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": peak, "unit": "GB/s", "frac": hbm_ach / peak,
            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})", "per_unit": BYTES_PER_NV_STAGE}
     alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
-           "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
+           "peak_source": "measured: FP32 FMA chains on every SM (hlb_fp32_peak)", "peak_context": alu_ctx}
     roof = dict(alu if alu["frac"] >= hbm["frac"] else hbm)
     roof.update({"traffic": None, "kernel": "the groups' FP32 marching kernels (march1_kernel), per-stage launches",
                  "stage_ms_per_step": stage_ms_per_step, "hbm": hbm, "alu": alu})
@@ -745,10 +769,12 @@ def run_other(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         steps = max(args.steps, 30)
+        torch.cuda.nvtx.range_push("bench_timed")
         e0.record(stream)
         h.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1)
         n, u, T, q = h.moments()
         nv = h.values
@@ -763,8 +789,9 @@ def run_other(args):
     peak, peak_kind = measured_peaks()
     hbm = nv * bytes_nv / (stage_ms * 1e-3) / 1e9
     alu = nv * flops_per_nv_stage(cfg) / (stage_ms * 1e-3) / 1e12
+    alu_peak, _ = fp32_alu_peak(MAX_SM_MHZ)
     stage = {"stage_avg_ms": stage_ms, "hbm_gbs": hbm, "hbm_frac": hbm / peak, "hbm_peak_source": peak_kind,
-             "alu_tflops": alu, "alu_frac": alu / (SMS * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12),
+             "alu_tflops": alu, "alu_frac": alu / alu_peak, "alu_peak_tflops_measured": alu_peak,
              "per_unit_bytes": bytes_nv, "per_unit_flops": flops_per_nv_stage(cfg)}
     if cfg["precision"] == W.FP64:
         stage.update({"fp64_tflops": alu, "fp64_frac": alu / FP64_NOMINAL_TFLOPS,
@@ -793,6 +820,8 @@ def main():
     ap.add_argument("--nx", type=int, default=0, help="profiling: the large 2D workload on a smaller grid")
     ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--fp64-sample", type=int, default=64)
+    ap.add_argument("--qx", type=int, default=0, help="batched: only the instances with this Qx (4, 8 or 16)")
+    ap.add_argument("--tune", type=int, default=1, help="batched: 0 skips hlb_autotune (persistent kernel kept)")
     ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
                     help="FP32 workloads: the force term's form (fp32: the library's choice; tf32x3, bf16split: "
                          "on the tensor cores)")

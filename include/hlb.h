@@ -374,6 +374,14 @@ hlb_status hlb_set_wait_test(hlb_handle* h, int withhold_copies, double wait_lim
  * disarms.  nth == 0 disarms it.  Errors: HLB_EINVAL (nth < 0). */
 hlb_status hlb_set_alloc_fail_test(long long nth);
 
+/* FP32 FMA throughput of the current device in TFLOP/s (an FMA counts two
+ * flop), measured with independent dependent-FMA chains on every SM (scalar
+ * fmaf for packed == 0, packed f32x2 FMAs otherwise), best of three timed
+ * launches after a warm-up (about 0.1 s; allocates and frees a small device
+ * buffer; synchronises the device).  The ALU roof of the FP32 stage kernels;
+ * no counterpart in the paper.  Errors: HLB_EINVAL, HLB_ENOMEM, HLB_ECUDA. */
+hlb_status hlb_fp32_peak(int packed, double* tflops);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char* hlb_last_error(void);
 

@@ -1610,6 +1610,14 @@ hlb_status hlb_autotune(hlb_handle* h, int* segments_out) {
     return check_device_error(h);
 }
 
+hlb_status hlb_fp32_peak(int packed, double* tflops) {
+    if (!tflops) return fail(HLB_EINVAL, "tflops is NULL");
+    const cudaError_t e = hlb::measure_fp32_peak(packed, tflops);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? HLB_ENOMEM : HLB_ECUDA,
+                                      std::string("FP32 peak measurement: ") + cudaGetErrorString(e));
+    return HLB_OK;
+}
+
 hlb_status hlb_set_persistent(hlb_handle* h, int on) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (h->persistent != (on != 0) && h->graph) {     // the captured steps change: re-capture

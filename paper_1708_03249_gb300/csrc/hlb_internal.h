@@ -215,6 +215,9 @@ size_t persist_smem_bytes(int QX2, int VY, int form);
 void launch_persist(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, const PersistArgs& a,
                     int grid, cudaStream_t st);
 void launch_broadcast(int precision, void* f, const void* gvec, long long nvalues, int V, cudaStream_t st);
+// FP32 FMA throughput of the current device in TFLOP/s (FMA = 2 flop), scalar
+// or packed f32x2 (hlb_kernels.cu)
+cudaError_t measure_fp32_peak(int packed, double* tflops);
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
                     double* q, int node_base, cudaStream_t st);
 void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out,

@@ -885,3 +885,79 @@ void launch_residual(int precision, const GroupDev& g, const void* a, const void
 }
 
 }  // namespace hlb
+
+// ---------------------------------------------------------------------------
+// FP32 FMA throughput of the device (the ALU roof of the FP32 stage kernels):
+// every thread runs kFmaChains independent chains of dependent FMAs (scalar
+// fmaf, or packed f32x2 __ffma2_rn counting two FMAs each), enough warps per SM
+// to cover the pipeline latency; the result is written so that no chain is
+// dropped.
+// ---------------------------------------------------------------------------
+namespace hlb {
+namespace {
+constexpr int kFmaChains = 8, kFmaIters = 4096;
+
+__global__ void __launch_bounds__(256) fma_peak_kernel(float* out, float a, float b) {
+    float x[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = threadIdx.x * 1e-7f + c;
+#pragma unroll 16
+    for (int i = 0; i < kFmaIters; ++i)
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) x[c] = fmaf(x[c], a, b);
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += x[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) fma2_peak_kernel(float* out, float a, float b) {
+    float2 x[kFmaChains / 2];
+#pragma unroll
+    for (int c = 0; c < kFmaChains / 2; ++c) x[c] = make_float2(threadIdx.x * 1e-7f + c, c + 0.5f);
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll 16
+    for (int i = 0; i < kFmaIters; ++i)
+#pragma unroll
+        for (int c = 0; c < kFmaChains / 2; ++c) x[c] = __ffma2_rn(x[c], a2, b2);
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kFmaChains / 2; ++c) s += x[c].x + x[c].y;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+cudaError_t measure_fp32_peak(int packed, double* tflops) {
+    int dev = 0, nsm = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int block = 256, grid = nsm * 8;          // 64 warps per SM
+    float* out = nullptr;
+    e = cudaMalloc(&out, (size_t)grid * block * sizeof(float));
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 0.0f;
+    for (int rep = 0; rep < 4; ++rep) {             // the first launch is a warm-up
+        cudaEventRecord(e0);
+        if (packed) fma2_peak_kernel<<<grid, block>>>(out, 0.999f, 1e-3f);
+        else fma_peak_kernel<<<grid, block>>>(out, 0.999f, 1e-3f);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * kFmaChains * (double)kFmaIters * grid * block;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return cudaSuccess;
+}
+}  // namespace hlb

@@ -61,6 +61,7 @@ SIGNATURES = {
     "hlb_get_dt": (C.c_int, [_P, C.c_int, _D]),
     "hlb_force_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "hlb_set_persistent": (C.c_int, [_P, C.c_int]),
+    "hlb_fp32_peak": (C.c_int, [C.c_int, _D]),
     "hlb_step_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _D]),
     "hlb_get_nsteps": (C.c_int, [_P, _LL]),
     "hlb_get_state": (C.c_int, [_P, _P, C.c_size_t]),
@@ -323,6 +324,13 @@ def axis(Q: int, half, laguerre: bool = False):
     p, w, K = np.empty(n), np.empty(n), np.empty(n * n)
     _check(lib().hlb_axis(Q, (2 if laguerre else 1) if half else 0, _dptr(p), _dptr(w), _dptr(K)))
     return p, w, K.reshape(n, n)
+
+
+def fp32_peak(packed: bool = False) -> float:
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    t = C.c_double()
+    _check(lib().hlb_fp32_peak(1 if packed else 0, C.byref(t)))
+    return t.value
 
 
 def version() -> str:
