@@ -338,31 +338,41 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // WENO-5 face value from a stencil already divided by the population's
-// weight (values O(1) wherever the population matters), without epsilon.
-// Reassociated from Sec. IV.C.2: the candidates come pre-multiplied by their
-// linear weights, G_k = d_k q_k; the smoothness indicators are scaled by
-// 12/13 (B_k = t_k^2 + (3/13) s_k^2; a common factor leaves the weights
-// unchanged) and carry an additive floor of 1e-30, below which FP32 cannot
-// resolve them anyway; the nonlinear weights are formed from the ratios
-// u_k = min_j B_j / B_k in (0, 1], so nothing overflows, and a zero B_k
-// takes the limit of Tab. "weno" (the zero-indicator stencils share the
-// weight in proportion to d_k).
+// weight (values O(1) wherever the population matters), without epsilon
+// (Sec. IV.C.2), face between c and d of the upwind-ordered stencil a..e:
+// - the candidates relative to c, q_k = c + R_k / 6, with R_1 = 2a - 7b + 5c,
+//   R_2 = 2d - b - c, R_3 = 5d - 4c - e, and the indicators' t_k, s_k, all from
+//   the differences of neighbouring stencil values;
+// - the indicators scaled by 12/13, B_k = t_k^2 + (3/13) s_k^2 (a common factor
+//   leaves the weights unchanged), with an additive floor of 1e-30, below which
+//   FP32 cannot resolve them anyway;
+// - the nonlinear weights from the ratios u_k = min_j B_j / B_k in (0, 1], so
+//   nothing overflows, and a zero B_k takes the limit of Tab. "weno" (the
+//   zero-indicator stencils share the weight in proportion to d_k);
+// - face = c + (v_1 R_1 + 6 v_2 R_2 + 3 v_3 R_3) / (6 (v_1 + 6 v_2 + 3 v_3)) with
+//   v_k = u_k^2: the linear weights (0.1, 0.6, 0.3) scaled by 10, so the
+//   denominator is at least 1.
+// The packed form below needs six constants (f32x2 instructions take no
+// immediates).  The scalar form performs the same roundings in the same
+// order (explicit _rn operations, no contraction), so a face gives the same
+// bits in either form: the wall kernel's incident flux is the stage kernels'.
 __device__ __forceinline__ float weno5_scaled(float a, float b, float c, float d, float e) {
-    const float G1 = fmaf(11.0f / 60.0f, c, fmaf(-7.0f / 60.0f, b, (1.0f / 30.0f) * a));
-    const float G2 = fmaf(0.2f, d, fmaf(0.5f, c, -0.1f * b));
-    const float G3 = fmaf(-0.05f, e, fmaf(0.25f, d, 0.1f * c));
-    const float t1 = fmaf(-2.0f, b, a + c), s1 = fmaf(-4.0f, b, fmaf(3.0f, c, a));
-    const float t2 = fmaf(-2.0f, c, b + d), s2 = b - d;
-    const float t3 = fmaf(-2.0f, d, c + e), s3 = fmaf(-4.0f, d, fmaf(3.0f, c, e));
-    constexpr float k = 3.0f / 13.0f;
-    const float B1 = fmaf(t1, t1, fmaf(k * s1, s1, 1e-30f));
-    const float B2 = fmaf(t2, t2, fmaf(k * s2, s2, 1e-30f));
-    const float B3 = fmaf(t3, t3, fmaf(k * s3, s3, 1e-30f));
+    const float dmm = __fsub_rn(a, b), dm = __fsub_rn(c, b), dp = __fsub_rn(d, c), dpp = __fsub_rn(e, d);
+    const float t1 = __fadd_rn(dm, dmm), s1 = __fmaf_rn(3.0f, dm, dmm);
+    const float t2 = __fsub_rn(dp, dm), s2 = __fadd_rn(dm, dp);
+    const float t3 = __fsub_rn(dpp, dp), s3 = __fmaf_rn(-3.0f, dp, dpp);
+    const float R1 = __fadd_rn(__fadd_rn(t1, s1), dm), R2 = __fadd_rn(s2, dp), R3 = __fsub_rn(dp, s3);
+    constexpr float k = 3.0f / 13.0f, fl = 1e-30f;
+    const float B1 = __fmaf_rn(t1, t1, __fmaf_rn(__fmul_rn(k, s1), s1, fl));
+    const float B2 = __fmaf_rn(t2, t2, __fmaf_rn(__fmul_rn(k, s2), s2, fl));
+    const float B3 = __fmaf_rn(t3, t3, __fmaf_rn(__fmul_rn(k, s3), s3, fl));
     const float m = fminf(B1, fminf(B2, B3));
-    const float u1 = m * rcp_approx(B1), u2 = m * rcp_approx(B2), u3 = m * rcp_approx(B3);
-    const float v1 = u1 * u1, v2 = u2 * u2, v3 = u3 * u3;
-    const float den = fmaf(0.1f, v1, fmaf(0.6f, v2, 0.3f * v3));
-    return fmaf(v1, G1, fmaf(v2, G2, v3 * G3)) * rcp_approx(den);
+    const float u1 = __fmul_rn(m, rcp_approx(B1)), u2 = __fmul_rn(m, rcp_approx(B2)), u3 = __fmul_rn(m, rcp_approx(B3));
+    const float v1 = __fmul_rn(u1, u1);
+    const float V2 = __fmul_rn(6.0f, __fmul_rn(u2, u2)), V3 = __fmul_rn(3.0f, __fmul_rn(u3, u3));
+    const float den = __fadd_rn(__fadd_rn(v1, V2), V3);
+    const float num = __fmaf_rn(V3, R3, __fmaf_rn(V2, R2, __fmul_rn(v1, R1)));
+    return __fmaf_rn(__fmul_rn(num, 1.0f / 6.0f), rcp_approx(den), c);
 }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -379,17 +389,13 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
 }
 
 // Two independent faces at once in the packed FP32 pipe (f32x2 on sm_100+);
-// the same arithmetic as weno5_scaled.
+// the arithmetic of weno5_scaled, lane by lane.
 __device__ __forceinline__ float2 weno5_scaled2(float2 a, float2 b, float2 c, float2 d, float2 e) {
-    const float2 G1 = __ffma2_rn(f2(11.0f / 60.0f), c, __ffma2_rn(f2(-7.0f / 60.0f), b, __fmul2_rn(f2(1.0f / 30.0f), a)));
-    const float2 G2 = __ffma2_rn(f2(0.2f), d, __ffma2_rn(f2(0.5f), c, __fmul2_rn(f2(-0.1f), b)));
-    const float2 G3 = __ffma2_rn(f2(-0.05f), e, __ffma2_rn(f2(0.25f), d, __fmul2_rn(f2(0.1f), c)));
-    const float2 t1 = __ffma2_rn(f2(-2.0f), b, __fadd2_rn(a, c));
-    const float2 s1 = __ffma2_rn(f2(-4.0f), b, __ffma2_rn(f2(3.0f), c, a));
-    const float2 t2 = __ffma2_rn(f2(-2.0f), c, __fadd2_rn(b, d));
-    const float2 s2 = fsub2(b, d);
-    const float2 t3 = __ffma2_rn(f2(-2.0f), d, __fadd2_rn(c, e));
-    const float2 s3 = __ffma2_rn(f2(-4.0f), d, __ffma2_rn(f2(3.0f), c, e));
+    const float2 dmm = fsub2(a, b), dm = fsub2(c, b), dp = fsub2(d, c), dpp = fsub2(e, d);
+    const float2 t1 = __fadd2_rn(dm, dmm), s1 = __ffma2_rn(f2(3.0f), dm, dmm);
+    const float2 t2 = fsub2(dp, dm), s2 = __fadd2_rn(dm, dp);
+    const float2 t3 = fsub2(dpp, dp), s3 = __ffma2_rn(f2(-3.0f), dp, dpp);
+    const float2 R1 = __fadd2_rn(__fadd2_rn(t1, s1), dm), R2 = __fadd2_rn(s2, dp), R3 = fsub2(dp, s3);
     const float2 k = f2(3.0f / 13.0f), fl = f2(1e-30f);
     const float2 B1 = __ffma2_rn(t1, t1, __ffma2_rn(__fmul2_rn(k, s1), s1, fl));
     const float2 B2 = __ffma2_rn(t2, t2, __ffma2_rn(__fmul2_rn(k, s2), s2, fl));
@@ -398,10 +404,11 @@ __device__ __forceinline__ float2 weno5_scaled2(float2 a, float2 b, float2 c, fl
     const float2 u1 = __fmul2_rn(m, make_float2(rcp_approx(B1.x), rcp_approx(B1.y)));
     const float2 u2 = __fmul2_rn(m, make_float2(rcp_approx(B2.x), rcp_approx(B2.y)));
     const float2 u3 = __fmul2_rn(m, make_float2(rcp_approx(B3.x), rcp_approx(B3.y)));
-    const float2 v1 = __fmul2_rn(u1, u1), v2 = __fmul2_rn(u2, u2), v3 = __fmul2_rn(u3, u3);
-    const float2 den = __ffma2_rn(f2(0.1f), v1, __ffma2_rn(f2(0.6f), v2, __fmul2_rn(f2(0.3f), v3)));
-    const float2 num = __ffma2_rn(v1, G1, __ffma2_rn(v2, G2, __fmul2_rn(v3, G3)));
-    return __fmul2_rn(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    const float2 v1 = __fmul2_rn(u1, u1);
+    const float2 V2 = __fmul2_rn(f2(6.0f), __fmul2_rn(u2, u2)), V3 = __fmul2_rn(f2(3.0f), __fmul2_rn(u3, u3));
+    const float2 den = __fadd2_rn(__fadd2_rn(v1, V2), V3);
+    const float2 num = __ffma2_rn(V3, R3, __ffma2_rn(V2, R2, __fmul2_rn(v1, R1)));
+    return __ffma2_rn(__fmul2_rn(num, f2(1.0f / 6.0f)), make_float2(rcp_approx(den.x), rcp_approx(den.y)), c);
 }
 
 __device__ __forceinline__ float2 upwind2_face2(float2 b, float2 c) {

@@ -17,6 +17,9 @@ rounding bound exceeds 1e-12, so the sizes below are what one host can run):
                  number, 3000 steps (t = 0.176; the residual reached is stored);
   box24          the 2D box's velocity set and physics (Q = 16 x 16, walls 1 and
                  1.2, g = 0.2 at 45 deg, Kn = 0.05) on 24 x 24 cells, 2000 steps;
+  large24        the large channel's velocity set and physics (16 x 8 x 8 velocities,
+                 walls 1 and 2, a = (-0.3, -0.3, 0), Kn = 0.5, its cell size and time
+                 step) on a 24 x 24-cell window, 500 steps (its stated length);
   batched_<i>    the first 64 seeded batched instances, 5000 steps each, except
                  the sixteen whose run would exceed 5000 s of one core here (Q = 16
                  with nx >= 258, Q = 8 with nx >= 452), which run 500 steps.
@@ -43,6 +46,8 @@ from paper_1708_03249_gb300 import workloads as W  # noqa: E402
 STRETCHED_STEPS = 3000
 BOX_STEPS = 2000
 BOX_N = 24
+LARGE_STEPS = W.LARGE_2D_STEPS
+LARGE_N = 24
 BATCH_COUNT = 64
 BATCH_LONG, BATCH_SHORT = W.BATCH_STEPS, 500
 # measured one-core cost of the oracle, seconds per node and RK-3 step
@@ -61,9 +66,17 @@ def cases():
     for k, Kn in enumerate(W.CHANNEL_1D_STRETCHED_KN):
         out.append((f"stretched_kn{Kn:g}", W.channel_1d_stretched(Kn), STRETCHED_STEPS, 500 + k))
     out.append((f"box{BOX_N}", W.scaled(W.BOX_2D, nx=BOX_N, ny=BOX_N), BOX_STEPS, 600))
+    out.append((f"large{LARGE_N}", large_window(), LARGE_STEPS, 700))
     for i, c in enumerate(W.batched_instances(BATCH_COUNT)):
         out.append((f"batched_{i:02d}", c, batch_steps(c), 1000 + i))
     return out
+
+
+def large_window(n: int = LARGE_N) -> dict:
+    """The large channel's workload on an n x n window: same velocity set,
+    physics, cell size and time step (the channel is n cells wide)."""
+    c = W.LARGE_2D
+    return W.scaled(c, nx=n, ny=n, Lx=c["Lx"] * n / c["nx"], Ly=c["Ly"] * n / c["ny"])
 
 
 def initial_state(cfg: dict, seed: int) -> np.ndarray:

@@ -12,6 +12,8 @@ s_u = sqrt(max T), s_T = max T, s_q = max n T^{3/2}, per instance.
       30 deg) at Kn = 0.01, 0.1, 1, 10: 3000 steps each;
   the 2D box's velocity set and physics (Q = 16 x 16, Kn = 0.05) on 24 x 24
       cells: 2000 steps;
+  the large channel's velocity set and physics (16 x 8 x 8 velocities, Kn =
+      0.5, its cell size and time step) on a 24 x 24 window: 500 steps;
   the first 64 seeded batched instances: 5000 steps (500 for the sixteen
       largest, whose oracle runs would exceed 5000 s of one core);
   the 2D box at its full size (256 x 256 x 512 velocities): one step, checked
@@ -87,6 +89,17 @@ def test_fp32_box_q16_at_length():
     ref = _load(f"box{BOX_N}")
     cfg = json.loads(str(ref["config"]))
     assert cfg == W.scaled(W.BOX_2D, nx=BOX_N, ny=BOX_N)
+    mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]))
+    errs = _errors(mom, ref)
+    assert max(errs.values()) < 1e-5, errs
+    assert N[0] == pytest.approx(float(ref["N"]), rel=1e-5)
+
+
+def test_fp32_large_channel_window_at_length():
+    from make_long_runs import LARGE_N, initial_state, large_window
+    ref = _load(f"large{LARGE_N}")
+    cfg = json.loads(str(ref["config"]))
+    assert cfg == large_window()
     mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]))
     errs = _errors(mom, ref)
     assert max(errs.values()) < 1e-5, errs
