@@ -183,13 +183,18 @@ hlb_status hlb_step(hlb_handle* h, long nsteps);
  * with D the number of momentum axes; q = q_x = sum (p_x-u_x)|p-u|^2 f/2.
  * Any output pointer may be NULL.  The values are copied from device memory
  * straight into the caller's arrays (page-locked arrays avoid a staging
- * copy).  Synchronises the handle's stream.  Errors: HLB_ECUDA, HLB_ETIMEOUT
+ * copy): with several instances, each velocity-set group's moments kernel
+ * writes its nodes into a device buffer in this layout (6 doubles per node,
+ * allocated on first use), then one copy per requested array.  Synchronises
+ * the handle's stream.  Errors: HLB_ECUDA, HLB_ETIMEOUT
  * (a bounded device wait ran out since the last check), HLB_ENOMEM,
  * HLB_ENONFINITE (a non-finite n or T; outputs are still written). */
 hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q);
 
 /* Same as hlb_moments, but the outputs are device arrays (each may be NULL);
- * enqueued on the handle's stream, no synchronisation, no non-finite check. */
+ * enqueued on the handle's stream, no synchronisation, no non-finite check.
+ * With several instances every group's moments kernel writes its nodes in
+ * place; with one, the kernel's scratch is copied. */
 hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev);
 
 /* Same outputs as hlb_moments_dev, for callers that cannot allocate device
@@ -243,7 +248,11 @@ hlb_status hlb_get_nsteps(const hlb_handle* h, long long* nsteps);
 
 /* Copy the state to / from a caller buffer of exactly hlb_sizes(...bytes)
  * bytes (layout in the header comment).  Host variants synchronise the
- * stream; _dev variants enqueue a device copy.  Errors: HLB_EINVAL (size). */
+ * stream; _dev variants enqueue a device copy on the handle's stream: with
+ * several instances and f_dev 16-byte aligned, one copy kernel per velocity-set
+ * group (the first call also uploads a table of the instances' chunks), else
+ * one cudaMemcpyAsync per instance.  Errors: HLB_EINVAL (size), HLB_ENOMEM
+ * (the chunk table), HLB_ECUDA. */
 hlb_status hlb_get_state(hlb_handle* h, void* host_f, size_t bytes);
 hlb_status hlb_set_state(hlb_handle* h, const void* host_f, size_t bytes);
 hlb_status hlb_get_state_dev(hlb_handle* h, void* f_dev, size_t bytes);
@@ -275,8 +284,10 @@ hlb_status hlb_autotune(hlb_handle* h, int* segments_out);
  * copy has run, i.e. until the hlb_commit_state that consumes it has been
  * followed by a synchronisation of the handle's stream (hlb_moments, or the
  * caller's own).  A second prefetch before a commit replaces the first.
- * hlb_commit_state makes the handle's stream wait for that copy, then enqueues
- * a device-to-device copy of the staging buffer into the current state.
+ * hlb_commit_state makes the handle's stream wait for that copy, then makes
+ * the staging buffer the current state: for a single velocity set whose layout
+ * is the caller's, by swapping the two buffers (no copy); otherwise by a
+ * device-to-device copy as in hlb_set_state_dev.
  * Errors: HLB_EINVAL (size, NULL, commit with nothing staged), HLB_ENOMEM,
  * HLB_ECUDA. */
 hlb_status hlb_prefetch_state(hlb_handle* h, const void* host_f, size_t bytes);

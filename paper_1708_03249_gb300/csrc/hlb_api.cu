@@ -91,6 +91,7 @@ struct Group {
     int cur = 0, prev = -1;
     DevBuf d_inst, d_node_start, d_row_start, d_K, d_p, d_pd, d_T, d_rec, d_dx, d_gw, d_nw, d_resid;
     DevBuf d_mom;                            // moments scratch: 6 doubles per node
+    DevBuf d_gnode;                          // [members]: each member's first node in the caller's layout
     PinnedBuf h_mom;                         // pinned word for the non-finite flag (hlb_moments), first use
     DevBuf d_Td, d_invdx, d_wscale, d_coef, d_works, d_err, d_recf, d_Tf, d_sums;
     DevBuf d_KxT, d_KxJ;                     // FP64 Kx transposed and its jump factors (kx_global groups only)
@@ -176,6 +177,17 @@ struct hlb_handle {
     std::vector<cudaEvent_t> group_done;
     cudaEvent_t step_fork = nullptr;
     bool persistent = true;                  // eligible groups step with the persistent kernel
+    // device-to-device state copies between the caller's layout and the
+    // groups' buffers (commit of a staged state, the _dev state I/O): chunks
+    // of at most kRegroupChunk bytes, group by group, copied by one launch per
+    // group instead of one cudaMemcpyAsync per instance; built on first use
+    void* d_regroup = nullptr;
+    std::vector<int> regroup_first;          // per group: its first chunk (size ngroups + 1)
+    int regroup_state = 0;                   // 0 not built, 1 built, -1 a layout the kernel cannot take
+    // moments of a handle with several instances, in the caller's layout
+    // (n [N], u [3N], T [N], q [N], N = total_nodes): written there by the
+    // moments kernels directly, then read back in four copies; first use
+    DevBuf d_mom_global;
 };
 
 namespace {
@@ -909,6 +921,12 @@ hlb_status hlb_create(const hlb_config* cfg, int ninst, void* cuda_stream, hlb_h
     }
     h->total_nodes = nodes;
     h->total_values = values;
+    for (auto& G : h->groups) {
+        std::vector<long long> gn;
+        for (int i : G->members) gn.push_back(h->inst_node_off[i]);
+        hlb_status s = upload(G->d_gnode, gn);
+        if (s != HLB_OK) return s;
+    }
     if (h->groups.size() > 1) {
         HLB_CUDA(cudaEventCreateWithFlags(&h->step_fork, cudaEventDisableTiming));
         for (size_t k = 1; k < h->groups.size(); ++k) {
@@ -936,6 +954,7 @@ void hlb_destroy(hlb_handle* h) {
     if (h->stage_free) cudaEventDestroy(h->stage_free);
     if (h->stage_filled) cudaEventDestroy(h->stage_filled);
     if (h->stage_buf) cudaFree(h->stage_buf);
+    if (h->d_regroup) cudaFree(h->d_regroup);
     for (cudaStream_t s2 : h->group_stream) { cudaStreamSynchronize(s2); cudaStreamDestroy(s2); }
     for (cudaEvent_t e2 : h->group_done) cudaEventDestroy(e2);
     if (h->step_fork) cudaEventDestroy(h->step_fork);
@@ -1111,6 +1130,15 @@ hlb_status hlb_step(hlb_handle* h, long nsteps) {
 hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* T_dev, double* q_dev) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     wait_moments(h, h->stream);
+    if (h->cfg.size() > 1) {          // every group's kernel writes its nodes in place: no copies
+        for (auto& Gp : h->groups) {
+            Group& G = *Gp;
+            hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, n_dev, u_dev, T_dev, q_dev, 0, h->stream,
+                                (const long long*)G.d_gnode.p);
+            HLB_CUDA(cudaGetLastError());
+        }
+        return HLB_OK;
+    }
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
         double* m = (double*)G.d_mom.p;
@@ -1131,49 +1159,88 @@ hlb_status hlb_moments_dev(hlb_handle* h, double* n_dev, double* u_dev, double* 
     return HLB_OK;
 }
 
+// The non-finite flag's pinned word of a group (first use).
+static hlb_status ensure_mom_flag(Group& G) {
+    if (!G.h_mom.p) {
+        if (host_malloc((void**)&G.h_mom.p, 16) != cudaSuccess) {
+            cudaGetLastError();
+            G.h_mom.p = nullptr;
+            return fail(HLB_ENOMEM, "cudaMallocHost of the moments flag failed");
+        }
+        G.h_mom.bytes = 16;
+    }
+    return HLB_OK;
+}
+
+// Several instances: every group's moments kernel writes its nodes into the
+// handle's buffer in the caller's layout, then one copy per requested array
+// and one per group's non-finite flag, all on stream st (instead of four
+// copies per instance).
+static hlb_status moments_global_to_host(hlb_handle* h, double* n, double* u, double* T, double* q, cudaStream_t st) {
+    const long long N = h->total_nodes;
+    if (!h->d_mom_global.p && dev_malloc(&h->d_mom_global.p, (size_t)N * 6 * sizeof(double)) != cudaSuccess) {
+        h->d_mom_global.p = nullptr;
+        return fail(HLB_ENOMEM, "cudaMalloc of the moments buffer failed");
+    }
+    double* gm = (double*)h->d_mom_global.p;
+    double* on = n ? gm : nullptr;
+    double* ou = u ? gm + N : nullptr;
+    double* oT = T ? gm + 4 * N : nullptr;
+    double* oq = q ? gm + 5 * N : nullptr;
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        hlb_status e = ensure_mom_flag(G);
+        if (e != HLB_OK) return e;
+        HLB_CUDA(cudaMemsetAsync(G.dev.nonfinite, 0, sizeof(int), st));
+        hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, on, ou, oT, oq, 0, st, (const long long*)G.d_gnode.p);
+        HLB_CUDA(cudaGetLastError());
+        G.mom_buf = G.buf[G.cur].p;
+        HLB_CUDA(cudaMemcpyAsync(G.h_mom.p, G.dev.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+    if (n) HLB_CUDA(cudaMemcpyAsync(n, on, (size_t)N * 8, d2h, st));
+    if (u) HLB_CUDA(cudaMemcpyAsync(u, ou, (size_t)N * 24, d2h, st));
+    if (T) HLB_CUDA(cudaMemcpyAsync(T, oT, (size_t)N * 8, d2h, st));
+    if (q) HLB_CUDA(cudaMemcpyAsync(q, oq, (size_t)N * 8, d2h, st));
+    return HLB_OK;
+}
+
+// A single instance (one group, the caller's layout): the moments kernel into
+// the group's scratch, four copies and the non-finite flag, on stream st.
+static hlb_status moments_one_to_host(Group& G, double* n, double* u, double* T, double* q, cudaStream_t st) {
+    hlb_status e = ensure_mom_flag(G);
+    if (e != HLB_OK) return e;
+    double* m = (double*)G.d_mom.p;
+    const size_t N = (size_t)G.nnodes;
+    HLB_CUDA(cudaMemsetAsync(G.dev.nonfinite, 0, sizeof(int), st));
+    hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + N, m + 4 * N, m + 5 * N, 0, st);
+    HLB_CUDA(cudaGetLastError());
+    G.mom_buf = G.buf[G.cur].p;
+    const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+    if (n) HLB_CUDA(cudaMemcpyAsync(n, m, N * 8, d2h, st));
+    if (u) HLB_CUDA(cudaMemcpyAsync(u, m + N, N * 24, d2h, st));
+    if (T) HLB_CUDA(cudaMemcpyAsync(T, m + 4 * N, N * 8, d2h, st));
+    if (q) HLB_CUDA(cudaMemcpyAsync(q, m + 5 * N, N * 8, d2h, st));
+    HLB_CUDA(cudaMemcpyAsync(G.h_mom.p, G.dev.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return HLB_OK;
+}
+
 hlb_status hlb_moments(hlb_handle* h, double* n, double* u, double* T, double* q) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     NvtxRange range("hlb_moments");
     wait_moments(h, h->stream);                         // the moments scratch is shared
     {
-        hlb_status e = check_device_error(h);
-        if (e != HLB_OK) return e;
+        hlb_status e0 = check_device_error(h);
+        if (e0 != HLB_OK) return e0;
     }
     // every group: clear its non-finite flag, launch the moments kernel, copy
-    // each instance's moments straight into the caller's arrays (direct DMA
-    // when they are page-locked) and the flag into a small pinned word; then
-    // one synchronisation
-    for (auto& Gp : h->groups) {
-        Group& G = *Gp;
-        if (!G.h_mom.p) {
-            if (host_malloc((void**)&G.h_mom.p, 16) != cudaSuccess) {
-                cudaGetLastError();
-                G.h_mom.p = nullptr;
-                return fail(HLB_ENOMEM, "cudaMallocHost of the moments flag failed");
-            }
-            G.h_mom.bytes = 16;
-        }
-        double* m = (double*)G.d_mom.p;
-        HLB_CUDA(cudaMemsetAsync(G.dev.nonfinite, 0, sizeof(int), h->stream));
-        hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + G.nnodes, m + 4LL * G.nnodes,
-                            m + 5LL * G.nnodes, 0, h->stream);
-        HLB_CUDA(cudaGetLastError());
-        const double* dn = m;
-        const double* du = m + G.nnodes;
-        const double* dT = m + 4LL * G.nnodes;
-        const double* dq = m + 5LL * G.nnodes;
-        for (size_t k = 0; k < G.members.size(); ++k) {
-            const long long go = h->inst_node_off[G.members[k]];
-            const int j0 = G.node_start[k];
-            const size_t cnt = (size_t)(G.node_start[k + 1] - j0);
-            const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
-            if (n) HLB_CUDA(cudaMemcpyAsync(n + go, dn + j0, cnt * 8, d2h, h->stream));
-            if (u) HLB_CUDA(cudaMemcpyAsync(u + 3 * go, du + 3LL * j0, 3 * cnt * 8, d2h, h->stream));
-            if (T) HLB_CUDA(cudaMemcpyAsync(T + go, dT + j0, cnt * 8, d2h, h->stream));
-            if (q) HLB_CUDA(cudaMemcpyAsync(q + go, dq + j0, cnt * 8, d2h, h->stream));
-        }
-        HLB_CUDA(cudaMemcpyAsync(G.h_mom.p, G.dev.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    }
+    // the moments into the caller's arrays (direct DMA when they are
+    // page-locked) and the flag into a small pinned word; then one
+    // synchronisation
+    hlb_status e = h->cfg.size() > 1 ? moments_global_to_host(h, n, u, T, q, h->stream)
+                                     : moments_one_to_host(*h->groups[0], n, u, T, q, h->stream);
+    for (auto& Gp : h->groups) Gp->mom_buf = nullptr;  // read on this stream, which synchronises below
+    if (e != HLB_OK) return e;
     HLB_CUDA(cudaStreamSynchronize(h->stream));
     bool finite = true;
     for (auto& Gp : h->groups)
@@ -1192,34 +1259,9 @@ hlb_status hlb_moments_async(hlb_handle* h, double* n, double* u, double* T, dou
     // after the work already on the handle's stream (the state to read)
     HLB_CUDA(cudaEventRecord(h->mom_state, h->stream));
     HLB_CUDA(cudaStreamWaitEvent(h->mom_stream, h->mom_state, 0));
-    for (auto& Gp : h->groups) {
-        Group& G = *Gp;
-        if (!G.h_mom.p) {
-            if (host_malloc((void**)&G.h_mom.p, 16) != cudaSuccess) {
-                cudaGetLastError();
-                G.h_mom.p = nullptr;
-                return fail(HLB_ENOMEM, "cudaMallocHost of the moments flag failed");
-            }
-            G.h_mom.bytes = 16;
-        }
-        double* m = (double*)G.d_mom.p;
-        HLB_CUDA(cudaMemsetAsync(G.dev.nonfinite, 0, sizeof(int), h->mom_stream));
-        hlb::launch_moments(G.precision, G.dev, G.buf[G.cur].p, m, m + G.nnodes, m + 4LL * G.nnodes,
-                            m + 5LL * G.nnodes, 0, h->mom_stream);
-        HLB_CUDA(cudaGetLastError());
-        G.mom_buf = G.buf[G.cur].p;
-        for (size_t k = 0; k < G.members.size(); ++k) {
-            const long long go = h->inst_node_off[G.members[k]];
-            const int j0 = G.node_start[k];
-            const size_t cnt = (size_t)(G.node_start[k + 1] - j0);
-            const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
-            if (n) HLB_CUDA(cudaMemcpyAsync(n + go, m + j0, cnt * 8, d2h, h->mom_stream));
-            if (u) HLB_CUDA(cudaMemcpyAsync(u + 3 * go, m + G.nnodes + 3LL * j0, 3 * cnt * 8, d2h, h->mom_stream));
-            if (T) HLB_CUDA(cudaMemcpyAsync(T + go, m + 4LL * G.nnodes + j0, cnt * 8, d2h, h->mom_stream));
-            if (q) HLB_CUDA(cudaMemcpyAsync(q + go, m + 5LL * G.nnodes + j0, cnt * 8, d2h, h->mom_stream));
-        }
-        HLB_CUDA(cudaMemcpyAsync(G.h_mom.p, G.dev.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->mom_stream));
-    }
+    hlb_status e = h->cfg.size() > 1 ? moments_global_to_host(h, n, u, T, q, h->mom_stream)
+                                     : moments_one_to_host(*h->groups[0], n, u, T, q, h->mom_stream);
+    if (e != HLB_OK) return e;
     HLB_CUDA(cudaEventRecord(h->mom_done, h->mom_stream));
     h->mom_pending = true;
     return HLB_OK;
@@ -1271,12 +1313,78 @@ hlb_status hlb_get_nsteps(const hlb_handle* h, long long* nsteps) {
     return HLB_OK;
 }
 
+struct RegroupChunk {
+    long long ext, dev;      // byte offsets in the caller's layout and in the group's buffer
+    int bytes, pad;
+};
+constexpr int kRegroupChunk = 1 << 16;
+
+// One chunk per CTA, 16-byte words (every offset and length a multiple of 16).
+__global__ void __launch_bounds__(256) regroup_kernel(char* __restrict__ dev, char* __restrict__ ext,
+                                                      const RegroupChunk* __restrict__ chunks, int to_ext) {
+    const RegroupChunk c = chunks[blockIdx.x];
+    const int4* src = reinterpret_cast<const int4*>(to_ext ? dev + c.dev : ext + c.ext);
+    int4* dst = reinterpret_cast<int4*>(to_ext ? ext + c.ext : dev + c.dev);
+    for (int i = threadIdx.x; i < c.bytes / 16; i += blockDim.x) dst[i] = src[i];
+}
+
+// The chunk table of the handle's layout, or regroup_state = -1 if some
+// instance's offset or length is not a multiple of 16 bytes.
+static hlb_status build_regroup(hlb_handle* h) {
+    std::vector<RegroupChunk> ch;
+    h->regroup_first.assign(1, 0);
+    for (auto& Gp : h->groups) {
+        const Group& G = *Gp;
+        for (size_t k = 0; k < G.members.size(); ++k) {
+            const long long ext = h->inst_value_off[G.members[k]] * (long long)G.esize;
+            const long long dev = (long long)G.inst[k].f_off * (long long)G.esize;
+            const long long len = (long long)(G.node_start[k + 1] - G.node_start[k]) * G.V * (long long)G.esize;
+            if (ext % 16 || dev % 16 || len % 16) {
+                h->regroup_state = -1;
+                return HLB_OK;
+            }
+            for (long long o = 0; o < len; o += kRegroupChunk)
+                ch.push_back({ext + o, dev + o, (int)std::min<long long>(kRegroupChunk, len - o), 0});
+        }
+        h->regroup_first.push_back((int)ch.size());
+    }
+    if (!ch.empty()) {
+        if (dev_malloc(&h->d_regroup, ch.size() * sizeof(RegroupChunk)) != cudaSuccess) {
+            h->d_regroup = nullptr;
+            return fail(HLB_ENOMEM, "cudaMalloc of the regroup table failed");
+        }
+        HLB_CUDA(cudaMemcpy(h->d_regroup, ch.data(), ch.size() * sizeof(RegroupChunk), cudaMemcpyHostToDevice));
+    }
+    h->regroup_state = 1;
+    return HLB_OK;
+}
+
 static hlb_status state_copy(hlb_handle* h, void* ext, size_t bytes, bool to_ext, cudaMemcpyKind kind, bool sync) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (!ext) return fail(HLB_EINVAL, "buffer is NULL");
     if (!to_ext) wait_moments(h, h->stream);            // the state buffer may be read by pending moments
     if (bytes != (size_t)(h->total_values * (long long)h->esize))
         return fail(HLB_EINVAL, "state buffer must be exactly " + std::to_string(h->total_values * (long long)h->esize) + " bytes");
+    // device to device across several instances: one launch per group
+    if (kind == cudaMemcpyDeviceToDevice && h->cfg.size() > 1 && (reinterpret_cast<uintptr_t>(ext) % 16) == 0) {
+        if (h->regroup_state == 0) {
+            const hlb_status e = build_regroup(h);
+            if (e != HLB_OK) return e;
+        }
+        if (h->regroup_state == 1) {
+            for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+                const int c0 = h->regroup_first[gi], n = h->regroup_first[gi + 1] - c0;
+                if (n == 0) continue;
+                Group& G = *h->groups[gi];
+                regroup_kernel<<<n, 256, 0, h->stream>>>((char*)G.buf[G.cur].p, (char*)ext,
+                                                         (const RegroupChunk*)h->d_regroup + c0, to_ext ? 1 : 0);
+                HLB_CUDA(cudaGetLastError());
+            }
+            if (sync) HLB_CUDA(cudaStreamSynchronize(h->stream));
+            if (!to_ext) h->have_residual = false;
+            return HLB_OK;
+        }
+    }
     for (auto& Gp : h->groups) {
         Group& G = *Gp;
         char* dev = (char*)G.buf[G.cur].p;

@@ -218,8 +218,11 @@ void launch_broadcast(int precision, void* f, const void* gvec, long long nvalue
 // FP32 FMA throughput of the current device in TFLOP/s (FMA = 2 flop), scalar
 // or packed f32x2 (hlb_kernels.cu)
 cudaError_t measure_fp32_peak(int packed, double* tflops);
+// n, u, T, q of every node of the group (any output may be NULL).  Node j of
+// member k goes to index gnode[k] + (j - node_start[k]) of the outputs when
+// gnode (device, [ninst]) is given, else to node_base + j.
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
-                    double* q, int node_base, cudaStream_t st);
+                    double* q, int node_base, cudaStream_t st, const long long* gnode = nullptr);
 void launch_residual(int precision, const GroupDev& g, const void* a, const void* b, double* out,
                      cudaStream_t st);
 }  // namespace hlb

@@ -589,7 +589,7 @@ constexpr int kMomentTableMax = 1536;
 template <typename R, bool kTable>
 __global__ void __launch_bounds__(256)
 moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double* u_out,
-               double* T_out, double* q_out, int node_base) {
+               double* T_out, double* q_out, int node_base, const long long* __restrict__ gnode) {
     using R4 = typename std::conditional<sizeof(R) == 4, float4, double4>::type;
     extern __shared__ __align__(16) unsigned char mom_smem[];
     R4* sP = reinterpret_cast<R4*>(mom_smem);            // [V]: p_x, p_y, p_z   (kTable)
@@ -761,7 +761,11 @@ moments_kernel(const GroupDev g, const R* __restrict__ fs, double* n_out, double
             const double E = d[4] + d[5];
             const double Tn = (E - n * u2) / (g.D * n);
             const double qx = 0.5 * (d[8] - 2.0 * (ux * d[4] + uy * d[6] + uz * d[7]) - ux * E + 2.0 * n * ux * u2);
-            const long long o = node_base + node;
+            long long o = node_base + node;
+            if (gnode) {                    // the caller's layout: instance by instance
+                const int k = find_slot(g.node_start, g.ninst, node);
+                o = gnode[k] + (node - g.node_start[k]);
+            }
             if (n_out) n_out[o] = n;
             if (u_out) { u_out[3 * o] = ux; u_out[3 * o + 1] = uy; u_out[3 * o + 2] = uz; }
             if (T_out) T_out[o] = Tn;
@@ -864,16 +868,16 @@ void launch_broadcast(int precision, void* f, const void* gvec, long long nvalue
 }
 
 void launch_moments(int precision, const GroupDev& g, const void* fs, double* n, double* u, double* T,
-                    double* q, int node_base, cudaStream_t st) {
+                    double* q, int node_base, cudaStream_t st, const long long* gnode) {
     const int block = 256;                               // 8 warps, 32 nodes per warp and batch
     const int grid = (g.nnodes + 255) / 256 < 152 * 8 ? (g.nnodes + 255) / 256 : 152 * 8;
     const bool table = g.V + g.VY * g.VZ <= kMomentTableMax;
     if (precision == HLB_FP64_) {
-        if (table) moments_kernel<double, true><<<grid, block, (g.V + g.VY * g.VZ) * sizeof(double4), st>>>(g, (const double*)fs, n, u, T, q, node_base);
-        else moments_kernel<double, false><<<grid, block, 0, st>>>(g, (const double*)fs, n, u, T, q, node_base);
+        if (table) moments_kernel<double, true><<<grid, block, (g.V + g.VY * g.VZ) * sizeof(double4), st>>>(g, (const double*)fs, n, u, T, q, node_base, gnode);
+        else moments_kernel<double, false><<<grid, block, 0, st>>>(g, (const double*)fs, n, u, T, q, node_base, gnode);
     } else {
-        if (table) moments_kernel<float, true><<<grid, block, (g.V + g.VY * g.VZ) * sizeof(float4), st>>>(g, (const float*)fs, n, u, T, q, node_base);
-        else moments_kernel<float, false><<<grid, block, 0, st>>>(g, (const float*)fs, n, u, T, q, node_base);
+        if (table) moments_kernel<float, true><<<grid, block, (g.V + g.VY * g.VZ) * sizeof(float4), st>>>(g, (const float*)fs, n, u, T, q, node_base, gnode);
+        else moments_kernel<float, false><<<grid, block, 0, st>>>(g, (const float*)fs, n, u, T, q, node_base, gnode);
     }
 }
 

@@ -23,13 +23,20 @@ def _cfgs(kind="groups"):
         # one velocity set: the commit swaps the staging and state buffers
         return [W.make(Qx=8, Qy=8, nx=30, ny=5, Ly=0.2, Kn=0.5, ax=-0.2, precision=W.FP32),
                 W.make(Qx=8, Qy=8, nx=16, Kn=1.0, T_right=1.5, precision=W.FP32)]
+    if kind == "unaligned":
+        # instances whose slices are not multiples of 16 bytes (6 velocities,
+        # odd cell counts): the commit copies instance by instance
+        return [W.make(Qx=3, nx=25, Kn=0.3, ax=-0.2, advection=W.UPWIND2, precision=W.FP32),
+                W.make(Qx=4, Qy=4, nx=16, Kn=1.0, T_right=1.5, precision=W.FP32),
+                W.make(Qx=3, nx=31, Kn=0.1, advection=W.UPWIND2, precision=W.FP32)]
     # two velocity sets: the commit copies the staging buffer into the groups
+    # (one launch per group)
     return [W.make(Qx=4, Qy=4, nx=24, Kn=0.3, ax=-0.2, precision=W.FP32),
             W.make(Qx=8, Qy=8, nx=16, Kn=1.0, T_right=1.5, precision=W.FP32),
             W.make(Qx=4, Qy=4, nx=40, Kn=0.1, precision=W.FP32)]
 
 
-@pytest.mark.parametrize("kind", ["groups", "one_group"])
+@pytest.mark.parametrize("kind", ["groups", "one_group", "unaligned"])
 def test_committed_state_equals_set_state_and_steps_agree(kind):
     from paper_1708_03249_gb300 import hlb
     with hlb.Handle(_cfgs(kind)) as a, hlb.Handle(_cfgs(kind)) as b:
@@ -170,3 +177,43 @@ def test_checkpoint_resume_is_bit_exact(prec):
         resumed = c.get_state()
     assert resumed.dtype == whole.dtype
     assert np.array_equal(resumed.view(np.uint8), whole.view(np.uint8))
+
+
+@pytest.mark.parametrize("kind", ["groups", "unaligned"])
+def test_device_state_io_matches_host_state_io(kind):
+    # hlb_set_state_dev / hlb_get_state_dev between a device buffer in the
+    # caller's layout and the groups' buffers: the same bytes as the host forms
+    # (one launch per group when every slice is a multiple of 16 bytes, one
+    # copy per instance otherwise)
+    from paper_1708_03249_gb300 import hlb
+    with hlb.Handle(_cfgs(kind), stream=torch.cuda.current_stream().cuda_stream) as h:
+        h.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+        f = (h.get_state().astype(np.float64) * W.perturbation(h.values, seed=17, amplitude=0.05)).astype(np.float32)
+        d_in = torch.from_numpy(f).cuda()
+        torch.cuda.synchronize()
+        h.set_state_dev(d_in.data_ptr(), h.state_bytes)
+        np.testing.assert_array_equal(h.get_state(), f)
+        h.step(2)
+        d_out = torch.full((h.values,), float("nan"), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        h.get_state_dev(d_out.data_ptr(), h.state_bytes)
+        torch.cuda.current_stream().synchronize()
+        np.testing.assert_array_equal(d_out.cpu().numpy(), h.get_state())
+
+
+@pytest.mark.parametrize("kind", ["groups", "one_group"])
+def test_device_moments_match_host_moments(kind):
+    # hlb_moments_dev (several instances: each group's moments kernel writes
+    # its nodes straight into the caller's arrays) against hlb_moments
+    from paper_1708_03249_gb300 import hlb
+    with hlb.Handle(_cfgs(kind), stream=torch.cuda.current_stream().cuda_stream) as h:
+        h.init_equilibrium(1.0, 0.02, 0.0, 1.1)
+        h.step(3)
+        ref = h.moments()
+        N = h.nodes
+        outs = [torch.full((k * N,), float("nan"), dtype=torch.float64, device="cuda") for k in (1, 3, 1, 1)]
+        torch.cuda.synchronize()
+        h.moments_dev(*(o.data_ptr() for o in outs))
+        torch.cuda.current_stream().synchronize()
+        for got, want in zip(outs, ref):
+            np.testing.assert_array_equal(got.cpu().numpy(), np.asarray(want).reshape(-1))
