@@ -807,15 +807,67 @@ def run_other(args):
     print(json.dumps(line), flush=True)
 
 
+def run_steady(args):
+    """The stretched channel (512 cells, Q = 8 x 8, WENO5) toward its steady state:
+    the FP64 and FP32 paths from the same FP32-rounded perturbed equilibrium,
+    stepped side by side in chunks, recording the last step's residual
+    max|f^{n+1} - f^n| / (dt max f) of each and the largest relative deviation
+    of the FP32 moments n, T, q from the FP64 ones.  A diagnostic of how far
+    the FP32 state can follow the FP64 one over long runs, not a parity test."""
+    import numpy as np
+    import torch
+
+    from paper_1708_03249_gb300 import build as hbuild
+    from paper_1708_03249_gb300 import hlb
+
+    torch.cuda.set_device(0)
+    if not os.path.exists(hlb.LIB_PATH):
+        hbuild.build()
+    stream = torch.cuda.Stream()
+    chunk = 20000
+    total = max(chunk, args.steps if args.steps > 20 else 220000)
+    per_kn = {}
+    t0 = time.perf_counter()
+    for Kn in W.CHANNEL_1D_STRETCHED_KN:
+        c32, c64 = W.channel_1d_stretched(Kn), W.channel_1d_stretched(Kn, precision=W.FP64)
+        with hlb.Handle(c64, stream=stream.cuda_stream) as h, hlb.Handle(c32, stream=stream.cuda_stream) as g:
+            g.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+            f0 = (g.get_state().astype(np.float64) * W.perturbation(g.values, seed=1, amplitude=0.05)).astype(np.float32)
+            g.set_state(f0)
+            h.set_state(f0.astype(np.float64))
+            hist, steps = [], 0
+            while steps < total:
+                h.step(chunk)
+                g.step(chunk)
+                steps += chunk
+                r64, r32 = float(h.diag()[1][0]), float(g.diag()[1][0])
+                n6, _, T6, q6 = h.moments()
+                n3, _, T3, q3 = g.moments()
+                dev = max(np.abs(n3 - n6).max() / np.abs(n6).max(), np.abs(T3 - T6).max() / np.abs(T6).max(),
+                          np.abs(q3 - q6).max() / max(np.abs(q6).max(), 1e-300))
+                hist.append({"steps": steps, "residual_fp64": r64, "residual_fp32": r32, "moment_dev": float(dev)})
+            per_kn[f"{Kn:g}"] = {"dt": h.dt(), "history": hist}
+    line = {"metric": "steady-state residual and FP32 moment deviation from FP64", "n_gpus": 1,
+            "config": {"workload": "stretched_channel_steady_state",
+                       "desc": "1D channel, 512 cells tanh A=0.9, Qx=8 x Qy=8, WENO5, T 0.5/1.5, g=0.5 at 30 deg; "
+                               "FP64 and FP32 paths side by side from one perturbed equilibrium",
+                       "chunk_steps": chunk, "steps": total},
+            "per_kn": per_kn, "seconds": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="large2d", choices=["large2d", "batched"] + sorted(OTHER_WORKLOADS),
+    ap.add_argument("--workload", default="large2d",
+                    choices=["large2d", "batched", "stretched_steady_state"] + sorted(OTHER_WORKLOADS),
                     help="large2d: the JSON line of record; batched: the 4096-channel batch vs per-instance "
-                         "FP64; the others time one handle of that configuration")
+                         "FP64; stretched_steady_state: FP32 and FP64 stretched channels stepped side by side "
+                         "toward the steady state (--steps: total steps, default 220000); the others time one "
+                         "handle of that configuration")
     ap.add_argument("--ninst", type=int, default=4096)
     ap.add_argument("--nx", type=int, default=0, help="profiling: the large 2D workload on a smaller grid")
     ap.add_argument("--ny", type=int, default=0)
@@ -830,6 +882,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "stretched_steady_state":
+        run_steady(args)
     elif args.workload in OTHER_WORKLOADS:
         run_other(args)
     else:

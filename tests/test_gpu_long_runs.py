@@ -134,6 +134,13 @@ def test_fp32_batched_instances_at_length():
     assert len(worst) == BATCH_COUNT
 
 
+def test_every_long_run_case_has_its_golden_file():
+    # the stored runs cover every case tests/golden/make_long_runs.py defines
+    from make_long_runs import cases
+    missing = [name for name, *_ in cases() if not os.path.exists(os.path.join(LONG, name + ".npz"))]
+    assert not missing, missing
+
+
 def test_fp32_box_full_size_sampled_nodes():
     # The 2D box at its stated size (256 x 256 cells, 512 velocities), one RK-3
     # step from a perturbed equilibrium; the oracle steps a 19 x 19 window
