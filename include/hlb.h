@@ -339,6 +339,25 @@ hlb_status hlb_equilibrium_x(int Qx, int Nx_eq, double u, double T, double* g);
  * No counterpart in the paper.  Errors: HLB_EINVAL. */
 hlb_status hlb_set_persistent(hlb_handle* h, int on);
 
+/* Rounding of the FP32 stage outputs (each RK-3 stage's f, Eq. "eq:rk3"):
+ * HLB_ROUND_NEAREST (the default) or HLB_ROUND_STOCHASTIC.  With round to
+ * nearest, a stage drops an increment dt L below half a unit in the last
+ * place of f, so near a steady state the FP32 state stops where |dt L| is
+ * below that, short of L = 0 by about that over dt times the slowest
+ * relaxation rate (with small time steps this can exceed 1e-5 of the
+ * moments).  Stochastic rounding moves each output one unit in the last
+ * place toward its exact value (out of TwoSum error terms of the stage's last
+ * additions) with probability equal to the remainder's fraction of that
+ * unit, so that its expectation is exact; the random number is a hash of the
+ * value's address, the stage and the bits of the value and its error:
+ * deterministic, run to run and inside a captured graph.  It costs a few
+ * tens of instructions per node-velocity and stage, and the FP32 marching
+ * kernels then take the FMA force term (not the tensor-core forms).  FP64
+ * groups are unaffected.  Drops a captured graph (synchronises).  No
+ * counterpart in the paper.  Errors: HLB_EINVAL, HLB_ECUDA. */
+enum { HLB_ROUND_NEAREST = 0, HLB_ROUND_STOCHASTIC = 1 };
+hlb_status hlb_set_rounding(hlb_handle* h, int mode);
+
 /* How instance `inst`'s velocity-set group steps: persistent (1: the
  * persistent kernel, 0: per-stage launches), segment_cells (cells per work
  * item or CTA of the marching kernels; 0 if the group does not march), ctas

@@ -111,6 +111,7 @@ struct Group {
     DevBuf d_afield;
     std::vector<char> field_on;
     bool has_field = false;
+    bool sround = false;                     // FP32 stage outputs rounded stochastically (hlb_set_rounding)
     const void* mom_buf = nullptr;           // state buffer read by a pending hlb_moments_async
     // persistent batched kernel (1D FP32 groups without a p_z axis): one
     // launch per step; control words [head, abort, pad, pad, node counters
@@ -290,6 +291,14 @@ hlb_status refresh_walls(hlb_handle* h, Group& G) {
 
 constexpr unsigned long long kDefaultWaitNs = 1000000000ull;   // 1 s
 
+// The form the FP32 marching kernels of group G launch with: the resolved
+// force-term form, or the FMA form's instantiations with a per-node field (3),
+// with stochastic rounding (4), or both (5).
+int march_form(const Group& G) {
+    if (G.precision != HLB_FP32 || (!G.has_field && !G.sround)) return G.force_form;
+    return G.has_field ? (G.sround ? 5 : 3) : 4;
+}
+
 void fill_dev(Group& G) {
     hlb::GroupDev& d = G.dev;
     d.V = G.V; d.QX2 = G.QX2; d.VY = G.VY; d.VZ = G.VZ; d.Qx = G.tx.Q; d.x_full = G.x_full ? 1 : 0;
@@ -330,8 +339,10 @@ void fill_dev(Group& G) {
     d.use_df = (G.precision == HLB_FP32 && G.Nx <= 15) ? 1 : 0;
     d.wait_ns = kDefaultWaitNs;
     d.inject_stall = 0;
-    // with a field the FP32 marching kernels run their field instantiation (FMA form)
-    d.force_form = G.has_field && G.precision == HLB_FP32 ? 3 : G.force_form;
+    // with a field and / or stochastic rounding the FP32 marching kernels run
+    // the FMA form's instantiations for them
+    d.force_form = march_form(G);
+    d.sround = G.sround && G.precision == HLB_FP32 ? 1 : 0;
     d.quad_x = G.quad_x ? 1 : 0;
     d.wchunks = G.wchunks;
     d.wpart = static_cast<double*>(G.d_wpart.p);
@@ -1022,7 +1033,8 @@ hlb_status hlb_set_force_field(hlb_handle* h, int inst, const double* ax, const 
         }
         HLB_CUDA(cudaMemset(G->d_afield.p, 0, (size_t)G->nnodes * 3 * sizeof(double)));
         // the FP32 marching kernels' field instantiations (FMA force term)
-        if (G->march_ok && G->precision == HLB_FP32) HLB_CUDA(hlb::prepare_march(G->precision, G->adv, G->QX2, G->VY, G->TY, 3));
+        if (G->march_ok && G->precision == HLB_FP32)
+            HLB_CUDA(hlb::prepare_march(G->precision, G->adv, G->QX2, G->VY, G->TY, G->sround ? 5 : 3));
     }
     if (G->field_on.size() != G->members.size()) G->field_on.assign(G->members.size(), 0);
     if (G->d_afield.p) {
@@ -1734,6 +1746,23 @@ hlb_status hlb_set_persistent(hlb_handle* h, int on) {
         h->graph = nullptr;
     }
     h->persistent = on != 0;
+    return HLB_OK;
+}
+
+hlb_status hlb_set_rounding(hlb_handle* h, int mode) {
+    if (!h) return fail(HLB_EINVAL, "handle is NULL");
+    if (mode != HLB_ROUND_NEAREST && mode != HLB_ROUND_STOCHASTIC)
+        return fail(HLB_EINVAL, "mode must be HLB_ROUND_NEAREST or HLB_ROUND_STOCHASTIC");
+    HLB_CUDA(cudaStreamSynchronize(h->stream));
+    for (cudaStream_t s2 : h->group_stream) HLB_CUDA(cudaStreamSynchronize(s2));
+    for (auto& Gp : h->groups) {
+        Group& G = *Gp;
+        G.sround = mode == HLB_ROUND_STOCHASTIC;
+        if (G.march_ok && G.precision == HLB_FP32)
+            HLB_CUDA(hlb::prepare_march(G.precision, G.adv, G.QX2, G.VY, G.TY, march_form(G)));
+        fill_dev(G);
+    }
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     return HLB_OK;
 }
 

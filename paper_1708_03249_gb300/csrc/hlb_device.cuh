@@ -323,10 +323,12 @@ struct ForceMMABF16 {
     }
 };
 
-// Force-term forms of the FP32 marching kernels (template parameter FM); the
-// dispatch form kForceField selects the FMA form with a per-node acceleration
-// field (template parameter FF of the kernels).
-constexpr int kForceFMA = 0, kForceTF32x3 = 1, kForceBF16x6 = 2, kForceField = 3;
+// Force-term forms of the FP32 marching kernels (template parameter FM).  The
+// dispatch forms kForceField, kForceFMASR and kForceFieldSR select the FMA form
+// with a per-node acceleration field (template parameter FF of the kernels),
+// with stochastically rounded stage outputs (SR), or both.
+constexpr int kForceFMA = 0, kForceTF32x3 = 1, kForceBF16x6 = 2, kForceField = 3, kForceFMASR = 4,
+              kForceFieldSR = 5;
 template <int FM, int QX2, int VY>
 using ForceTC = typename std::conditional<FM == kForceBF16x6, ForceMMABF16<QX2, VY>, ForceMMA<QX2, VY>>::type;
 
@@ -409,6 +411,100 @@ __device__ __forceinline__ float2 weno5_scaled2(float2 a, float2 b, float2 c, fl
     const float2 den = __fadd2_rn(__fadd2_rn(v1, V2), V3);
     const float2 num = __ffma2_rn(V3, R3, __ffma2_rn(V2, R2, __fmul2_rn(v1, R1)));
     return __ffma2_rn(__fmul2_rn(num, f2(1.0f / 6.0f)), make_float2(rcp_approx(den.x), rcp_approx(den.y)), c);
+}
+
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the FP32 stage outputs (optional, hlb_set_rounding).
+// With round-to-nearest, a stage adds dt L to f and drops it when it is below
+// half a unit in the last place (ulp): near a steady state the FP32 state
+// stops where |dt L| < ulp / 2, short of L = 0 by about ulp / (dt x the
+// slowest relaxation rate), which can exceed the 1e-5 parity bar when dt is
+// small.  Here the stage output s = RN(v) comes with the error e of its last
+// additions (s + e = v, by the TwoSum of Knuth and Moller), and s moves one
+// ulp toward v with probability |e| / ulp, so that its expectation is v and
+// the state keeps drifting toward L = 0.  The probability comes from a hash
+// of the value's address, the stage and the bits of s and e: deterministic,
+// no state, the same inside a captured graph.
+// ---------------------------------------------------------------------------
+// A 32-bit integer finaliser (xor-shift and multiply rounds, the constants of
+// C. Wellons' "lowbias32" from his hash-prospector search).
+__device__ __forceinline__ uint32_t sr_hash(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// s + e = a - b exactly (TwoSum of a and -b).
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2& s, float2& e) {
+    s = fsub2(a, b);
+    const float2 bb = fsub2(s, a);
+    e = fsub2(fsub2(a, fsub2(s, bb)), __fadd2_rn(b, bb));
+}
+// s + e = a + b exactly (TwoSum).
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = fsub2(s, a);
+    e = __fadd2_rn(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+}
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
+    s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb));
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s rounded stochastically toward s + e (|e| <= ulp(s) / 2).
+__device__ __forceinline__ float sround(float s, float e, uint32_t key) {
+    if (e == 0.0f || s == 0.0f || !(fabsf(s) < 3.0e38f)) return s;
+    const uint32_t b = __float_as_uint(s);
+    const float nxt = __uint_as_float((e > 0.0f) == (s > 0.0f) ? b + 1u : b - 1u);
+    const float dist = fabsf(__fsub_rn(nxt, s));
+    const uint32_t h = sr_hash(key ^ sr_hash(b ^ (__float_as_uint(e) * 0x9e3779b9u)));
+    const float r = (float)(h >> 8) * (1.0f / 16777216.0f);      // uniform in [0, 1)
+    return fabsf(e) > r * dist ? nxt : s;
+}
+
+// The RK-3 stage output (Eq. "eq:rk3") from fc, dtL = dt L[fc] and, at stages
+// 1 and 2, f^n, with stochastic rounding: stage 0 gives fc - dtL; stages 1
+// and 2 give fp + c (f^n - fp) with fp = fc - dtL, c = 3/4 or 1/3, whose exact
+// value is out + e2 + (1 - c) e1 for the errors e1 of fp and e2 of the final
+// addition (the product's rounding is relative to the increment and left out).
+__device__ __forceinline__ float2 rk3_out_sr2(int stage, float2 fc, float2 dtL, float2 fn, uint32_t key0,
+                                              uint32_t key1) {
+    float2 fp, e1;
+    two_diff2(fc, dtL, fp, e1);
+    float2 out = fp, e = e1;
+    if (stage > 0) {
+        const float c = stage == 1 ? 0.75f : 1.0f / 3.0f;
+        float2 e2;
+        two_sum2(fp, __fmul2_rn(f2(c), fsub2(fn, fp)), out, e2);
+        e = __ffma2_rn(f2(1.0f - c), e1, e2);
+    }
+    const uint32_t ks = (uint32_t)stage * 0x85ebca77u;
+    return make_float2(sround(out.x, e.x, key0 ^ ks), sround(out.y, e.y, key1 ^ ks));
+}
+__device__ __forceinline__ float rk3_out_sr(int stage, float fc, float dtL, float fn, uint32_t key) {
+    float fp, e1;
+    two_diff(fc, dtL, fp, e1);
+    float out = fp, e = e1;
+    if (stage > 0) {
+        const float c = stage == 1 ? 0.75f : 1.0f / 3.0f;
+        float e2;
+        two_sum(fp, __fmul_rn(c, __fsub_rn(fn, fp)), out, e2);
+        e = __fmaf_rn(1.0f - c, e1, e2);
+    }
+    return sround(out, e, key ^ ((uint32_t)stage * 0x85ebca77u));
+}
+// The key of a value: its address in the stage output (unique within a launch).
+__device__ __forceinline__ uint32_t sr_key(const void* p) {
+    return (uint32_t)(reinterpret_cast<uintptr_t>(p) >> 2);
 }
 
 __device__ __forceinline__ float2 upwind2_face2(float2 b, float2 c) {

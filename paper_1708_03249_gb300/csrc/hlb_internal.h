@@ -122,6 +122,7 @@ struct GroupDev {
     int* nonfinite;          // set by the moments kernel when a node's n or T is not finite
     unsigned long long wait_ns;   // bound of every pipeline wait in the marching kernels
     int inject_stall;        // test hook: nonzero withholds the copies of a marching CTA's second step
+    int sround;              // FP32 stage outputs rounded stochastically (hlb_set_rounding), else to nearest
     int force_form;          // FP32 marching kernels: force term by FMA (0), 3xTF32 (1) or split-BF16 (2)
                              // tensor-core products
     // FP64 half-range groups above the recurrence's stable order: the

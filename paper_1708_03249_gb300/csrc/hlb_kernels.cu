@@ -367,16 +367,27 @@ stage_kernel(const GroupDev g, const R* __restrict__ fs, const R* __restrict__ f
             Lval -= force;
             if (collide) Lval -= (f - feq) * inv_tau;
             R out;
-            if (stage == 0) {
-                out = f + dt * Lval;
-            } else {
-                const R fnv = fn[row_off + (size_t)x * V + v];
-                // c f^n + (1 - c) f' as f' + c (f^n - f'): the weights sum to
-                // 1 exactly whatever the rounding of c
-                const R fp = f + dt * Lval;
-                out = fp + (stage == 1 ? R(0.75) : R(1.0 / 3.0)) * (fnv - fp);
+            bool done = false;
+            if constexpr (sizeof(R) == 4) {
+                if (g.sround) {      // stochastic rounding of the stage output (hlb_device.cuh)
+                    R* dst = fo + row_off + (size_t)x * V + v;
+                    *dst = rk3_out_sr(stage, f, -(dt * Lval), stage > 0 ? fn[row_off + (size_t)x * V + v] : R(0),
+                                      sr_key(dst));
+                    done = true;
+                }
             }
-            fo[row_off + (size_t)x * V + v] = out;
+            if (!done) {
+                if (stage == 0) {
+                    out = f + dt * Lval;
+                } else {
+                    const R fnv = fn[row_off + (size_t)x * V + v];
+                    // c f^n + (1 - c) f' as f' + c (f^n - f'): the weights sum to
+                    // 1 exactly whatever the rounding of c
+                    const R fp = f + dt * Lval;
+                    out = fp + (stage == 1 ? R(0.75) : R(1.0 / 3.0)) * (fnv - fp);
+                }
+                fo[row_off + (size_t)x * V + v] = out;
+            }
         }
         __syncthreads();
     }

@@ -48,8 +48,9 @@ constexpr size_t line_smem_bytes() {
 
 // FF = 1: the group has a per-node acceleration field; the a K rows are then
 // plain K rows, K_x f and K_y f are kept apart and scaled per cell by the a_x,
-// a_y of the factor lines (uniform plus field).
-template <int ADV, int QX2, int VY, int FM, int FF>
+// a_y of the factor lines (uniform plus field).  SR = 1: the stage outputs are
+// rounded stochastically (rk3_out_sr2, hlb_device.cuh).
+template <int ADV, int QX2, int VY, int FM, int FF, int SR = 0>
 __global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? 8 : (QX2 * VY <= 256 ? 4 : 2))))
 march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
               const float* __restrict__ fn, float* __restrict__ fo, int stage) {
@@ -317,7 +318,11 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
             }
             const float2 L = __ffma2_rn(fsub2(fc, feq), itau, __fadd2_rn(q ? divx23 : divx01, fk));
             float2 out;  // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
-            if (stage == 0) {
+            if constexpr (SR != 0) {
+                const float2 fo_n = stage > 0 ? make_float2(B.fnr[2 * q][vl], B.fnr[2 * q + 1][vl]) : f2(0.0f);
+                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, L), fo_n, sr_key(fov + roff + (x0 + 2 * q) * V),
+                                  sr_key(fov + roff + (x0 + 2 * q + 1) * V));
+            } else if (stage == 0) {
                 out = fsub2(fc, __fmul2_rn(dt2, L));
             } else {
                 const float2 fo_n = make_float2(B.fnr[2 * q][vl], B.fnr[2 * q + 1][vl]);
@@ -340,17 +345,17 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
     }
 }
 
-template <int ADV, int QX2, int VY, int FM, int FF = 0>
+template <int ADV, int QX2, int VY, int FM, int FF = 0, int SR = 0>
 void launch_line_t(const GroupDev& g, const Work* works, int nworks, const void* fs, const void* fn, void* fo,
                    int stage, cudaStream_t st) {
-    march1_kernel<ADV, QX2, VY, FM, FF><<<nworks, QX2 * VY, line_smem_bytes<QX2, VY, FM>(), st>>>(
+    march1_kernel<ADV, QX2, VY, FM, FF, SR><<<nworks, QX2 * VY, line_smem_bytes<QX2, VY, FM>(), st>>>(
         g, works, (const float*)fs, (const float*)fn, (float*)fo, stage);
 }
 
-template <int ADV, int QX2, int VY, int FM, int FF = 0>
+template <int ADV, int QX2, int VY, int FM, int FF = 0, int SR = 0>
 cudaError_t prepare_line_t() {
-    return cudaFuncSetAttribute(march1_kernel<ADV, QX2, VY, FM, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)line_smem_bytes<QX2, VY, FM>());
+    return cudaFuncSetAttribute(march1_kernel<ADV, QX2, VY, FM, FF, SR>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem_bytes<QX2, VY, FM>());
 }
 
 }  // namespace

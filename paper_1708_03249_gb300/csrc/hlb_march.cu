@@ -265,6 +265,14 @@ march_kernel(const GroupDev g, const Work* __restrict__ works, const R* __restri
             const R itau = cr[csrc_t];
             const R L = -divx[r] - divy[r] - (axr * kxf + ayr * kyf) - (fc[r] - feq) * itau;
             R out;
+            if constexpr (sizeof(R) == 4) {
+                if (g.sround) {      // stochastic rounding of the stage output (hlb_device.cuh)
+                    out = rk3_out_sr(stage, fc[r], -(dt * L), stage > 0 ? B.fnr[r][t] : R(0),
+                                     sr_key(fov + roff[r] + x * V));
+                    if (valid[r]) fov[roff[r] + x * V] = out;
+                    continue;
+                }
+            }
             if (stage == 0) {
                 out = fc[r] + dt * L;
             } else {

@@ -14,11 +14,18 @@ bool pair_available(int QX2, int VY) {
 }
 
 cudaError_t prepare_pair(int adv, int QX2, int VY, int form) {
-    if (form == kForceField) {
-#define HLB_PRF(A, B)                                                                         \
-        if (QX2 == A && VY == B)                                                              \
-            return adv == HLB_WENO5_ ? prepare_pair_t<HLB_WENO5_, A, B, kForceFMA, 1>()     \
-                                     : prepare_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1>();
+    if (form >= kForceField) {          // FMA force term with a field (FF) and / or stochastic rounding (SR)
+        const int ff = form != kForceFMASR, sr = form != kForceField;
+#define HLB_PRF(A, B)                                                                                   \
+        if (QX2 == A && VY == B) {                                                                      \
+            if (adv == HLB_WENO5_)                                                                      \
+                return ff ? (sr ? prepare_pair_t<HLB_WENO5_, A, B, kForceFMA, 1, 1>()                   \
+                                : prepare_pair_t<HLB_WENO5_, A, B, kForceFMA, 1, 0>())                  \
+                          : prepare_pair_t<HLB_WENO5_, A, B, kForceFMA, 0, 1>();                        \
+            return ff ? (sr ? prepare_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1, 1>()                     \
+                            : prepare_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1, 0>())                    \
+                      : prepare_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 0, 1>();                          \
+        }
         HLB_PAIR_LIST(HLB_PRF)
 #undef HLB_PRF
         return cudaErrorInvalidValue;
@@ -35,12 +42,20 @@ cudaError_t prepare_pair(int adv, int QX2, int VY, int form) {
 
 void launch_pair(int adv, int QX2, int VY, int form, const GroupDev& g, const Work* works, int nworks,
                  const void* fs, const void* fn, void* fo, int stage, cudaStream_t st) {
-    if (form == kForceField) {
-#define HLB_LAF(A, B)                                                                                         \
-        if (QX2 == A && VY == B) {                                                                            \
-            if (adv == HLB_WENO5_) launch_pair_t<HLB_WENO5_, A, B, kForceFMA, 1>(g, works, nworks, fs, fn, fo, stage, st); \
-            else launch_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1>(g, works, nworks, fs, fn, fo, stage, st);              \
-            return;                                                                                           \
+    if (form >= kForceField) {
+        const int ff = form != kForceFMASR, sr = form != kForceField;
+#define HLB_LAF(A, B)                                                                                       \
+        if (QX2 == A && VY == B) {                                                                          \
+            if (adv == HLB_WENO5_) {                                                                        \
+                if (!sr) launch_pair_t<HLB_WENO5_, A, B, kForceFMA, 1, 0>(g, works, nworks, fs, fn, fo, stage, st); \
+                else if (ff) launch_pair_t<HLB_WENO5_, A, B, kForceFMA, 1, 1>(g, works, nworks, fs, fn, fo, stage, st); \
+                else launch_pair_t<HLB_WENO5_, A, B, kForceFMA, 0, 1>(g, works, nworks, fs, fn, fo, stage, st); \
+            } else {                                                                                         \
+                if (!sr) launch_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1, 0>(g, works, nworks, fs, fn, fo, stage, st); \
+                else if (ff) launch_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 1, 1>(g, works, nworks, fs, fn, fo, stage, st); \
+                else launch_pair_t<HLB_UPWIND2_, A, B, kForceFMA, 0, 1>(g, works, nworks, fs, fn, fo, stage, st); \
+            }                                                                                               \
+            return;                                                                                         \
         }
         HLB_PAIR_LIST(HLB_LAF)
 #undef HLB_LAF

@@ -58,8 +58,9 @@ constexpr size_t pair_smem_bytes() {
 
 // FF = 1: the group has a per-node acceleration field; the a K rows are then
 // plain K rows, K_x f and K_y f are kept apart and scaled per cell by the a_x,
-// a_y of the factor lines (uniform plus field).
-template <int ADV, int QX2, int VY, int FM, int FF>
+// a_y of the factor lines (uniform plus field).  SR = 1: the stage outputs are
+// rounded stochastically (rk3_out_sr2, hlb_device.cuh).
+template <int ADV, int QX2, int VY, int FM, int FF, int SR = 0>
 __global__ void __launch_bounds__(QX2 * VY, (QX2 * VY <= 32 ? 16 : (QX2 * VY <= 128 ? HLB_PAIR_MIN_BLOCKS : 2)))
 march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float* __restrict__ fs,
                   const float* __restrict__ fn, float* __restrict__ fo, int stage) {
@@ -401,7 +402,11 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             float2 L = __fadd2_rn(__fadd2_rn(divx, divy), fk);
             L = __ffma2_rn(fsub2(fc, feq), itau, L);
             float2 out;      // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
-            if (stage == 0) {
+            if constexpr (SR != 0) {
+                const float2 fo_n = stage > 0 ? make_float2(B.fnr[i][0][vl], B.fnr[i][1][vl]) : f2(0.0f);
+                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, L), fo_n, sr_key(fo0 + (size_t)i * V),
+                                  sr_key(fo1 + (size_t)i * V));
+            } else if (stage == 0) {
                 out = fsub2(fc, __fmul2_rn(dt2, L));
             } else {
                 const float2 fo_n = make_float2(B.fnr[i][0][vl], B.fnr[i][1][vl]);
@@ -428,17 +433,17 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
 }
 
 
-template <int ADV, int QX2, int VY, int FM, int FF = 0>
+template <int ADV, int QX2, int VY, int FM, int FF = 0, int SR = 0>
 void launch_pair_t(const GroupDev& g, const Work* works, int nworks, const void* fs, const void* fn, void* fo,
                    int stage, cudaStream_t st) {
-    march_pair_kernel<ADV, QX2, VY, FM, FF><<<nworks, QX2 * VY, pair_smem_bytes<QX2, VY, FM>(), st>>>(
+    march_pair_kernel<ADV, QX2, VY, FM, FF, SR><<<nworks, QX2 * VY, pair_smem_bytes<QX2, VY, FM>(), st>>>(
         g, works, (const float*)fs, (const float*)fn, (float*)fo, stage);
 }
 
-template <int ADV, int QX2, int VY, int FM, int FF = 0>
+template <int ADV, int QX2, int VY, int FM, int FF = 0, int SR = 0>
 cudaError_t prepare_pair_t() {
-    return cudaFuncSetAttribute(march_pair_kernel<ADV, QX2, VY, FM, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pair_smem_bytes<QX2, VY, FM>());
+    return cudaFuncSetAttribute(march_pair_kernel<ADV, QX2, VY, FM, FF, SR>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pair_smem_bytes<QX2, VY, FM>());
 }
 
 }  // namespace

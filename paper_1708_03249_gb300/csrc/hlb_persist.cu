@@ -81,7 +81,7 @@ struct PersistLayout {
     static constexpr size_t sPt = al16(sSum + (size_t)S * 8 * sizeof(float));
     static constexpr size_t sRec = al16(sPt + (size_t)(PX + PY) * NM * sizeof(float4));
     static constexpr size_t sPv = al16(sRec + (5 * NM + 2) * sizeof(float2));
-    static constexpr size_t sRed = al16(sPv + (QX2 + VY) * sizeof(float));
+    static constexpr size_t sRed = al16(sPv + 4 * (QX2 + VY) * sizeof(float));   // p, its remainder, p^2, its remainder
     static constexpr size_t bars = al16(sRed + (2 * (S / 32) + 2) * sizeof(double));
     static constexpr size_t ints = al16(bars + (kPDepth + 3) * sizeof(unsigned long long));
     static constexpr size_t bytes = ints + 4 * sizeof(int);
@@ -134,11 +134,16 @@ __device__ __forceinline__ void node_item(const GroupDev& g, const PersistArgs& 
         for (int m = 0; m < S / 32; ++m) {
             const int vv = lane + 32 * m;
             const float f = __ldcg(fc + vv);
-            const float px = sPv[vv % QX2], py = sPv[QX2 + vv / QX2];
+            // the FP64 momenta as rounding plus remainder (the node pass's
+            // sums_kernel does the same; a fixed half-ulp error per velocity
+            // is a heat and momentum source under strong collisions)
+            const int ix = vv % QX2, jy = QX2 + vv / QX2;
+            constexpr int P = QX2 + VY;
             csum_add(s0, c0, f);
-            csum_add(s1, c1, px * f);
-            csum_add(s2, c2, py * f);
-            csum_add(s3, c3, (px * px + py * py) * f);
+            csum_add(s1, c1, __fmaf_rn(sPv[P + ix], f, sPv[ix] * f));
+            csum_add(s2, c2, __fmaf_rn(sPv[P + jy], f, sPv[jy] * f));
+            csum_add(s3, c3, __fmaf_rn(sPv[3 * P + ix] + sPv[3 * P + jy], f,
+                                       __fmaf_rn(sPv[2 * P + ix], f, sPv[2 * P + jy] * f)));
         }
         csum_warp(s0, c0);
         csum_warp(s1, c1);
@@ -426,7 +431,11 @@ __device__ HLB_MARCH_ITEM_ATTR uint32_t march_item(const GroupDev& g, const Pers
             const float2 fc = q ? fc23 : fc01;
             const float2 Lv = __ffma2_rn(fsub2(fc, feq), itau, __fadd2_rn(q ? divx23 : divx01, q ? fk23 : fk01));
             float2 out;
-            if (stage == 0) {
+            if (g.sround) {      // stochastic rounding of the stage output (hlb_device.cuh)
+                const float2 fo_n = stage > 0 ? make_float2(B.fnr[2 * q][vl], B.fnr[2 * q + 1][vl]) : f2(0.0f);
+                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, Lv), fo_n, sr_key(fov + (x0 + 2 * q) * V),
+                                  sr_key(fov + (x0 + 2 * q + 1) * V));
+            } else if (stage == 0) {
                 out = fsub2(fc, __fmul2_rn(dt2, Lv));
             } else {
                 const float2 fo_n = make_float2(B.fnr[2 * q][vl], B.fnr[2 * q + 1][vl]);
@@ -470,7 +479,14 @@ persist_line_kernel(const GroupDev g, const Work* __restrict__ works, const Pers
 
     // the tables every item reads: momenta, the equilibrium tables as row
     // pairs (dot2_pair layout), the recurrence
-    for (int i = t; i < QX2 + VY; i += S) sPv[i] = static_cast<const float*>(g.p)[i];
+    for (int i = t; i < QX2 + VY; i += S) {
+        const double p = g.pd[i], p2 = p * p;
+        const float hi = (float)p, hi2 = (float)p2;
+        sPv[i] = hi;
+        sPv[QX2 + VY + i] = (float)(p - (double)hi);
+        sPv[2 * (QX2 + VY) + i] = hi2;
+        sPv[3 * (QX2 + VY) + i] = (float)(p2 - (double)hi2);
+    }
     {
         const float2* Tx = g.Tf;
         const float2* Ty = Tx + Qx * (Nx + 1);

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhlb.so")
 HLB_OK, HLB_EINVAL, HLB_ENOMEM, HLB_ECUDA, HLB_ETIMEOUT, HLB_ENONFINITE, HLB_EUNSUPPORTED = range(7)
 HLB_UPWIND2, HLB_WENO5 = 0, 1
 HLB_FP64, HLB_FP32, HLB_FP32_TF32X3, HLB_FP32_BF16SPLIT = 0, 1, 2, 3
+HLB_ROUND_NEAREST, HLB_ROUND_STOCHASTIC = 0, 1
 STATUS_NAMES = {0: "HLB_OK", 1: "HLB_EINVAL", 2: "HLB_ENOMEM", 3: "HLB_ECUDA",
                 4: "HLB_ETIMEOUT", 5: "HLB_ENONFINITE", 6: "HLB_EUNSUPPORTED"}
 
@@ -61,6 +62,7 @@ SIGNATURES = {
     "hlb_get_dt": (C.c_int, [_P, C.c_int, _D]),
     "hlb_force_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "hlb_set_persistent": (C.c_int, [_P, C.c_int]),
+    "hlb_set_rounding": (C.c_int, [_P, C.c_int]),
     "hlb_fp32_peak": (C.c_int, [C.c_int, _D]),
     "hlb_step_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _D]),
     "hlb_get_nsteps": (C.c_int, [_P, _LL]),
@@ -191,6 +193,10 @@ class Handle:
 
     def set_persistent(self, on: bool = True):
         _check(lib().hlb_set_persistent(self._h, 1 if on else 0))
+
+    def set_rounding(self, stochastic: bool):
+        """hlb_set_rounding: FP32 stage outputs rounded stochastically or to nearest."""
+        _check(lib().hlb_set_rounding(self._h, HLB_ROUND_STOCHASTIC if stochastic else HLB_ROUND_NEAREST))
 
     def step_form(self, inst=0) -> dict:
         """{"persistent": bool, "segment_cells": int, "ctas": int, "tuned_ms": (persistent, per-stage)}

@@ -39,12 +39,17 @@ def moment_errors(mom, ref):
     }
 
 
-def run_pair(cfg, steps, seed=1, amp=0.05, init=(1.0, 0.0, 0.0, 1.0), graphs=True):
+def run_pair(cfg, steps, seed=1, amp=0.05, init=(1.0, 0.0, 0.0, 1.0), graphs=True, stochastic=None,
+             persistent=None):
     from oracle.solver import Solver, config_from
     from paper_1708_03249_gb300 import hlb
     cfgs = cfg if isinstance(cfg, list) else [cfg]
     h = hlb.Handle(cfgs, stream=_stream())
     h.set_options(use_graphs=graphs)
+    if stochastic is not None:
+        h.set_rounding(stochastic)
+    if persistent is not None:
+        h.set_persistent(persistent)
     h.init_equilibrium(*init)
     f0 = h.get_state().astype(np.float64)
     f0 = f0 * W.perturbation(f0.shape, seed=seed, amplitude=amp)
@@ -551,3 +556,49 @@ def test_fp32_moments_of_a_given_state():
     s.f = f.astype(np.float64).reshape(s.f.shape)
     errs = moment_errors(mom, _oracle_moments([s]))
     assert max(errs.values()) < 2e-7, errs
+
+
+# --- stochastic rounding of the FP32 stage outputs (hlb_set_rounding) ----------
+_SR_PHYS = dict(Kn=0.2, T_left=1.0, T_right=1.4, advection=W.WENO5, precision=W.FP32, **W.gravity(0.4, 35.0))
+_SR_CASES = {
+    "pair_2d_16x8": (dict(Qx=8, Qy=8, nx=40, ny=6, Ly=0.3, stretch_A=0.5), None),
+    "line_1d_16x8": (dict(Qx=8, Qy=8, nx=60), False),
+    "persistent_1d_16x8": (dict(Qx=8, Qy=8, nx=60), True),
+    "line_1d_32x16": (dict(Qx=16, Qy=16, nx=40), False),     # FMA force term with stochastic rounding
+    "march_scalar_8x1": (dict(Qx=4, Qy=0, nx=40), None),
+    "generic_8x2": (dict(Qx=4, Qy=2, nx=40), None),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_SR_CASES))
+def test_fp32_stochastic_rounding_parity(case):
+    # every kind of FP32 stage kernel with stochastically rounded outputs, at
+    # the FP32 bar against the oracle
+    kw, persistent = _SR_CASES[case]
+    cfg = W.make(**kw, **_SR_PHYS)
+    got, mom, N, refs = run_pair(cfg, 20, stochastic=True, persistent=persistent)
+    _check_fp32(got, mom, refs)
+    assert N[0] == pytest.approx(refs[0].total_number(), rel=1e-6)
+
+
+def test_fp32_stochastic_rounding_is_deterministic_and_takes_effect():
+    # the random numbers are a hash of address, stage and values: two runs
+    # give the same bits, and they differ from round-to-nearest in the last place
+    from paper_1708_03249_gb300 import hlb
+    cfgs = [W.make(Qx=8, Qy=8, nx=40, ny=6, Ly=0.3, **_SR_PHYS), W.make(Qx=8, Qy=8, nx=60, **_SR_PHYS)]
+    out = []
+    for stochastic in (True, True, False):
+        with hlb.Handle(cfgs, stream=_stream()) as h:
+            h.set_rounding(stochastic)
+            h.init_equilibrium(1.0, 0.02, 0.0, 1.1)
+            h.step(5)
+            out.append(h.get_state())
+    np.testing.assert_array_equal(out[0], out[1])
+    diff = out[0] != out[2]
+    assert 0.01 < diff.mean() < 0.9
+    rel = np.abs(out[0][diff].astype(np.float64) - out[2][diff]) / np.abs(out[2][diff])
+    assert rel.max() < 1e-5
+    with hlb.Handle(cfgs[0]) as h:
+        with pytest.raises(hlb.HlbError):
+            lib = hlb.lib()
+            hlb._check(lib.hlb_set_rounding(h._h, 2))
