@@ -809,11 +809,13 @@ def run_other(args):
 
 def run_steady(args):
     """The stretched channel (512 cells, Q = 8 x 8, WENO5) toward its steady state:
-    the FP64 and FP32 paths from the same FP32-rounded perturbed equilibrium,
-    stepped side by side in chunks, recording the last step's residual
-    max|f^{n+1} - f^n| / (dt max f) of each and the largest relative deviation
-    of the FP32 moments n, T, q from the FP64 ones.  A diagnostic of how far
-    the FP32 state can follow the FP64 one over long runs, not a parity test."""
+    the FP64 path and the FP32 path with round-to-nearest and with stochastic
+    stage outputs (hlb_set_rounding), from the same FP32-rounded perturbed
+    equilibrium, stepped side by side in chunks, recording the last step's
+    residual max|f^{n+1} - f^n| / (dt max f) of each and the largest relative
+    deviation of each FP32 run's moments n, T, q from the FP64 ones.  A
+    diagnostic of how far the FP32 state can follow the FP64 one over long
+    runs, not a parity test."""
     import numpy as np
     import torch
 
@@ -830,22 +832,28 @@ def run_steady(args):
     t0 = time.perf_counter()
     for Kn in W.CHANNEL_1D_STRETCHED_KN:
         c32, c64 = W.channel_1d_stretched(Kn), W.channel_1d_stretched(Kn, precision=W.FP64)
-        with hlb.Handle(c64, stream=stream.cuda_stream) as h, hlb.Handle(c32, stream=stream.cuda_stream) as g:
+        with hlb.Handle(c64, stream=stream.cuda_stream) as h, hlb.Handle(c32, stream=stream.cuda_stream) as g, \
+                hlb.Handle(c32, stream=stream.cuda_stream) as gs:
             g.init_equilibrium(1.0, 0.0, 0.0, 1.0)
             f0 = (g.get_state().astype(np.float64) * W.perturbation(g.values, seed=1, amplitude=0.05)).astype(np.float32)
             g.set_state(f0)
+            gs.set_state(f0)
+            gs.set_rounding(True)
             h.set_state(f0.astype(np.float64))
             hist, steps = [], 0
+
+            def dev(a, b):
+                return float(max(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max(),
+                                 np.abs(a[2] - b[2]).max() / np.abs(b[2]).max(),
+                                 np.abs(a[3] - b[3]).max() / max(np.abs(b[3]).max(), 1e-300)))
             while steps < total:
-                h.step(chunk)
-                g.step(chunk)
+                for hh in (h, g, gs):
+                    hh.step(chunk)
                 steps += chunk
-                r64, r32 = float(h.diag()[1][0]), float(g.diag()[1][0])
-                n6, _, T6, q6 = h.moments()
-                n3, _, T3, q3 = g.moments()
-                dev = max(np.abs(n3 - n6).max() / np.abs(n6).max(), np.abs(T3 - T6).max() / np.abs(T6).max(),
-                          np.abs(q3 - q6).max() / max(np.abs(q6).max(), 1e-300))
-                hist.append({"steps": steps, "residual_fp64": r64, "residual_fp32": r32, "moment_dev": float(dev)})
+                m64 = h.moments()
+                hist.append({"steps": steps, "residual_fp64": float(h.diag()[1][0]),
+                             "residual_fp32": float(g.diag()[1][0]), "residual_fp32_sr": float(gs.diag()[1][0]),
+                             "moment_dev": dev(g.moments(), m64), "moment_dev_sr": dev(gs.moments(), m64)})
             per_kn[f"{Kn:g}"] = {"dt": h.dt(), "history": hist}
     line = {"metric": "steady-state residual and FP32 moment deviation from FP64", "n_gpus": 1,
             "config": {"workload": "stretched_channel_steady_state",
