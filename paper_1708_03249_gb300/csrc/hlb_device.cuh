@@ -460,15 +460,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// s rounded stochastically toward s + e (|e| <= ulp(s) / 2).
-__device__ __forceinline__ float sround(float s, float e, uint32_t key) {
+// s rounded stochastically toward s + e (|e| <= ulp(s) / 2), r uniform in [0, 1).
+__device__ __forceinline__ float sround(float s, float e, float r) {
     if (e == 0.0f || s == 0.0f || !(fabsf(s) < 3.0e38f)) return s;
     const uint32_t b = __float_as_uint(s);
     const float nxt = __uint_as_float((e > 0.0f) == (s > 0.0f) ? b + 1u : b - 1u);
-    const float dist = fabsf(__fsub_rn(nxt, s));
-    const uint32_t h = sr_hash(key ^ sr_hash(b ^ (__float_as_uint(e) * 0x9e3779b9u)));
-    const float r = (float)(h >> 8) * (1.0f / 16777216.0f);      // uniform in [0, 1)
-    return fabsf(e) > r * dist ? nxt : s;
+    return fabsf(e) > r * fabsf(__fsub_rn(nxt, s)) ? nxt : s;
 }
 
 // The RK-3 stage output (Eq. "eq:rk3") from fc, dtL = dt L[fc] and, at stages
@@ -476,8 +473,8 @@ __device__ __forceinline__ float sround(float s, float e, uint32_t key) {
 // and 2 give fp + c (f^n - fp) with fp = fc - dtL, c = 3/4 or 1/3, whose exact
 // value is out + e2 + (1 - c) e1 for the errors e1 of fp and e2 of the final
 // addition (the product's rounding is relative to the increment and left out).
-__device__ __forceinline__ float2 rk3_out_sr2(int stage, float2 fc, float2 dtL, float2 fn, uint32_t key0,
-                                              uint32_t key1) {
+// One hash serves both lanes (16 bits of probability each).
+__device__ __forceinline__ float2 rk3_out_sr2(int stage, float2 fc, float2 dtL, float2 fn, uint32_t key) {
     float2 fp, e1;
     two_diff2(fc, dtL, fp, e1);
     float2 out = fp, e = e1;
@@ -487,8 +484,11 @@ __device__ __forceinline__ float2 rk3_out_sr2(int stage, float2 fc, float2 dtL, 
         two_sum2(fp, __fmul2_rn(f2(c), fsub2(fn, fp)), out, e2);
         e = __ffma2_rn(f2(1.0f - c), e1, e2);
     }
-    const uint32_t ks = (uint32_t)stage * 0x85ebca77u;
-    return make_float2(sround(out.x, e.x, key0 ^ ks), sround(out.y, e.y, key1 ^ ks));
+    const uint32_t h = sr_hash(key ^ ((uint32_t)stage * 0x85ebca77u) ^ __float_as_uint(out.x) ^
+                               (__float_as_uint(e.x) * 0x9e3779b9u) ^
+                               ((__float_as_uint(out.y) ^ __float_as_uint(e.y)) * 0xc2b2ae35u));
+    return make_float2(sround(out.x, e.x, (float)(h & 0xffffu) * (1.0f / 65536.0f)),
+                       sround(out.y, e.y, (float)(h >> 16) * (1.0f / 65536.0f)));
 }
 __device__ __forceinline__ float rk3_out_sr(int stage, float fc, float dtL, float fn, uint32_t key) {
     float fp, e1;
@@ -500,7 +500,9 @@ __device__ __forceinline__ float rk3_out_sr(int stage, float fc, float dtL, floa
         two_sum(fp, __fmul_rn(c, __fsub_rn(fn, fp)), out, e2);
         e = __fmaf_rn(1.0f - c, e1, e2);
     }
-    return sround(out, e, key ^ ((uint32_t)stage * 0x85ebca77u));
+    const uint32_t h = sr_hash(key ^ ((uint32_t)stage * 0x85ebca77u) ^ __float_as_uint(out) ^
+                               (__float_as_uint(e) * 0x9e3779b9u));
+    return sround(out, e, (float)(h >> 8) * (1.0f / 16777216.0f));
 }
 // The key of a value: its address in the stage output (unique within a launch).
 __device__ __forceinline__ uint32_t sr_key(const void* p) {

@@ -320,8 +320,7 @@ march1_kernel(const GroupDev g, const Work* __restrict__ works, const float* __r
             float2 out;  // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
             if constexpr (SR != 0) {
                 const float2 fo_n = stage > 0 ? make_float2(B.fnr[2 * q][vl], B.fnr[2 * q + 1][vl]) : f2(0.0f);
-                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, L), fo_n, sr_key(fov + roff + (x0 + 2 * q) * V),
-                                  sr_key(fov + roff + (x0 + 2 * q + 1) * V));
+                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, L), fo_n, sr_key(fov + roff + (x0 + 2 * q) * V));
             } else if (stage == 0) {
                 out = fsub2(fc, __fmul2_rn(dt2, L));
             } else {

@@ -404,8 +404,7 @@ march_pair_kernel(const GroupDev g, const Work* __restrict__ works, const float*
             float2 out;      // fc + dt (-L), then the RK-3 combination (Eq. "eq:rk3")
             if constexpr (SR != 0) {
                 const float2 fo_n = stage > 0 ? make_float2(B.fnr[i][0][vl], B.fnr[i][1][vl]) : f2(0.0f);
-                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, L), fo_n, sr_key(fo0 + (size_t)i * V),
-                                  sr_key(fo1 + (size_t)i * V));
+                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, L), fo_n, sr_key(fo0 + (size_t)i * V));
             } else if (stage == 0) {
                 out = fsub2(fc, __fmul2_rn(dt2, L));
             } else {

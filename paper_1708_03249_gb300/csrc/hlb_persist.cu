@@ -433,8 +433,7 @@ __device__ HLB_MARCH_ITEM_ATTR uint32_t march_item(const GroupDev& g, const Pers
             float2 out;
             if (g.sround) {      // stochastic rounding of the stage output (hlb_device.cuh)
                 const float2 fo_n = stage > 0 ? make_float2(B.fnr[2 * q][vl], B.fnr[2 * q + 1][vl]) : f2(0.0f);
-                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, Lv), fo_n, sr_key(fov + (x0 + 2 * q) * V),
-                                  sr_key(fov + (x0 + 2 * q + 1) * V));
+                out = rk3_out_sr2(stage, fc, __fmul2_rn(dt2, Lv), fo_n, sr_key(fov + (x0 + 2 * q) * V));
             } else if (stage == 0) {
                 out = fsub2(fc, __fmul2_rn(dt2, Lv));
             } else {
