@@ -1,5 +1,5 @@
 """FP32 parity with the FP64 oracle at the configurations' stated sizes and
-lengths (the spec bar: moments within 1e-5 of the oracle).
+lengths (the FP32 bar: moments within 1e-5 of the oracle).
 
 The oracle's long runs are stored by ``tests/golden/make_long_runs.py`` (which
 calls only the oracle): the final n, u, T, q per node after the stated number
@@ -62,9 +62,10 @@ def _errors(mom, ref, sl=slice(None)):
             "q": np.abs(q - rq).max() / max(np.abs(rq).max(), np.abs(rn).max() * sT ** 1.5)}
 
 
-def _run(cfgs, states, steps):
+def _run(cfgs, states, steps, stochastic=False):
     from paper_1708_03249_gb300 import hlb
     with hlb.Handle(cfgs, stream=_stream()) as h:
+        h.set_rounding(stochastic)
         h.set_state(np.concatenate([s.reshape(-1) for s in states]).astype(np.float32))
         h.step(steps)
         mom = h.moments()
@@ -72,35 +73,38 @@ def _run(cfgs, states, steps):
     return mom, N
 
 
+@pytest.mark.parametrize("stochastic", [False, True], ids=["nearest", "stochastic"])
 @pytest.mark.parametrize("Kn", W.CHANNEL_1D_STRETCHED_KN)
-def test_fp32_stretched_channel_at_length(Kn):
+def test_fp32_stretched_channel_at_length(Kn, stochastic):
     from make_long_runs import initial_state
     ref = _load(f"stretched_kn{Kn:g}")
     cfg = json.loads(str(ref["config"]))
     assert cfg == W.channel_1d_stretched(Kn)
-    mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]))
+    mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]), stochastic)
     errs = _errors(mom, ref)
     assert max(errs.values()) < 1e-5, errs
     assert N[0] == pytest.approx(float(ref["N"]), rel=1e-5)
 
 
-def test_fp32_box_q16_at_length():
+@pytest.mark.parametrize("stochastic", [False, True], ids=["nearest", "stochastic"])
+def test_fp32_box_q16_at_length(stochastic):
     from make_long_runs import BOX_N, initial_state
     ref = _load(f"box{BOX_N}")
     cfg = json.loads(str(ref["config"]))
     assert cfg == W.scaled(W.BOX_2D, nx=BOX_N, ny=BOX_N)
-    mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]))
+    mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]), stochastic)
     errs = _errors(mom, ref)
     assert max(errs.values()) < 1e-5, errs
     assert N[0] == pytest.approx(float(ref["N"]), rel=1e-5)
 
 
-def test_fp32_large_channel_window_at_length():
+@pytest.mark.parametrize("stochastic", [False, True], ids=["nearest", "stochastic"])
+def test_fp32_large_channel_window_at_length(stochastic):
     from make_long_runs import LARGE_N, initial_state, large_window
     ref = _load(f"large{LARGE_N}")
     cfg = json.loads(str(ref["config"]))
     assert cfg == large_window()
-    mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]))
+    mom, N = _run([cfg], [initial_state(cfg, int(ref["seed"]))], int(ref["steps"]), stochastic)
     errs = _errors(mom, ref)
     assert max(errs.values()) < 1e-5, errs
     assert N[0] == pytest.approx(float(ref["N"]), rel=1e-5)
