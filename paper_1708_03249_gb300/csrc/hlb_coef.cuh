@@ -123,7 +123,7 @@ __device__ __forceinline__ void factor_line_df(const GD& g, double n, double ux,
         return;
     }
     NodeDF in;
-    node_inputs_df(n, ux, uy, uz, T, in);
+    node_inputs_df(n, ux, uy, uz, T, Nx, in);
     float2 G[NM];
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {                    // n g_x, p_x > 0 then p_x < 0

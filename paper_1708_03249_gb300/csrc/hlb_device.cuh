@@ -757,10 +757,63 @@ __device__ __forceinline__ void mbar_drain(unsigned long long* bar, uint32_t par
     }
 }
 
+// exp(y) in double-float for y in [-60, 0]: y = k ln 2 + r with |r| <= ln2 / 2
+// (k ln 2 subtracted exactly: ln 2 as hi + lo, k hi by TwoProduct), exp(r) by
+// its Taylor polynomial to degree 13 (remainder below 2e-17) evaluated by
+// Horner's rule in double-float, then times 2^k (exact).
+__device__ inline float2 df_exp_nonpos(float2 y) {
+    // 1/n!, n = 0 .. 13, as double-float pairs (rounded from the exact rationals)
+    const float fh[14] = {1.0f, 1.0f, 0.5f, 0.1666666716337204f, 0.0416666679084301f, 0.008333333767950535f,
+                          0.0013888889225199819f, 0.00019841270113829523f, 2.4801587642286904e-05f,
+                          2.7557318844628753e-06f, 2.755731998149713e-07f, 2.5052107943679403e-08f,
+                          2.0876755879584152e-09f, 1.6059044372074283e-10f};
+    const float fl[14] = {0.0f, 0.0f, 0.0f, -4.967053879312289e-09f, -1.2417634698280722e-09f,
+                          -4.34617203337595e-10f, -3.3631094437103215e-11f, -2.725596874933456e-12f,
+                          -3.40699609366682e-13f, 3.793571224297229e-14f, -7.575112209051195e-15f,
+                          4.4176230446483665e-16f, 1.1082839147459852e-16f, -5.352526511562726e-18f};
+    const float ln2h = 0.6931471824645996f, ln2l = -1.9046542121259336e-09f;
+    const float k = rintf(y.x * 1.4426950408889634f);
+    const float p = k * ln2h, e = fmaf(k, ln2h, -p);          // k ln2h = p + e exactly
+    const float q = k * ln2l, eq = fmaf(k, ln2l, -q);
+    float2 r = df_add(df_add(y, make_float2(-p, -e)), make_float2(-q, -eq));
+    float2 sum = make_float2(fh[13], fl[13]);
+#pragma unroll
+    for (int n = 12; n >= 0; --n) sum = df_add(df_mul(sum, r), make_float2(fh[n], fl[n]));
+    const int ki = (int)k;
+    return make_float2(ldexpf(sum.x, ki), ldexpf(sum.y, ki));
+}
+
+// x / m in double-float for a small positive integer m: the high part's
+// remainder x.hi - q1 m is exact (FMA), the low part carries it.
+__device__ __forceinline__ float2 df_div_small(float2 x, float m) {
+    const float q1 = __fdividef(x.x, m);
+    const float rem = fmaf(-q1, m, x.x);
+    return df_fast_two_sum(q1, __fdividef(rem + x.y, m));
+}
+
+// erf(z) in double-float for |z| <= 2.5 from E = exp(-z^2): erf z =
+// (2/sqrt(pi)) E z sum_n (2 z^2)^n / (1 3 5 ... (2n+1)), a series of positive
+// terms (no cancellation; they peak near n = z^2 and fall below 2^-52 of the
+// sum by n = 40 at z = 2.5).
+__device__ inline float2 df_erf_series(float2 z, float2 z2, float2 E) {
+    const float2 w = make_float2(2.0f * z2.x, 2.0f * z2.y);
+    float2 t = make_float2(1.0f, 0.0f), sum = t;
+    for (int n = 1; n < 48; ++n) {
+        t = df_div_small(df_mul(t, w), (float)(2 * n + 1));
+        sum = df_add(sum, t);
+        if (__all_sync(__activemask(), t.x < sum.x * 2.0e-16f)) break;
+    }
+    const float2 two_sqrtpi = make_float2(1.128379225730896f, -5.8635382771399236e-08f);
+    return df_mul(df_mul(two_sqrtpi, E), df_mul(z, sum));
+}
+
 // The half-range coefficients G^{+-}_l (roles 0, 1) and the full-range ones
 // (roles 2: p_y, 3: p_z) of node_coefficients, in double-float.  recf holds
 // (hi, lo) pairs of ra, rb, rc, h0, 1/ra in the layout of rec; the values that
-// start the recurrence (erf, exp, sqrt) are formed in FP64 once.
+// start the recurrence come from FP64 n, u, T: sqrt(T) and 1/sqrt(T) in FP64,
+// erf and exp in double-float where the recurrence's growth (about threefold
+// per order) keeps their ~1e-13 error below FP32 resolution (orders up to 10),
+// in FP64 above.
 // Per-node inputs of node_coefficients_df, formed once per node in FP64:
 // ux, uy, uz, T, and for the half-range recurrence
 // E = erf(u_x / sqrt(2T)) and g(0) = exp(-u_x^2 / 2T) / sqrt(2 pi T).
@@ -768,16 +821,29 @@ struct NodeDF {
     float2 ux, uy, uz, T, Tm1, erf_z, g0, n;
 };
 
-__device__ inline void node_inputs_df(double n, double ux, double uy, double uz, double T, NodeDF& o) {
+#ifndef HLB_DF_SPECIAL_MAX_N
+#define HLB_DF_SPECIAL_MAX_N 10
+#endif
+__device__ inline void node_inputs_df(double n, double ux, double uy, double uz, double T, int Nx, NodeDF& o) {
     o.n = df_from_double(n);
     o.ux = df_from_double(ux);
     o.uy = df_from_double(uy);
     o.uz = df_from_double(uz);
     o.T = df_from_double(T);
     o.Tm1 = df_from_double(T - 1.0);
-    const double rt = sqrt(T);
-    o.erf_z = df_from_double(erf(ux / (1.4142135623730951 * rt)));
-    o.g0 = df_from_double(exp(-ux * ux / (2.0 * T)) / (kSqrt2Pi * rt));
+    const double irt = 1.0 / sqrt(T);
+    const double z = ux * irt * 0.70710678118654752440;     // u_x / sqrt(2T)
+    if (Nx <= HLB_DF_SPECIAL_MAX_N && fabs(z) <= 2.5) {
+        const float2 zd = df_from_double(z);
+        const float2 z2 = df_mul(zd, zd);
+        const float2 E = df_exp_nonpos(make_float2(-z2.x, -z2.y));          // exp(-u_x^2 / 2T)
+        o.erf_z = df_erf_series(zd, z2, E);
+        const float2 inv_sqrt2pi = make_float2(0.3989422917366028f, -1.1335170135851058e-08f);
+        o.g0 = df_mul(df_mul(E, inv_sqrt2pi), df_from_double(irt));          // E / sqrt(2 pi T)
+    } else {
+        o.erf_z = df_from_double(erf(z));
+        o.g0 = df_from_double(exp(-z * z) * (irt / kSqrt2Pi));
+    }
 }
 
 // The half-range coefficients G^{+-}_l (roles 0, 1) and the full-range ones

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(32) coef_kernel(const GroupDev g, const R* __r
             sNT[2 * lane + 1] = n * inv_Kn;
             if (active) {
                 if (df) {
-                    node_inputs_df(n, ux, uy, uz, T, sIn[lane]);
+                    node_inputs_df(n, ux, uy, uz, T, Nx, sIn[lane]);
                     for (int role = 0; role < 4; ++role)
                         node_coefficients_df(g, role, sIn[lane], sRecF, sGF + lane * ncoef);
                 } else {
