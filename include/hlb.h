@@ -396,6 +396,14 @@ hlb_status hlb_launch_count(hlb_handle* h, long long* launches, int reset);
  * are unaffected.  Synchronises if a CUDA graph has to be re-captured. */
 hlb_status hlb_set_wait_test(hlb_handle* h, int withhold_copies, double wait_limit_s);
 
+/* Test hook: the double-float exp(-z^2) and erf(z) from which the FP32
+ * groups' node pass starts the half-range recurrence (App. A; used for
+ * equilibrium orders up to 10 and |z| = |u_x| / sqrt(2T) <= 2.5, FP64 erf and
+ * exp otherwise), evaluated for n values z in device memory, the results as
+ * doubles (hi + lo) into device arrays; synchronises the device.  No
+ * counterpart in the paper.  Errors: HLB_EINVAL (n < 0, NULL), HLB_ECUDA. */
+hlb_status hlb_df_special_check(const double* z_dev, int n, double* erf_dev, double* exp_dev);
+
 /* Test hook of the out-of-memory paths (no counterpart in the paper; process
  * wide, no handle).  nth > 0 arms it: the nth device or page-locked
  * allocation the library makes from then on fails as if memory were

@@ -1738,6 +1738,14 @@ hlb_status hlb_fp32_peak(int packed, double* tflops) {
     return HLB_OK;
 }
 
+hlb_status hlb_df_special_check(const double* z_dev, int n, double* erf_dev, double* exp_dev) {
+    if (n < 0) return fail(HLB_EINVAL, "n < 0");
+    if (n > 0 && (!z_dev || !erf_dev || !exp_dev)) return fail(HLB_EINVAL, "buffer is NULL");
+    const cudaError_t e = hlb::launch_df_special(z_dev, n, erf_dev, exp_dev);
+    if (e != cudaSuccess) return fail(HLB_ECUDA, std::string("double-float check: ") + cudaGetErrorString(e));
+    return HLB_OK;
+}
+
 hlb_status hlb_set_persistent(hlb_handle* h, int on) {
     if (!h) return fail(HLB_EINVAL, "handle is NULL");
     if (h->persistent != (on != 0) && h->graph) {     // the captured steps change: re-capture

@@ -219,6 +219,9 @@ void launch_broadcast(int precision, void* f, const void* gvec, long long nvalue
 // FP32 FMA throughput of the current device in TFLOP/s (FMA = 2 flop), scalar
 // or packed f32x2 (hlb_kernels.cu)
 cudaError_t measure_fp32_peak(int packed, double* tflops);
+// The double-float exp(-z^2) and erf(z) of the factor-line prelude for n
+// device values z (|z| <= 2.5), as doubles (hi + lo), synchronously.
+cudaError_t launch_df_special(const double* z, int n, double* erf_out, double* exp_out);
 // n, u, T, q of every node of the group (any output may be NULL).  Node j of
 // member k goes to index gnode[k] + (j - node_start[k]) of the outputs when
 // gnode (device, [ninst]) is given, else to node_base + j.

@@ -372,6 +372,24 @@ static int one_wave(const void* func, int block, size_t smem, int want) {
     return want < nsm * per ? (want > 0 ? want : 1) : nsm * per;
 }
 
+__global__ void df_special_kernel(const double* __restrict__ z, int n, double* __restrict__ erf_out,
+                                  double* __restrict__ exp_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 zd = df_from_double(z[i]);
+    const float2 z2 = df_mul(zd, zd);
+    const float2 E = df_exp_nonpos(make_float2(-z2.x, -z2.y));
+    const float2 er = df_erf_series(zd, z2, E);
+    erf_out[i] = (double)er.x + (double)er.y;
+    exp_out[i] = (double)E.x + (double)E.y;
+}
+
+cudaError_t launch_df_special(const double* z, int n, double* erf_out, double* exp_out) {
+    if (n > 0) df_special_kernel<<<(n + 127) / 128, 128>>>(z, n, erf_out, exp_out);
+    const cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : cudaDeviceSynchronize();
+}
+
 // Node pass of a stage: the quadrature sums of every node, then the factor
 // lines.  The sums live in the first 8 R of each node's factor line slot of
 // an auxiliary buffer (g.sums).

@@ -63,6 +63,7 @@ SIGNATURES = {
     "hlb_force_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "hlb_set_persistent": (C.c_int, [_P, C.c_int]),
     "hlb_set_rounding": (C.c_int, [_P, C.c_int]),
+    "hlb_df_special_check": (C.c_int, [_P, C.c_int, _P, _P]),
     "hlb_fp32_peak": (C.c_int, [C.c_int, _D]),
     "hlb_step_form": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _D]),
     "hlb_get_nsteps": (C.c_int, [_P, _LL]),
@@ -341,3 +342,8 @@ def fp32_peak(packed: bool = False) -> float:
 
 def version() -> str:
     return lib().hlb_version().decode()
+
+
+def df_special_check(z_ptr: int, n: int, erf_ptr: int, exp_ptr: int):
+    """hlb_df_special_check: the node pass's double-float erf(z) and exp(-z^2) (device pointers)."""
+    _check(lib().hlb_df_special_check(z_ptr, n, erf_ptr, exp_ptr))

@@ -602,3 +602,26 @@ def test_fp32_stochastic_rounding_is_deterministic_and_takes_effect():
         with pytest.raises(hlb.HlbError):
             lib = hlb.lib()
             hlb._check(lib.hlb_set_rounding(h._h, 2))
+
+
+def test_double_float_erf_and_exp_of_the_node_pass():
+    # the double-float exp(-z^2) and erf(z) that start the FP32 groups' half-
+    # range recurrence at orders up to 10, against FP64 (Python's math module):
+    # the recurrence grows an error about threefold per order, so 3^10 x their
+    # error must stay below FP32 resolution
+    from paper_1708_03249_gb300 import hlb
+    z = np.concatenate([np.linspace(0.0, 2.5, 501), -np.linspace(1e-3, 2.5, 97), [1e-8, 1e-4, 0.05]])
+    zd = torch.from_numpy(z).cuda()
+    e_out = torch.zeros_like(zd)
+    x_out = torch.zeros_like(zd)
+    torch.cuda.synchronize()
+    hlb.df_special_check(zd.data_ptr(), z.size, e_out.data_ptr(), x_out.data_ptr())
+    got_erf, got_exp = e_out.cpu().numpy(), x_out.cpu().numpy()
+    ref_erf = np.array([math.erf(v) for v in z])
+    ref_exp = np.array([math.exp(-v * v) for v in z])
+    err_exp = np.abs(got_exp / ref_exp - 1.0).max()
+    nz = ref_erf != 0.0
+    err_erf = np.abs(got_erf[nz] / ref_erf[nz] - 1.0).max()
+    assert err_exp < 1e-13 and err_erf < 1e-13, (err_exp, err_erf)
+    assert got_erf[z == 0.0].max() == 0.0
+    assert 3.0 ** 10 * max(err_exp, err_erf) < 2.0 ** -24
