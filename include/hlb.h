@@ -345,14 +345,13 @@ hlb_status hlb_set_persistent(hlb_handle* h, int on);
  * place of f, so near a steady state the FP32 state stops where |dt L| is
  * below that, short of L = 0 by about that over dt times the slowest
  * relaxation rate (with small time steps this can exceed 1e-5 of the
- * moments).  Stochastic rounding moves each output of a step's last stage
- * one unit in the last place toward its exact value (out of TwoSum error
- * terms of the stage's last additions) with probability equal to the
- * remainder's fraction of that unit, so that its expectation is exact (the
- * intermediate stages round to nearest); the random number is a hash of the
+ * moments).  Stochastic rounding moves each output one unit in the last
+ * place toward its exact value (out of TwoSum error terms of the stage's last
+ * additions) with probability equal to the remainder's fraction of that
+ * unit, so that its expectation is exact; the random number is a hash of the
  * value's address, the stage and the bits of the value and its error:
- * deterministic, run to run and inside a captured graph.  It costs a few tens
- * of instructions per node-velocity in that stage, and the FP32 marching
+ * deterministic, run to run and inside a captured graph.  It costs a few
+ * tens of instructions per node-velocity and stage, and the FP32 marching
  * kernels then take the FMA force term (not the tensor-core forms).  FP64
  * groups are unaffected.  Drops a captured graph (synchronises).  No
  * counterpart in the paper.  Errors: HLB_EINVAL, HLB_ECUDA. */

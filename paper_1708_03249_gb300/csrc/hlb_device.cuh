@@ -419,14 +419,12 @@ __device__ __forceinline__ float2 weno5_scaled2(float2 a, float2 b, float2 c, fl
 // half a unit in the last place (ulp): near a steady state the FP32 state
 // stops where |dt L| < ulp / 2, short of L = 0 by about ulp / (dt x the
 // slowest relaxation rate), which can exceed the 1e-5 parity bar when dt is
-// small.  Here the step's last stage output s = RN(v) comes with the error e
-// of its last additions (s + e = v, by the TwoSum of Knuth and Moller), and s
-// moves one ulp toward v with probability |e| / ulp, so that its expectation
-// is v and the state keeps drifting toward L = 0 (the two intermediate stages
-// round to nearest: where they freeze, the last stage still adds 2/3 dt L,
-// rounded without bias).  The probability comes from a hash of the value's
-// address, the stage and the bits of s and e: deterministic, no state, the
-// same inside a captured graph.
+// small.  Here the stage output s = RN(v) comes with the error e of its last
+// additions (s + e = v, by the TwoSum of Knuth and Moller), and s moves one
+// ulp toward v with probability |e| / ulp, so that its expectation is v and
+// the state keeps drifting toward L = 0.  The probability comes from a hash
+// of the value's address, the stage and the bits of s and e: deterministic,
+// no state, the same inside a captured graph.
 // ---------------------------------------------------------------------------
 // A 32-bit integer finaliser (xor-shift and multiply rounds, the constants of
 // C. Wellons' "lowbias32" from his hash-prospector search).
@@ -471,17 +469,12 @@ __device__ __forceinline__ float sround(float s, float e, float r) {
 }
 
 // The RK-3 stage output (Eq. "eq:rk3") from fc, dtL = dt L[fc] and, at stages
-// 1 and 2, f^n: stage 0 gives fc - dtL, stages 1 and 2 fp + c (f^n - fp) with
-// fp = fc - dtL, c = 3/4 or 1/3.  Stages 0 and 1 round to nearest; stage 2,
-// whose exact value is out + e2 + (2/3) e1 for the errors e1 of fp and e2 of
-// the final addition (the product's rounding is relative to the increment
-// and left out), rounds stochastically.  One hash serves both lanes (16 bits
-// of probability each).
+// 1 and 2, f^n, with stochastic rounding: stage 0 gives fc - dtL; stages 1
+// and 2 give fp + c (f^n - fp) with fp = fc - dtL, c = 3/4 or 1/3, whose exact
+// value is out + e2 + (1 - c) e1 for the errors e1 of fp and e2 of the final
+// addition (the product's rounding is relative to the increment and left out).
+// One hash serves both lanes (16 bits of probability each).
 __device__ __forceinline__ float2 rk3_out_sr2(int stage, float2 fc, float2 dtL, float2 fn, uint32_t key) {
-    if (stage < 2) {          // intermediate stages to nearest
-        const float2 fp = fsub2(fc, dtL);
-        return stage == 0 ? fp : __ffma2_rn(f2(0.75f), fsub2(fn, fp), fp);
-    }
     float2 fp, e1;
     two_diff2(fc, dtL, fp, e1);
     float2 out = fp, e = e1;
@@ -498,10 +491,6 @@ __device__ __forceinline__ float2 rk3_out_sr2(int stage, float2 fc, float2 dtL, 
                        sround(out.y, e.y, (float)(h >> 16) * (1.0f / 65536.0f)));
 }
 __device__ __forceinline__ float rk3_out_sr(int stage, float fc, float dtL, float fn, uint32_t key) {
-    if (stage < 2) {          // intermediate stages to nearest
-        const float fp = __fsub_rn(fc, dtL);
-        return stage == 0 ? fp : __fmaf_rn(0.75f, __fsub_rn(fn, fp), fp);
-    }
     float fp, e1;
     two_diff(fc, dtL, fp, e1);
     float out = fp, e = e1;
