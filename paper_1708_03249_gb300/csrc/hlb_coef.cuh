@@ -112,9 +112,9 @@ __device__ __forceinline__ void lines_dot2(float* line, const float4* P, int nro
 // (dot2_pair layout), sRec the double-float recurrence table.  GD is GroupDev
 // or FactorDims (the fields read here).
 template <int NM, typename GD>
-__device__ __forceinline__ void factor_line_df(const GD& g, double n, double ux, double uy, double uz, double T,
-                                               double itau, const float4* sPx, const float4* sPy, const float4* sPz,
-                                               const float2* sRec, float* line) {
+__device__ __forceinline__ void factor_line_df_in(const GD& g, const NodeDF& in, double itau, const float4* sPx,
+                                                  const float4* sPy, const float4* sPz, const float2* sRec,
+                                                  float* line) {
     const int Nx = g.Nx, Ny = g.Ny, Nz = g.Nz, Qx = g.Qx, QX2 = g.QX2, VY = g.VY, VZ = g.VZ, ncp = g.ncp;
     for (int o = QX2 + VY + VZ; o < ncp; ++o) line[o] = 0.0f;
     line[QX2 + VY + VZ] = (float)itau;
@@ -122,8 +122,6 @@ __device__ __forceinline__ void factor_line_df(const GD& g, double n, double ux,
         for (int o = 0; o < QX2 + VY + VZ; ++o) line[o] = 0.0f;
         return;
     }
-    NodeDF in;
-    node_inputs_df(n, ux, uy, uz, T, Nx, in);
     float2 G[NM];
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {                    // n g_x, p_x > 0 then p_x < 0
@@ -145,6 +143,78 @@ __device__ __forceinline__ void factor_line_df(const GD& g, double n, double ux,
     } else {
         line[QX2 + VY] = 1.0f;
     }
+}
+
+template <int NM, typename GD>
+__device__ __forceinline__ void factor_line_df(const GD& g, double n, double ux, double uy, double uz, double T,
+                                               double itau, const float4* sPx, const float4* sPy, const float4* sPz,
+                                               const float2* sRec, float* line) {
+    NodeDF in;
+    if (itau != 0.0) node_inputs_df(n, ux, uy, uz, T, g.Nx, in);
+    factor_line_df_in<NM>(g, in, itau, sPx, sPy, sPz, sRec, line);
+}
+
+// s + e = a + b exactly (TwoSum), whatever the magnitudes.
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+
+// 1/x in double-float: the FP32 reciprocal refined by one Newton step
+// (r + r (1 - x r), the residual formed exactly enough in double-float).
+__device__ __forceinline__ float2 df_recip(float2 x) {
+    const float r = 1.0f / x.x;
+    const float2 res = df_add(make_float2(1.0f, 0.0f), df_mul(make_float2(-x.x, -x.y), make_float2(r, 0.0f)));
+    return df_add(make_float2(r, 0.0f), df_mul(make_float2(r, 0.0f), res));
+}
+
+// sqrt(x) in double-float (x > 0): the FP32 root s refined by one Newton step
+// s + (x - s^2) / (2 s), with s^2 by TwoProduct.
+__device__ __forceinline__ float2 df_sqrt(float2 x) {
+    const float s = sqrtf(x.x);
+    const float p = s * s, e = fmaf(s, s, -p);
+    const float2 res = df_add(x, make_float2(-p, -e));
+    return df_fast_two_sum(s, res.x / (2.0f * s));
+}
+
+// The per-node inputs of the recurrences (NodeDF) from the compensated FP32
+// moment sums (running sum and error term of n, j_x, j_y, j_z, E at sm[0..4]
+// and sm[8..12]) entirely in double-float: n = s + c, u = j / n, T = (E - n
+// |u|^2) / (D n), sqrt(T) and 1/sqrt(T) by Newton steps, and exp, erf as in
+// node_inputs_df (FP64 where |u_x| / sqrt(2T) > 2.5).  For equilibrium orders
+// up to 10: the relative error, about 1e-14, grows threefold per order in the
+// recurrence and stays below FP32 resolution there.  Returns n (FP64) for 1/tau.
+__device__ inline double node_inputs_from_sums_df(const float* sm, int D, NodeDF& o) {
+    const float2 n = df_two_sum(sm[0], sm[8]);
+    const float2 in = df_recip(n);
+    const float2 ux = df_mul(df_two_sum(sm[1], sm[9]), in), uy = df_mul(df_two_sum(sm[2], sm[10]), in),
+                 uz = df_mul(df_two_sum(sm[3], sm[11]), in);
+    const float2 u2 = df_add(df_add(df_mul(ux, ux), df_mul(uy, uy)), df_mul(uz, uz));
+    const float2 E = df_two_sum(sm[4], sm[12]);
+    float2 T = df_mul(df_add(E, df_mul(make_float2(-n.x, -n.y), u2)), in);
+    if (D == 3) T = df_mul(T, make_float2(0.3333333432674408f, -9.934107758624577e-09f));   // 1/3
+    else if (D == 2) T = make_float2(0.5f * T.x, 0.5f * T.y);
+    o.n = n;
+    o.ux = ux;
+    o.uy = uy;
+    o.uz = uz;
+    o.T = T;
+    o.Tm1 = df_add(T, make_float2(-1.0f, 0.0f));
+    const float2 irt = df_recip(df_sqrt(T));
+    const float2 z = df_mul(ux, df_mul(irt, make_float2(0.7071067690849304f, 1.2101617485882343e-08f)));
+    const float2 inv_sqrt2pi = make_float2(0.3989422917366028f, -1.1335170135851058e-08f);
+    if (fabsf(z.x) <= 2.5f) {
+        const float2 z2 = df_mul(z, z);
+        const float2 Ez = df_exp_nonpos(make_float2(-z2.x, -z2.y));
+        o.erf_z = df_erf_series(z, z2, Ez);
+        o.g0 = df_mul(df_mul(Ez, inv_sqrt2pi), irt);
+    } else {
+        const double zd = (double)z.x + (double)z.y;
+        o.erf_z = df_from_double(erf(zd));
+        o.g0 = df_mul(df_mul(df_from_double(exp(-zd * zd)), inv_sqrt2pi), irt);
+    }
+    return (double)n.x + (double)n.y;
 }
 
 }  // namespace hlb

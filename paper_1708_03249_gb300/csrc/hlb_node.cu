@@ -315,13 +315,26 @@ __global__ void __launch_bounds__(128) coef_df_kernel(const GroupDev g, const fl
         const int ii = g.ninst > 1 ? find_slot(g.node_start, g.ninst, node) : 0;
         const double inv_Kn = g.inst[ii].inv_Kn;
         const float* sm = sums + (size_t)node * kSumStride;
-        // n, u, T in FP64 from the compensated sums (one division)
-        const double n = (double)sm[0] + (double)sm[8], in = 1.0 / n;
-        const double ux = ((double)sm[1] + (double)sm[9]) * in, uy = ((double)sm[2] + (double)sm[10]) * in,
-                     uz = ((double)sm[3] + (double)sm[11]) * in;
-        const double T = ((double)sm[4] + (double)sm[12] - n * (ux * ux + uy * uy + uz * uz)) * in *
-                         (g.D == 3 ? 1.0 / 3.0 : (g.D == 2 ? 0.5 : 1.0));
-        factor_line_df<NM>(g, n, ux, uy, uz, T, (double)n * inv_Kn, sPx, sPy, sPz, sRec, line);
+        bool done = false;
+        if constexpr (NM <= 12) {
+            if (Nx <= HLB_DF_SPECIAL_MAX_N) {
+                // n, u, T and the recurrences' start in double-float (no FP64
+                // pipe work but for 1/tau and the rare |z| > 2.5)
+                NodeDF nin;
+                const double n = node_inputs_from_sums_df(sm, g.D, nin);
+                factor_line_df_in<NM>(g, nin, n * inv_Kn, sPx, sPy, sPz, sRec, line);
+                done = true;
+            }
+        }
+        if (!done) {
+            // n, u, T in FP64 from the compensated sums (one division)
+            const double n = (double)sm[0] + (double)sm[8], in = 1.0 / n;
+            const double ux = ((double)sm[1] + (double)sm[9]) * in, uy = ((double)sm[2] + (double)sm[10]) * in,
+                         uz = ((double)sm[3] + (double)sm[11]) * in;
+            const double T = ((double)sm[4] + (double)sm[12] - n * (ux * ux + uy * uy + uz * uz)) * in *
+                             (g.D == 3 ? 1.0 / 3.0 : (g.D == 2 ? 0.5 : 1.0));
+            factor_line_df<NM>(g, n, ux, uy, uz, T, (double)n * inv_Kn, sPx, sPy, sPz, sRec, line);
+        }
         if (g.has_field) {                           // a = a_uniform + a_field(node)
             const InstDev& I = g.inst[ii];
             line[g.field_off] = (float)(I.ax + g.afield[3 * (size_t)node]);
